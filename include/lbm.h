@@ -1,0 +1,168 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) solver for the coupled Cahn-Hilliard--Navier-Stokes
+ * equations by the hybrid central-moment / BGK lattice Boltzmann scheme of
+ * De Rosis, Saito, Kaneko & Abe, "Central-moments-based lattice Boltzmann scheme for coupled
+ * Cahn-Hilliard--Navier-Stokes equations" (arXiv:1803.11345).
+ *
+ * One lattice of nx * ny D2Q9 nodes lives on one GPU.  Each node carries two population sets:
+ * f (velocity; relaxed in the paper's non-orthogonal central-moment space, Eqs. 15-17, with
+ * the surface-tension pressure tensor in its equilibrium, Eqs. 8, 11, 14) and g (order
+ * parameter phi; BGK, Eqs. 7 and 9).  One call of lbm_step advances both sets by one time
+ * step in a single fused kernel: streaming (Eqs. 4-5), phi = sum g, the isotropic stencils of
+ * Eq. 12, mu = a(-phi + phi^3) - gamma Lap(phi), p0 and p~ (Eqs. 13-14), both collisions.
+ *
+ * Conventions for every entry point
+ *   - Host arrays are owned by the caller, row-major with index y * nx + x, FP64 whatever the
+ *     storage precision.  Population arrays are 9 planes of nx * ny values, plane i = direction
+ *     i in the paper's order c_x = [0,1,0,-1,0,1,-1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1].
+ *   - The state kept between calls is the post-collision populations f*, g* of the last
+ *     completed time step; the macroscopic fields returned are those of that time level
+ *     (the collision leaves rho, rho v and phi unchanged).
+ *   - Every call returns an lbm_status.  On failure the handle (or, for lbm_init, the calling
+ *     thread) keeps a message readable with lbm_last_error.  A handle must not be used from two
+ *     host threads at once.
+ *   - Kernels run on the CUDA stream given to lbm_init (NULL = legacy default stream).
+ *     lbm_step only enqueues work; lbm_fields, lbm_conservation, lbm_get_populations,
+ *     lbm_set_populations and lbm_check synchronise that stream.
+ */
+#ifndef LBM_CH_H
+#define LBM_CH_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_PARAM = -1,     /* invalid argument; nothing was changed                        */
+  LBM_ERR_OOM = -2,       /* device allocation failed or the caller's buffer is too small */
+  LBM_ERR_CUDA = -3,      /* a CUDA call failed; the message names it                     */
+  LBM_ERR_NONFINITE = -4, /* a node produced a non-finite rho or phi (state still readable)*/
+  LBM_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up                            */
+  LBM_ERR_STATE = -6      /* call not valid for this handle                                */
+} lbm_status;
+
+/* Storage precision of the populations.  FP64: stored and computed in FP64.  FP32: stored and
+ * computed in FP32.  FP16S / BF16S: f_i - w_i and g_i (i >= 1) stored as 16-bit deviations
+ * from the rest state, g_0 stored in FP32, all arithmetic in FP32. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
+
+/* Boundaries.  PERIODIC: both directions.  WALLS_Y: periodic in x, halfway bounce-back walls
+ * at y = -1/2 (moving with x-velocity u_bottom) and y = ny - 1/2 (u_top); phi is mirrored at
+ * the walls for the stencils (d phi / dy = 0, neutral wetting).  The paper's tests use no-slip
+ * and moving walls without stating the discrete form (contact-angle and shear paragraphs). */
+typedef enum { LBM_PERIODIC = 0, LBM_WALLS_Y = 1 } lbm_bc;
+
+/* How the f relaxation frequency varies with phi.  OMEGA_LINEAR is the paper's
+ * omega_rho = omega_g + (phi+1)/2 (omega_l - omega_g) (paragraph after Eq. 14); TAU_LINEAR
+ * interpolates tau = 1/omega the same way. */
+typedef enum { LBM_OMEGA_LINEAR = 0, LBM_TAU_LINEAR = 1 } lbm_visc_interp;
+
+/* The gradient term of k8_eq.  PROJECTED (default): -(c_s^2/2) gamma |grad phi|^2, the value of
+ * the projection T^T f_eq that defines k_eq.  PRINTED: -(c_s^2/2) gamma Lap(phi) as printed in
+ * Eq. 16. */
+typedef enum { LBM_K8_PROJECTED = 0, LBM_K8_PRINTED = 1 } lbm_k8_form;
+
+/* Collision of f.  CM: the paper's central-moment collision (Eq. 17; omega_4 = omega_5 =
+ * omega_rho, omega_3 free, omega_6..8 = 1).  BGK: the double-BGK baseline of Eq. 6. */
+typedef enum { LBM_COLLIDE_CM = 0, LBM_COLLIDE_BGK = 1 } lbm_collision;
+
+/* The problem statement, in the paper's symbols (paragraph after Eq. 14 and the set-ups of
+ * the bubble, contact-angle and shear tests). */
+typedef struct lbm_params {
+  int nx, ny;             /* lattice size, each >= 3; (pitch * ny) must fit in int32          */
+  double tau_l, tau_g;    /* f relaxation times of phase l (phi = +1) and g (phi = -1);       */
+                          /* nu = c_s^2 (tau - 1/2), c_s^2 = 1/3; each tau > 1/2              */
+  double M, Gamma;        /* mobility and the free parameter Gamma: omega_phi from            */
+                          /* M = (1/omega_phi - 1/2) Gamma c_s^2; M > 0, Gamma > 0            */
+  double gamma, a;        /* free-energy constants (sigma = sqrt(8 gamma a / 9)); >= 0        */
+  double omega3;          /* relaxation frequency of k3 (bulk viscosity), in (0, 2)           */
+  int k8_form;            /* lbm_k8_form                                                      */
+  int visc;               /* lbm_visc_interp                                                  */
+  int bc;                 /* lbm_bc                                                           */
+  double u_top, u_bottom; /* wall x-velocities for LBM_WALLS_Y                                */
+  int prec;               /* lbm_precision                                                    */
+  int collision;          /* lbm_collision                                                    */
+} lbm_params;
+
+typedef struct lbm_lattice lbm_lattice; /* opaque handle */
+
+/* Fill *p with the paper's defaults: M = 0.1, Gamma = 1, gamma = a = 0.04, tau_l = tau_g = 0.8
+ * (nu = 0.1), omega3 = 1, projected k8, omega-linear viscosity, periodic, FP32, CM collision.
+ * nx = ny = 0 (the caller must set them). */
+LBM_API void lbm_default_params(lbm_params* p);
+
+/* Device bytes one lattice needs (both population copies plus a small status block) when the
+ * caller supplies the memory to lbm_init.  Returns LBM_ERR_PARAM for invalid parameters. */
+LBM_API int lbm_state_bytes(const lbm_params* p, size_t* bytes);
+
+/* Create a lattice and set its state from the initial fields, following the paper's start
+ * ("fluid initially at rest, density 1", stability paragraph): the populations are the
+ * equilibria of Eqs. 8-10 built from phi0 (with the Eq. 12 stencils), ux0, uy0, rho0, after
+ * one collision at t = 0.
+ *   phi0            host, nx*ny FP64, required, finite.
+ *   ux0, uy0, rho0  host, nx*ny FP64 or NULL (NULL means 0, 0 and 1).
+ *   device_buffer   NULL: the library allocates (cudaMalloc) and frees in lbm_free.
+ *                   Otherwise a device pointer, 256-byte aligned, of buffer_bytes >=
+ *                   lbm_state_bytes(); the caller keeps ownership and must keep it alive
+ *                   until lbm_free.
+ *   stream          cudaStream_t to run on, or NULL.
+ *   out             receives the handle; *out is NULL on failure.
+ * Errors: LBM_ERR_PARAM (bad parameters or non-finite input), LBM_ERR_OOM, LBM_ERR_CUDA. */
+LBM_API int lbm_init(const lbm_params* p, const double* phi0, const double* ux0, const double* uy0,
+             const double* rho0, void* device_buffer, size_t buffer_bytes, void* stream,
+             lbm_lattice** out);
+
+/* Advance n >= 0 time steps (Eqs. 4-5 streaming, then both collisions), one fused kernel launch
+ * per step, asynchronously on the lattice's stream.  Errors: LBM_ERR_PARAM (n < 0),
+ * LBM_ERR_CUDA (launch failure). */
+LBM_API int lbm_step(lbm_lattice* h, int n);
+
+/* Copy the macroscopic fields rho = sum f, v = sum f c / rho, phi = sum g (paragraph after
+ * Eq. 14) of the current time level into host arrays of nx*ny FP64; any pointer may be NULL.
+ * Synchronises.  Returns LBM_ERR_NONFINITE if any step since the last check produced a
+ * non-finite rho or phi (the fields are still copied). */
+LBM_API int lbm_fields(lbm_lattice* h, double* rho, double* ux, double* uy, double* phi);
+
+/* FP64 totals over the lattice, computed on the GPU in a fixed order (deterministic):
+ * sum phi, sum rho and the momentum sum rho v (mom[0], mom[1]); any pointer may be NULL.
+ * The scheme conserves sum phi and sum rho exactly (Eq. 10 closures, k_0 invariance) and the
+ * momentum on a periodic lattice (k_1 = k_2 = 0 invariance, discussion after Eq. 17).
+ * Synchronises. */
+LBM_API int lbm_conservation(lbm_lattice* h, double* sum_phi, double* sum_rho, double* mom);
+
+/* Raw post-collision populations f*, g* as 9 planes of nx*ny FP64 each (host, caller-owned);
+ * either pointer may be NULL.  Synchronises. */
+LBM_API int lbm_get_populations(lbm_lattice* h, double* f, double* g);
+
+/* Replace the state with the given post-collision populations (same layout), e.g. to resume a
+ * checkpoint.  16-bit storage rounds them.  Synchronises.  LBM_ERR_PARAM on NULL input. */
+LBM_API int lbm_set_populations(lbm_lattice* h, const double* f, const double* g);
+
+/* Synchronise and report whether any step since the last check produced a non-finite rho or
+ * phi (LBM_ERR_NONFINITE) or a CUDA error occurred (LBM_ERR_CUDA); clears the flag. */
+LBM_API int lbm_check(lbm_lattice* h);
+
+/* Time level reached (number of completed steps since lbm_init). */
+LBM_API long long lbm_time(const lbm_lattice* h);
+
+/* Message of the last failure on this handle, or of the calling thread's last lbm_init failure
+ * when h is NULL.  Never NULL; the empty string when there was none. */
+LBM_API const char* lbm_last_error(const lbm_lattice* h);
+
+/* Release the handle and any memory the library allocated.  NULL-safe. */
+LBM_API void lbm_free(lbm_lattice* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_CH_H */

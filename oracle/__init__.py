@@ -91,6 +91,7 @@ def _load():
     lib.orc_set_populations.argtypes = [p, dp, dp]
     lib.orc_sums.argtypes = [p, dp]
     lib.orc_free.argtypes = [p]
+    lib.orc_node_update.argtypes = [pp, dp, dp, i, i, dp, dp]
     lib.orc_set_threads.argtypes = [i]
     lib.orc_set_threads.restype = i
     _lib = lib
@@ -188,6 +189,16 @@ def stencils(phi, walls: bool = False):
     gx, gy, lap = (np.zeros_like(phi) for _ in range(3))
     _load().orc_stencils(nx, ny, int(walls), _ptr(phi), _ptr(gx), _ptr(gy), _ptr(lap))
     return gx, gy, lap
+
+
+def node_update(params: _Params, f, g, x: int, y: int):
+    """Post-collision (f, g) of node (x, y) one step after the full-lattice post-collision
+    state f, g ((9, ny, nx) arrays), from that node's neighbourhood only."""
+    f = _f64(f)
+    g = _f64(g)
+    fo, go = np.zeros(9), np.zeros(9)
+    _load().orc_node_update(ctypes.byref(params), _ptr(f), _ptr(g), int(x), int(y), _ptr(fo), _ptr(go))
+    return fo, go
 
 
 # --------------------------------------------------------------------------------------

@@ -442,6 +442,69 @@ void orc_sums(void* h, double* out /* [sum_phi, sum_rho, sum_jx, sum_jy] */) {
   for (int q = 0; q < 4; ++q) out[q] = acc[q];
 }
 
+// Post-collision populations of the single node (x, y) one step after the given full-lattice
+// post-collision state (f, g: 9 planes of nx*ny each), computed from its neighbourhood only:
+// the populations arriving at each node of the 3x3 block around (x, y) by the same streaming
+// rule as stream_all (gathered instead of pushed), phi there, the Eq. 12 stencils at (x, y),
+// and both collisions.  Used to check single nodes of lattices too large for a full step.
+static double arriving(const orc_params* P, const double* s, long N, int x, int y, int i) {
+  const int nx = P->nx, ny = P->ny;
+  int ys = y - CY[i];
+  if (P->walls && (ys < 0 || ys >= ny)) {
+    // the population of direction opp(i) left (x, y) into the wall and came back reflected
+    int j = opposite(i);
+    long n = (long)y * nx + x;
+    double tot = 0;
+    for (int k = 0; k < 9; ++k) tot += s[k * N + n];
+    double uw = (ys < 0) ? P->u_bottom : P->u_top;
+    return s[j * N + n] - 2.0 * W[j] * tot * (CX[j] * uw) / CS2;
+  }
+  ys = (ys % ny + ny) % ny;
+  int xs = ((x - CX[i]) % nx + nx) % nx;
+  return s[i * N + (long)ys * nx + xs];
+}
+
+void orc_node_update(const orc_params* P, const double* f, const double* g, int x, int y,
+                     double* fout, double* gout) {
+  const int nx = P->nx, ny = P->ny;
+  const long N = (long)nx * ny;
+  double phi3[3][3];
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      int xx = ((x + dx) % nx + nx) % nx;
+      int yy = y + dy;
+      if (P->walls) {
+        if (yy < 0) yy = 0;
+        if (yy >= ny) yy = ny - 1;
+      } else {
+        yy = (yy % ny + ny) % ny;
+      }
+      double s = 0;
+      for (int i = 0; i < 9; ++i) s += arriving(P, g, N, xx, yy, i);
+      phi3[dy + 1][dx + 1] = s;
+    }
+  double gxv = 0, gyv = 0, lap = 0;
+  for (int i = 0; i < 9; ++i) {
+    double v = phi3[CY[i] + 1][CX[i] + 1];
+    gxv += SDX[i] * v;
+    gyv += SDY[i] * v;
+    lap += SLAP[i] * v;
+  }
+  double fn[9], gn[9];
+  for (int i = 0; i < 9; ++i) {
+    fn[i] = arriving(P, f, N, x, y, i);
+    gn[i] = arriving(P, g, N, x, y, i);
+  }
+  double rho = 0, jx = 0, jy = 0;
+  for (int i = 0; i < 9; ++i) {
+    rho += fn[i];
+    jx += fn[i] * CX[i];
+    jy += fn[i] * CY[i];
+  }
+  orc_collide_f(P, fn, phi3[1][1], gxv, gyv, lap, fout);
+  orc_collide_g(P, gn, jx / rho, jy / rho, gxv, gyv, lap, gout);
+}
+
 void orc_free(void* h) {
   orc_state* S = (orc_state*)h;
   if (!S) return;

@@ -1,0 +1,346 @@
+// C ABI of the solver (declarations and contracts in include/lbm.h).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmch;
+
+struct lbm_lattice {
+  lbm_params p;
+  HostGeometry geo;
+  HostPhys phys;
+  StepTile tile;
+  cudaStream_t stream;
+  int device;
+  char* buf;        // [buffer 0 | buffer 1 | status block]
+  size_t pop_bytes; // bytes of one population buffer (256-aligned)
+  bool owns;
+  int cur;          // which buffer holds the state
+  int* flag;        // device: non-finite flag
+  double* out4;     // device: reduction result
+  long long t;
+  char err[512];
+};
+
+namespace {
+
+thread_local char g_init_err[512] = "";
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kStatusBytes = 256;
+
+void set_err(char* dst, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(lbm_lattice* h, const char* what, cudaError_t e) {
+  set_err(h->err, "%s: %s", what, cudaGetErrorString(e));
+  return LBM_ERR_CUDA;
+}
+
+char* state_buf(lbm_lattice* h) { return h->buf + (size_t)h->cur * h->pop_bytes; }
+char* other_buf(lbm_lattice* h) { return h->buf + (size_t)(1 - h->cur) * h->pop_bytes; }
+
+// Validates parameters and fills the derived geometry/physics.  Returns a message or NULL.
+const char* check_params(const lbm_params* p, HostGeometry* g, HostPhys* ph) {
+  if (!p) return "params is NULL";
+  if (p->nx < 3 || p->ny < 3) return "nx and ny must be >= 3";
+  if (p->prec < LBM_FP64 || p->prec > LBM_BF16S) return "prec must be an lbm_precision";
+  if (p->bc != LBM_PERIODIC && p->bc != LBM_WALLS_Y) return "bc must be an lbm_bc";
+  if (p->visc != LBM_OMEGA_LINEAR && p->visc != LBM_TAU_LINEAR) return "visc must be an lbm_visc_interp";
+  if (p->k8_form != LBM_K8_PROJECTED && p->k8_form != LBM_K8_PRINTED) return "k8_form must be an lbm_k8_form";
+  if (p->collision != LBM_COLLIDE_CM && p->collision != LBM_COLLIDE_BGK) return "collision must be an lbm_collision";
+  const double vals[] = {p->tau_l, p->tau_g, p->M, p->Gamma, p->gamma, p->a, p->omega3, p->u_top, p->u_bottom};
+  for (double v : vals)
+    if (!std::isfinite(v)) return "parameters must be finite";
+  if (!(p->tau_l > 0.5) || !(p->tau_g > 0.5)) return "tau_l and tau_g must exceed 1/2 (positive viscosity)";
+  if (!(p->M > 0) || !(p->Gamma > 0)) return "M and Gamma must be positive";
+  if (p->gamma < 0 || p->a < 0) return "gamma and a must be >= 0";
+  if (!(p->omega3 > 0 && p->omega3 < 2)) return "omega3 must lie in (0, 2)";
+  const long long pitch = ((long long)p->nx + 31) / 32 * 32;
+  if (pitch * (long long)p->ny > INT_MAX) return "lattice too large: pitch * ny must fit in int32";
+  g->nx = p->nx;
+  g->ny = p->ny;
+  g->pitch = (int)pitch;
+  g->plane = pitch * p->ny;
+  g->walls = p->bc == LBM_WALLS_Y;
+  const double cs2 = 1.0 / 3.0;
+  ph->tau_l = p->tau_l;
+  ph->tau_g = p->tau_g;
+  ph->omega_l = 1.0 / p->tau_l;
+  ph->omega_g = 1.0 / p->tau_g;
+  ph->omega3 = p->omega3;
+  ph->omega_phi = 1.0 / (p->M / (p->Gamma * cs2) + 0.5);
+  ph->gamma = p->gamma;
+  ph->a = p->a;
+  ph->Gamma = p->Gamma;
+  ph->u_top = p->u_top;
+  ph->u_bottom = p->u_bottom;
+  ph->visc = p->visc;
+  ph->k8_printed = p->k8_form == LBM_K8_PRINTED;
+  ph->bgk = p->collision == LBM_COLLIDE_BGK;
+  return nullptr;
+}
+
+size_t total_bytes(int prec, const HostGeometry& g, size_t* pop_bytes) {
+  size_t pb = align_up(pop_buffer_bytes(prec, g.plane));
+  // The non-state buffer doubles as scratch for staging the fields (4 nx*ny FP64) and the
+  // reduction partials; make sure it is large enough for both.
+  const size_t need = align_up(sizeof(double) * 4 * (size_t)g.nx * g.ny) + reduce_partials_bytes();
+  if (pb < need) pb = align_up(need);
+  if (pop_bytes) *pop_bytes = pb;
+  return 2 * pb + kStatusBytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tau_l = 0.8;
+  p->tau_g = 0.8;
+  p->M = 0.1;
+  p->Gamma = 1.0;
+  p->gamma = 0.04;
+  p->a = 0.04;
+  p->omega3 = 1.0;
+  p->k8_form = LBM_K8_PROJECTED;
+  p->visc = LBM_OMEGA_LINEAR;
+  p->bc = LBM_PERIODIC;
+  p->prec = LBM_FP32;
+  p->collision = LBM_COLLIDE_CM;
+}
+
+int lbm_state_bytes(const lbm_params* p, size_t* bytes) {
+  HostGeometry g;
+  HostPhys ph;
+  const char* m = check_params(p, &g, &ph);
+  if (m) {
+    set_err(g_init_err, "lbm_state_bytes: %s", m);
+    return LBM_ERR_PARAM;
+  }
+  if (!bytes) return LBM_ERR_PARAM;
+  *bytes = total_bytes(p->prec, g, nullptr);
+  return LBM_OK;
+}
+
+int lbm_init(const lbm_params* p, const double* phi0, const double* ux0, const double* uy0,
+             const double* rho0, void* device_buffer, size_t buffer_bytes, void* stream,
+             lbm_lattice** out) {
+  g_init_err[0] = 0;
+  if (!out) {
+    set_err(g_init_err, "lbm_init: out is NULL");
+    return LBM_ERR_PARAM;
+  }
+  *out = nullptr;
+  HostGeometry g;
+  HostPhys ph;
+  const char* m = check_params(p, &g, &ph);
+  if (m) {
+    set_err(g_init_err, "lbm_init: %s", m);
+    return LBM_ERR_PARAM;
+  }
+  if (!phi0) {
+    set_err(g_init_err, "lbm_init: phi0 is NULL");
+    return LBM_ERR_PARAM;
+  }
+  const long long N = (long long)g.nx * g.ny;
+  const double* ins[4] = {phi0, ux0, uy0, rho0};
+  for (int k = 0; k < 4; ++k) {
+    if (!ins[k]) continue;
+    for (long long n = 0; n < N; ++n)
+      if (!std::isfinite(ins[k][n])) {
+        set_err(g_init_err, "lbm_init: non-finite initial field %d at node %lld", k, n);
+        return LBM_ERR_PARAM;
+      }
+  }
+  if (device_buffer && ((uintptr_t)device_buffer % kAlign) != 0) {
+    set_err(g_init_err, "lbm_init: device_buffer must be %zu-byte aligned", kAlign);
+    return LBM_ERR_PARAM;
+  }
+  size_t pop_bytes = 0;
+  const size_t need = total_bytes(p->prec, g, &pop_bytes);
+  if (device_buffer && buffer_bytes < need) {
+    set_err(g_init_err, "lbm_init: device buffer of %zu bytes is smaller than the %zu needed", buffer_bytes, need);
+    return LBM_ERR_OOM;
+  }
+  lbm_lattice* h = new (std::nothrow) lbm_lattice();
+  if (!h) {
+    set_err(g_init_err, "lbm_init: host allocation failed");
+    return LBM_ERR_OOM;
+  }
+  h->p = *p;
+  h->geo = g;
+  h->phys = ph;
+  h->stream = (cudaStream_t)stream;
+  h->pop_bytes = pop_bytes;
+  h->cur = 0;
+  h->t = 0;
+  h->err[0] = 0;
+  cudaGetDevice(&h->device);
+  if (device_buffer) {
+    h->buf = (char*)device_buffer;
+    h->owns = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&h->buf, need);
+    if (e != cudaSuccess) {
+      set_err(g_init_err, "lbm_init: cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+      delete h;
+      cudaGetLastError();
+      return LBM_ERR_OOM;
+    }
+    h->owns = true;
+  }
+  h->flag = (int*)(h->buf + 2 * pop_bytes);
+  h->out4 = (double*)(h->buf + 2 * pop_bytes + 64);
+  h->tile = default_tile(p->prec, g, h->device);
+
+  // Stage the initial fields [phi | ux | uy | rho] in buffer 1, build the state in buffer 0.
+  double* stage = (double*)(h->buf + pop_bytes);
+  cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  const double defaults[4] = {0.0, 0.0, 0.0, 1.0};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    if (ins[k]) {
+      e = cudaMemcpyAsync(stage + k * N, ins[k], sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+    } else if (defaults[k] == 0.0) {
+      e = cudaMemsetAsync(stage + k * N, 0, sizeof(double) * N, h->stream);
+    } else {
+      e = launch_fill(stage + k * N, N, defaults[k], h->stream);
+    }
+  }
+  if (e == cudaSuccess) e = launch_init(p->prec, g, ph, stage, h->buf, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    set_err(g_init_err, "lbm_init: %s", cudaGetErrorString(e));
+    if (h->owns) cudaFree(h->buf);
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_lattice* h, int n) {
+  if (!h) return LBM_ERR_PARAM;
+  if (n < 0) {
+    set_err(h->err, "lbm_step: n must be >= 0");
+    return LBM_ERR_PARAM;
+  }
+  for (int s = 0; s < n; ++s) {
+    cudaError_t e = launch_step(h->p.prec, h->geo, h->phys, h->tile, state_buf(h), other_buf(h),
+                                h->flag, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, "lbm_step launch", e);
+    h->cur = 1 - h->cur;
+    ++h->t;
+  }
+  return LBM_OK;
+}
+
+int lbm_check(lbm_lattice* h) {
+  if (!h) return LBM_ERR_PARAM;
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_check", e);
+  if (flag) {
+    cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+    set_err(h->err, "non-finite rho or phi produced before time step %lld", h->t);
+    return LBM_ERR_NONFINITE;
+  }
+  return LBM_OK;
+}
+
+int lbm_fields(lbm_lattice* h, double* rho, double* ux, double* uy, double* phi) {
+  if (!h) return LBM_ERR_PARAM;
+  const long long N = (long long)h->geo.nx * h->geo.ny;
+  double* stage = (double*)other_buf(h);
+  cudaError_t e = launch_fields(h->p.prec, h->geo, state_buf(h), stage, h->stream);
+  double* outs[4] = {rho, ux, uy, phi};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    if (outs[k]) e = cudaMemcpyAsync(outs[k], stage + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_fields", e);
+  return lbm_check(h);
+}
+
+int lbm_conservation(lbm_lattice* h, double* sum_phi, double* sum_rho, double* mom) {
+  if (!h) return LBM_ERR_PARAM;
+  double* partials = (double*)other_buf(h);
+  double res[4] = {0, 0, 0, 0};
+  cudaError_t e = launch_reduce(h->p.prec, h->geo, state_buf(h), partials, h->out4, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, h->out4, sizeof(res), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_conservation", e);
+  if (sum_phi) *sum_phi = res[0];
+  if (sum_rho) *sum_rho = res[1];
+  if (mom) {
+    mom[0] = res[2];
+    mom[1] = res[3];
+  }
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_lattice* h, double* f, double* g) {
+  if (!h) return LBM_ERR_PARAM;
+  const long long N = (long long)h->geo.nx * h->geo.ny;
+  double* stage = (double*)other_buf(h);
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 18 && e == cudaSuccess; ++p) {
+    double* dst = p < 9 ? (f ? f + p * N : nullptr) : (g ? g + (p - 9) * N : nullptr);
+    if (!dst) continue;
+    e = launch_plane_get(h->p.prec, h->geo, state_buf(h), p, stage, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, stage, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_get_populations", e);
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_lattice* h, const double* f, const double* g) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!f || !g) {
+    set_err(h->err, "lbm_set_populations: f and g are required");
+    return LBM_ERR_PARAM;
+  }
+  const long long N = (long long)h->geo.nx * h->geo.ny;
+  double* stage = (double*)other_buf(h);
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 18 && e == cudaSuccess; ++p) {
+    const double* src = p < 9 ? f + p * N : g + (p - 9) * N;
+    e = cudaMemcpyAsync(stage, src, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_plane_set(h->p.prec, h->geo, state_buf(h), p, stage, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_set_populations", e);
+  return LBM_OK;
+}
+
+long long lbm_time(const lbm_lattice* h) { return h ? h->t : -1; }
+
+const char* lbm_last_error(const lbm_lattice* h) { return h ? h->err : g_init_err; }
+
+void lbm_free(lbm_lattice* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->owns) cudaFree(h->buf);
+  delete h;
+}
+
+}  // extern "C"

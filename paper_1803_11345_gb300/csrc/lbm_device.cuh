@@ -1,0 +1,301 @@
+// Device-side building blocks of the fused step: lattice constants, population storage
+// policies, streaming by pull with moving-wall bounce-back, the isotropic stencils and both
+// collisions of the hybrid central-moment / BGK scheme (arXiv:1803.11345).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmch {
+
+// D2Q9 velocities in the paper's order: c_x = [0,1,0,-1,0,1,-1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1]
+// (lattice paragraph before Eq. 4).  Written as functions so that unrolled loops fold them.
+__host__ __device__ constexpr int lat_cx(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int lat_cy(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// Direction with c_opp = -c_i.
+__host__ __device__ constexpr int lat_opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+// Weights w_0 = 4/9, w_1..4 = 1/9, w_5..8 = 1/36 (paragraph after Eq. 14), as an exact rational
+// numerator over 36.
+__host__ __device__ constexpr int lat_w36(int i) { return i == 0 ? 16 : (i <= 4 ? 4 : 1); }
+
+// ---------------------------------------------------------------------------------------------
+// Storage policies.  A population buffer holds 18 planes (f_0..f_8, g_0..g_8) of `plane`
+// elements; node (x, y) sits at y * pitch + x inside each plane.
+
+template <int PREC> struct Pop;
+
+// FP64 / FP32: plain values, plane p at element offset p * plane.
+template <class T> struct PopDense {
+  using C = T;
+  static constexpr size_t kBytesPerElem = 18 * sizeof(T);
+  __device__ __forceinline__ static C ld(const char* b, long long pl, int p, int idx) {
+    return __ldg(reinterpret_cast<const T*>(b) + p * pl + idx);
+  }
+  __device__ __forceinline__ static void st(char* b, long long pl, int p, int idx, C v) {
+    reinterpret_cast<T*>(b)[p * pl + idx] = v;
+  }
+  __device__ __forceinline__ static C ldf(const char* b, long long pl, int i, int idx) { return ld(b, pl, i, idx); }
+  __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) { return ld(b, pl, 9 + i, idx); }
+  __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) { st(b, pl, i, idx, v); }
+  __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) { st(b, pl, 9 + i, idx, v); }
+};
+template <> struct Pop<0> : PopDense<double> {};
+template <> struct Pop<1> : PopDense<float> {};
+
+// 16-bit storage: planes 0..8 hold f_i - w_i (deviation from the rest state rho = 1, v = 0),
+// planes 9..16 hold g_1..g_8 (rest value 0), all as 16-bit floats; g_0 (~phi, O(1)) is kept in an
+// FP32 plane after them.  Arithmetic is FP32.
+template <class H> struct Cvt;
+template <> struct Cvt<__half> {
+  __device__ __forceinline__ static float to(__half h) { return __half2float(h); }
+  __device__ __forceinline__ static __half from(float v) { return __float2half_rn(v); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+  __device__ __forceinline__ static float to(__nv_bfloat16 h) { return __bfloat162float(h); }
+  __device__ __forceinline__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+template <class H> struct PopHalf {
+  using C = float;
+  static constexpr size_t kBytesPerElem = 17 * sizeof(H) + sizeof(float);
+  __device__ __forceinline__ static float wrest(int i) { return (float)lat_w36(i) * (1.0f / 36.0f); }
+  __device__ __forceinline__ static C ldf(const char* b, long long pl, int i, int idx) {
+    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + i * pl + idx)) + wrest(i);
+  }
+  __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) {
+    if (i == 0) return __ldg(reinterpret_cast<const float*>(reinterpret_cast<const H*>(b) + 17 * pl) + idx);
+    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (8 + i) * pl + idx));
+  }
+  __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) {
+    reinterpret_cast<H*>(b)[i * pl + idx] = Cvt<H>::from(v - wrest(i));
+  }
+  __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) {
+    if (i == 0) {
+      reinterpret_cast<float*>(reinterpret_cast<H*>(b) + 17 * pl)[idx] = v;
+      return;
+    }
+    reinterpret_cast<H*>(b)[(8 + i) * pl + idx] = Cvt<H>::from(v);
+  }
+};
+template <> struct Pop<2> : PopHalf<__half> {};
+template <> struct Pop<3> : PopHalf<__nv_bfloat16> {};
+
+// ---------------------------------------------------------------------------------------------
+// Lattice geometry and physical parameters as passed to the kernels.
+
+struct Geometry {
+  int nx, ny, pitch;
+  long long plane;  // elements per plane (pitch * ny)
+  int walls;        // 0 periodic, 1 bounce-back walls at y = -1/2 and y = ny - 1/2
+};
+
+template <class C> struct Phys {
+  C omega_l, omega_g, tau_l, tau_g;  // f relaxation of phase l (phi=+1) and g (phi=-1)
+  C omega3, omega_phi;
+  C gamma, a, Gamma;
+  C u_top, u_bottom;  // wall x-velocities
+  int visc;           // 0 omega-linear (paper), 1 tau-linear
+  int k8_printed;     // 0 projected k8, 1 printed k8
+  int bgk;            // 0 central moments (paper), 1 BGK baseline
+};
+
+// ---------------------------------------------------------------------------------------------
+// Streaming, Eqs. 4-5, in pull form: the population of direction i at node (x, y) and time t is
+// the post-collision value of node (x - c_xi, y - c_yi) at t - 1.  x is periodic; y periodic or
+// walled.  A link whose source lies beyond a wall is the bounced-back population of the node
+// itself, opposite direction, plus the moving-wall term 6 w_i s c_xi u_w, where s is the node's
+// own density (for f) or order parameter (for g) at t - 1.
+template <int PREC, bool IS_G>
+__device__ __forceinline__ void pull(const char* __restrict__ src, const Geometry& geo,
+                                     typename Pop<PREC>::C u_top, typename Pop<PREC>::C u_bot,
+                                     int x, int y, typename Pop<PREC>::C out[9]) {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  const long long pl = geo.plane;
+  auto LD = [&](int i, int idx) -> C { return IS_G ? P::ldg(src, pl, i, idx) : P::ldf(src, pl, i, idx); };
+  const int xm = (x == 0) ? geo.nx - 1 : x - 1;
+  const int xp = (x == geo.nx - 1) ? 0 : x + 1;
+  const int r0 = y * geo.pitch;
+  const bool bot = geo.walls && y == 0;
+  const bool top = geo.walls && y == geo.ny - 1;
+  if (!bot && !top) {
+    const int ym = (y == 0) ? geo.ny - 1 : y - 1;
+    const int yp = (y == geo.ny - 1) ? 0 : y + 1;
+    const int rm = ym * geo.pitch, rp = yp * geo.pitch;
+    out[0] = LD(0, r0 + x);
+    out[1] = LD(1, r0 + xm);
+    out[2] = LD(2, rm + x);
+    out[3] = LD(3, r0 + xp);
+    out[4] = LD(4, rp + x);
+    out[5] = LD(5, rm + xm);
+    out[6] = LD(6, rm + xp);
+    out[7] = LD(7, rp + xp);
+    out[8] = LD(8, rp + xm);
+    return;
+  }
+  // Wall row: the node's own nine post-collision values give s and the reflected links.
+  C own[9];
+  C s = C(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    own[i] = LD(i, r0 + x);
+    s += own[i];
+  }
+  out[0] = own[0];
+  out[1] = LD(1, r0 + xm);
+  out[3] = LD(3, r0 + xp);
+  const C k6 = C(6) * s / C(36);
+  if (bot) {  // directions 2, 5, 6 come from below the wall at y = -1/2
+    const int rp = (y + 1) * geo.pitch;
+    out[2] = own[4];
+    out[5] = own[7] + k6 * u_bot;   // 6 w_5 s c_x5 u_w, w_5 = 1/36, c_x5 = +1
+    out[6] = own[8] - k6 * u_bot;   // c_x6 = -1
+    out[4] = LD(4, rp + x);
+    out[7] = LD(7, rp + xp);
+    out[8] = LD(8, rp + xm);
+  } else {    // directions 4, 7, 8 come from above the wall at y = ny - 1/2
+    const int rm = (y - 1) * geo.pitch;
+    out[4] = own[2];
+    out[7] = own[5] - k6 * u_top;   // c_x7 = -1
+    out[8] = own[6] + k6 * u_top;   // c_x8 = +1
+    out[2] = LD(2, rm + x);
+    out[5] = LD(5, rm + xm);
+    out[6] = LD(6, rm + xp);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Collision of one node.  Inputs: pulled f, g; phi = sum g; the Eq. 12 stencils dx, dy, lap of
+// phi.  Outputs overwrite f and g with the post-collision values.  Returns rho.
+template <class C>
+__device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C dx, C dy, C lap) {
+  const C cs2 = C(1) / C(3);
+  // Macroscopic moments (paragraph after Eq. 14).
+  const C rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const C inv_rho = C(1) / rho;
+  const C ux = jx * inv_rho, uy = jy * inv_rho;
+  const C ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+  // Chemical potential (free-energy paragraph), bulk pressure p0 (Eq. 13) and p~ (Eq. 14).
+  const C phi2 = phi * phi;
+  const C mu = ph.a * (phi2 * phi - phi) - ph.gamma * lap;
+  const C p0 = rho * cs2 + ph.a * phi2 * (C(0.75) * phi2 - C(0.5));
+  const C pt = p0 - ph.gamma * phi * lap;
+  // Relaxation frequency of f for this phi (paragraph after Eq. 14).
+  C om;
+  if (ph.visc == 0) om = ph.omega_g + C(0.5) * (phi + C(1)) * (ph.omega_l - ph.omega_g);
+  else om = C(1) / (ph.tau_g + C(0.5) * (phi + C(1)) * (ph.tau_l - ph.tau_g));
+
+  if (!ph.bgk) {
+    // Pre-collision central moments k3, k4, k5 (Eq. 15 basis, k = T^T f) from the raw second
+    // moments: kappa_20 = m_20 - rho ux^2, kappa_02 = m_02 - rho uy^2, kappa_11 = m_11 - rho ux uy.
+    const C corners = (f[5] + f[6]) + (f[7] + f[8]);
+    const C m20 = (f[1] + f[3]) + corners;
+    const C m02 = (f[2] + f[4]) + corners;
+    const C m11 = (f[5] - f[6]) + (f[7] - f[8]);
+    const C k20 = m20 - rho * ux2, k02 = m02 - rho * uy2, k11 = m11 - rho * uxy;
+    const C k3 = k20 + k02, k4 = k20 - k02, k5 = k11;
+    // Equilibrium central moments (the k_eq list and Eq. 16).
+    const C k3e = C(2) * pt;
+    const C k4e = ph.gamma * (dx * dx - dy * dy);
+    const C k5e = ph.gamma * dx * dy;
+    const C k6e = -C(0.5) * uy * k4e - C(2) * ux * k5e + rho * uy * (cs2 - ux2) - pt * uy;
+    const C k7e = C(0.5) * ux * k4e - C(2) * uy * k5e + rho * ux * (cs2 - uy2) - pt * ux;
+    const C grad_term = ph.k8_printed ? lap : (dx * dx + dy * dy);
+    const C k8e = pt * (cs2 + ux2 + uy2) - rho * cs2 * (ux2 + uy2) + C(3) * rho * ux2 * uy2 -
+                  C(0.5) * cs2 * ph.gamma * grad_term + C(0.5) * k4e * (uy2 - ux2) + C(4) * uxy * k5e;
+    // Eq. 17 with omega_4 = omega_5 = omega_rho, omega_3 free, omega_6..8 = 1.
+    const C k3s = k3 + ph.omega3 * (k3e - k3);
+    const C k4s = k4 + om * (k4e - k4);
+    const C k5s = k5 + om * (k5e - k5);
+    // f* = (T^T)^-1 k*, k* = [rho, 0, 0, k3*, k4*, k5*, k6e, k7e, k8e]: central -> raw moments by
+    // the binomial shift c = cbar + u, then the D2Q9 raw-moment inversion.
+    const C a20 = C(0.5) * (k3s + k4s), a02 = C(0.5) * (k3s - k4s), a11 = k5s;
+    const C r20 = a20 + rho * ux2;
+    const C r02 = a02 + rho * uy2;
+    const C r11 = a11 + rho * uxy;
+    const C r21 = k6e + C(2) * ux * a11 + uy * a20 + rho * ux2 * uy;
+    const C r12 = k7e + C(2) * uy * a11 + ux * a02 + rho * ux * uy2;
+    const C r22 = k8e + C(2) * (uy * k6e + ux * k7e) + uy2 * a20 + ux2 * a02 + C(4) * uxy * a11 +
+                  rho * ux2 * uy2;
+    f[0] = rho - r20 - r02 + r22;
+    const C hx = C(0.5) * (r20 - r22), hy = C(0.5) * (r02 - r22);
+    const C qx = C(0.5) * (jx - r12), qy = C(0.5) * (jy - r21);
+    f[1] = hx + qx;
+    f[3] = hx - qx;
+    f[2] = hy + qy;
+    f[4] = hy - qy;
+    const C s22 = C(0.25) * r22, s11 = C(0.25) * r11, s21 = C(0.25) * r21, s12 = C(0.25) * r12;
+    f[5] = s22 + s11 + s21 + s12;
+    f[6] = s22 - s11 + s21 - s12;
+    f[7] = s22 + s11 - s21 - s12;
+    f[8] = s22 - s11 - s21 + s12;
+  } else {
+    // Double-BGK baseline, Eq. 6 with f_eq from Eqs. 8, 10, 11.
+    const C uu = ux2 + uy2;
+    const C gxx = ph.gamma * dx * dx, gyy = ph.gamma * dy * dy, gxy = ph.gamma * dx * dy;
+    C sum = C(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const C w = C(lat_w36(i)) / C(36);
+      const C cu = C(lat_cx(i)) * ux + C(lat_cy(i)) * uy;
+      // Eq. 11 weights (w^yy_4 = +1/3): axis i: w^xx = 1/3 on x-links, -1/6 on y-links; diagonals -1/24.
+      C wxx, wyy, wxy;
+      if (i <= 4) {
+        const bool xl = lat_cx(i) != 0;
+        wxx = xl ? C(1) / C(3) : -C(1) / C(6);
+        wyy = xl ? -C(1) / C(6) : C(1) / C(3);
+        wxy = C(0);
+      } else {
+        wxx = -C(1) / C(24);
+        wyy = -C(1) / C(24);
+        wxy = C(0.25) * C(lat_cx(i) * lat_cy(i));
+      }
+      const C feq = w * (C(3) * pt + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu)) +
+                    (wxx * gxx + wyy * gyy + wxy * gxy);
+      sum += feq;
+      f[i] = f[i] + om * (feq - f[i]);
+    }
+    const C feq0 = rho - sum;
+    f[0] = f[0] + om * (feq0 - f[0]);
+  }
+
+  // g: BGK towards g_eq (Eqs. 7, 9, 10).
+  {
+    const C uu = ux2 + uy2;
+    const C gmu = ph.Gamma * mu;
+    C sum = C(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const C w = C(lat_w36(i)) / C(36);
+      const C cu = C(lat_cx(i)) * ux + C(lat_cy(i)) * uy;
+      const C geq = w * (gmu + phi * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+      sum += geq;
+      g[i] = g[i] + ph.omega_phi * (geq - g[i]);
+    }
+    g[0] = g[0] + ph.omega_phi * ((phi - sum) - g[0]);
+  }
+  return rho;
+}
+
+// Isotropic stencils of Eq. 12 from the 3x3 neighbourhood of phi.  Index convention:
+// s[dy+1][dx+1] = phi(x + dx, y + dy).
+template <class C>
+__device__ __forceinline__ void stencils(const C s[3][3], C& dx, C& dy, C& lap) {
+  const C E = s[1][2], W = s[1][0], N = s[2][1], S = s[0][1];
+  const C NE = s[2][2], NW = s[2][0], SW = s[0][0], SE = s[0][2];
+  dx = (E - W) * (C(1) / C(3)) + ((NE - SW) + (SE - NW)) * (C(1) / C(12));
+  dy = (N - S) * (C(1) / C(3)) + ((NE - SW) + (NW - SE)) * (C(1) / C(12));
+  lap = (C(4) * ((E + W) + (N + S)) + ((NE + SW) + (NW + SE)) - C(20) * s[1][1]) * (C(1) / C(6));
+}
+
+}  // namespace lbmch

@@ -1,0 +1,536 @@
+// Kernels of the hybrid central-moment / BGK lattice Boltzmann scheme for the coupled
+// Cahn-Hilliard--Navier-Stokes equations (arXiv:1803.11345), for sm_103a.
+//
+// k_step is the whole time step in one launch: every CTA owns a strip of BX columns and
+// `rows` lattice rows and marches down it BY rows at a time.  For each block of rows it
+//   (1) pulls g (Eq. 5) for the NEXT block of rows, sums phi = sum g and stores phi in a
+//       shared-memory ring of rows that also holds one halo column on each side;
+//   (2) pulls f (Eq. 4) for the current rows;
+//   (3) after one __syncthreads, reads the 3x3 phi neighbourhood from the ring for the Eq. 12
+//       stencils and runs both collisions on the g values it pulled one iteration earlier;
+//   (4) writes f*, g* to the other population buffer.
+// phi at the neighbours at the same time level exists only after their g has been pulled, so
+// the halo rows/columns are pulled by this CTA as well (their bytes are mostly L2 hits).
+// Populations live in two buffers (A -> B, then B -> A); the state between launches is the
+// post-collision populations.
+#include <algorithm>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbmch {
+
+namespace {
+
+template <class C> Phys<C> to_phys(const HostPhys& h) {
+  Phys<C> p;
+  p.omega_l = (C)h.omega_l;
+  p.omega_g = (C)h.omega_g;
+  p.tau_l = (C)h.tau_l;
+  p.tau_g = (C)h.tau_g;
+  p.omega3 = (C)h.omega3;
+  p.omega_phi = (C)h.omega_phi;
+  p.gamma = (C)h.gamma;
+  p.a = (C)h.a;
+  p.Gamma = (C)h.Gamma;
+  p.u_top = (C)h.u_top;
+  p.u_bottom = (C)h.u_bottom;
+  p.visc = h.visc;
+  p.k8_printed = h.k8_printed;
+  p.bgk = h.bgk;
+  return p;
+}
+
+Geometry to_geo(const HostGeometry& h) {
+  Geometry g;
+  g.nx = h.nx;
+  g.ny = h.ny;
+  g.pitch = h.pitch;
+  g.plane = h.plane;
+  g.walls = h.walls;
+  return g;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------------------------
+// Fused step.
+
+template <int PREC, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
+       const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  constexpr int RING = 3 * BY + 1;  // rows kept: see the ring argument below
+  constexpr int SW = BX + 2;        // one halo column on each side
+  __shared__ C sphi[RING][SW];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * BX;
+  const int y0 = blockIdx.y * rows;
+  const int y1 = min(y0 + rows, geo.ny);
+  const int xv = min(BX, geo.nx - x0);  // valid columns of this strip
+  const int x = x0 + tx;
+  const bool colv = tx < xv;
+  const int xl = (x0 == 0) ? geo.nx - 1 : x0 - 1;        // left halo column
+  const int xr = (x0 + xv == geo.nx) ? 0 : x0 + xv;      // right halo column
+
+  // Virtual row r in [y0 - 1, y1] -> physical row (periodic wrap, or the wall mirror
+  // phi(x, -1) = phi(x, 0), phi(x, ny) = phi(x, ny - 1)).
+  auto phys_row = [&](int r) -> int {
+    if (r < 0) return geo.walls ? 0 : r + geo.ny;
+    if (r >= geo.ny) return geo.walls ? geo.ny - 1 : r - geo.ny;
+    return r;
+  };
+  auto slot = [&](int r) -> int { return (r - (y0 - 1)) % RING; };
+  auto sum9 = [](const C v[9]) -> C {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+  };
+  // phi of virtual row r for this thread's column (and the halo columns for tx == 0 / BX-1);
+  // the pulled g of the own column is returned in gkeep.
+  auto phi_row = [&](int r, C gkeep[9]) {
+    const int yr = phys_row(r);
+    const int sl = slot(r);
+    C gt[9];
+    if (colv) {
+      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, x, yr, gkeep);
+      sphi[sl][tx + 1] = sum9(gkeep);
+    }
+    if (tx == 0) {
+      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xl, yr, gt);
+      sphi[sl][0] = sum9(gt);
+    }
+    if (tx == BX - 1) {
+      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xr, yr, gt);
+      sphi[sl][xv + 1] = sum9(gt);
+    }
+  };
+
+  C gcur[9], gnxt[9];
+  // Prologue: rows y0 - 1 (halo) and y0 .. y0 + BY - 1 (own), or up to y1 if shorter.
+  {
+    const int r = y0 + ty;
+    if (r <= y1) phi_row(r, gcur);
+    if (ty == 0) {
+      C gt[9];
+      phi_row(y0 - 1, gt);
+    }
+  }
+
+  // Ring argument: iteration j writes rows [Y+BY, Y+2BY) and reads rows [Y-1, Y+BY]; iteration
+  // j-1 read [Y-BY-1, Y].  A thread may still be reading iteration j-1's rows while another
+  // writes iteration j's, so those two ranges (3BY+1 rows) must map to distinct slots: RING =
+  // 3BY+1.  Iteration j+1's writes cannot meet iteration j-1's reads (one barrier apart).
+  for (int Y = y0; Y < y1; Y += BY) {
+    const int rn = Y + BY + ty;
+    if (rn <= y1) phi_row(rn, gnxt);
+    const int r = Y + ty;
+    const bool act = colv && r < y1;
+    C f[9];
+    if (act) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, r, f);
+    __syncthreads();
+    if (act) {
+      C s[3][3];
+      const int sm = slot(r - 1), s0 = slot(r), sp = slot(r + 1);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        s[0][d] = sphi[sm][tx + d];
+        s[1][d] = sphi[s0][tx + d];
+        s[2][d] = sphi[sp][tx + d];
+      }
+      C dxp, dyp, lap;
+      stencils<C>(s, dxp, dyp, lap);
+      const C phi = s[1][1];
+      const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
+      if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
+      const int idx = r * geo.pitch + x;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        P::stf(dst, geo.plane, i, idx, f[i]);
+        P::stg(dst, geo.plane, i, idx, gcur[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gcur[i] = gnxt[i];
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// Initial state: populations = equilibria of Eqs. 8-10 built from the initial fields, then one
+// collision at t = 0.  fields = [phi | ux | uy | rho], each nx*ny FP64, dense rows.
+
+template <int PREC>
+__global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst, const Geometry geo,
+                       const Phys<typename Pop<PREC>::C> ph) {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const long long N = (long long)geo.nx * geo.ny;
+  const double* phi0 = fields;
+  const double* ux0 = fields + N;
+  const double* uy0 = fields + 2 * N;
+  const double* rho0 = fields + 3 * N;
+  C s[3][3];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      int xx = x + dx;
+      xx = xx < 0 ? xx + geo.nx : (xx >= geo.nx ? xx - geo.nx : xx);
+      int yy = y + dy;
+      if (geo.walls) yy = yy < 0 ? 0 : (yy >= geo.ny ? geo.ny - 1 : yy);
+      else yy = yy < 0 ? yy + geo.ny : (yy >= geo.ny ? yy - geo.ny : yy);
+      s[dy + 1][dx + 1] = (C)phi0[(long long)yy * geo.nx + xx];
+    }
+  C gx, gy, lap;
+  stencils<C>(s, gx, gy, lap);
+  const long long n = (long long)y * geo.nx + x;
+  const C phi = s[1][1], ux = (C)ux0[n], uy = (C)uy0[n], rho = (C)rho0[n];
+  const C cs2 = C(1) / C(3);
+  const C phi2 = phi * phi;
+  const C mu = ph.a * (phi2 * phi - phi) - ph.gamma * lap;
+  const C pt = rho * cs2 + ph.a * phi2 * (C(0.75) * phi2 - C(0.5)) - ph.gamma * phi * lap;
+  const C uu = ux * ux + uy * uy;
+  C f[9], g[9];
+  C sf = C(0), sg = C(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const C w = C(lat_w36(i)) / C(36);
+    const C cu = C(lat_cx(i)) * ux + C(lat_cy(i)) * uy;
+    const C poly = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+    C wxx, wyy, wxy;
+    if (i <= 4) {
+      const bool xl = lat_cx(i) != 0;
+      wxx = xl ? C(1) / C(3) : -C(1) / C(6);
+      wyy = xl ? -C(1) / C(6) : C(1) / C(3);
+      wxy = C(0);
+    } else {
+      wxx = -C(1) / C(24);
+      wyy = -C(1) / C(24);
+      wxy = C(0.25) * C(lat_cx(i) * lat_cy(i));
+    }
+    f[i] = w * (C(3) * pt + rho * poly) + ph.gamma * (wxx * gx * gx + wyy * gy * gy + wxy * gx * gy);
+    g[i] = w * (ph.Gamma * mu + phi * poly);
+    sf += f[i];
+    sg += g[i];
+  }
+  f[0] = rho - sf;
+  g[0] = phi - sg;
+  collide<C>(ph, f, g, phi, gx, gy, lap);
+  const int idx = y * geo.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    P::stf(dst, geo.plane, i, idx, f[i]);
+    P::stg(dst, geo.plane, i, idx, g[i]);
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// Macroscopic fields of the stored state: out = [rho | ux | uy | phi], dense FP64.
+
+template <int PREC>
+__global__ void k_fields(const char* __restrict__ src, const Geometry geo, double* __restrict__ out) {
+  using P = Pop<PREC>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const int idx = y * geo.pitch + x;
+  double rho = 0, jx = 0, jy = 0, phi = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double fi = (double)P::ldf(src, geo.plane, i, idx);
+    rho += fi;
+    jx += fi * lat_cx(i);
+    jy += fi * lat_cy(i);
+    phi += (double)P::ldg(src, geo.plane, i, idx);
+  }
+  const long long N = (long long)geo.nx * geo.ny;
+  const long long n = (long long)y * geo.nx + x;
+  out[n] = rho;
+  out[N + n] = jx / rho;
+  out[2 * N + n] = jy / rho;
+  out[3 * N + n] = phi;
+}
+
+// -------------------------------------------------------------------------------------------
+// Deterministic FP64 reduction: fixed grid, fixed per-thread order, fixed tree.
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+template <int PREC>
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_partials(const char* __restrict__ src, const Geometry geo, double* __restrict__ partials) {
+  using P = Pop<PREC>;
+  __shared__ double sh[4][kRedThreads];
+  double acc[4] = {0, 0, 0, 0};
+  const long long N = (long long)geo.nx * geo.ny;
+  for (long long n = (long long)blockIdx.x * kRedThreads + threadIdx.x; n < N;
+       n += (long long)gridDim.x * kRedThreads) {
+    const int y = (int)(n / geo.nx), x = (int)(n - (long long)y * geo.nx);
+    const int idx = y * geo.pitch + x;
+    double rho = 0, jx = 0, jy = 0, phi = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const double fi = (double)P::ldf(src, geo.plane, i, idx);
+      rho += fi;
+      jx += fi * lat_cx(i);
+      jy += fi * lat_cy(i);
+      phi += (double)P::ldg(src, geo.plane, i, idx);
+    }
+    acc[0] += phi;
+    acc[1] += rho;
+    acc[2] += jx;
+    acc[3] += jy;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_final(const double* __restrict__ partials, int nparts, double* __restrict__ out4) {
+  __shared__ double sh[4][kRedThreads];
+  double acc[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nparts; b += kRedThreads)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += partials[b * 4 + q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// -------------------------------------------------------------------------------------------
+// One population plane between the state and a dense FP64 array.
+
+template <int PREC>
+__global__ void k_plane_get(const char* __restrict__ src, const Geometry geo, int p, double* __restrict__ out) {
+  using P = Pop<PREC>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const int idx = y * geo.pitch + x;
+  const double v = p < 9 ? (double)P::ldf(src, geo.plane, p, idx) : (double)P::ldg(src, geo.plane, p - 9, idx);
+  out[(long long)y * geo.nx + x] = v;
+}
+
+template <int PREC>
+__global__ void k_plane_set(char* __restrict__ dst, const Geometry geo, int p, const double* __restrict__ in) {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= geo.nx || y >= geo.ny) return;
+  const int idx = y * geo.pitch + x;
+  const C v = (C)in[(long long)y * geo.nx + x];
+  if (p < 9) P::stf(dst, geo.plane, p, idx, v);
+  else P::stg(dst, geo.plane, p - 9, idx, v);
+}
+
+// -------------------------------------------------------------------------------------------
+// Host launchers.
+
+size_t pop_buffer_bytes(int prec, long long plane) {
+  switch (prec) {
+    case 0: return (size_t)plane * Pop<0>::kBytesPerElem;
+    case 1: return (size_t)plane * Pop<1>::kBytesPerElem;
+    case 2: return (size_t)plane * Pop<2>::kBytesPerElem;
+    case 3: return (size_t)plane * Pop<3>::kBytesPerElem;
+  }
+  return 0;
+}
+
+namespace {
+
+dim3 node_grid(const HostGeometry& g, dim3 blk) {
+  return dim3((g.nx + blk.x - 1) / blk.x, (g.ny + blk.y - 1) / blk.y);
+}
+
+template <int PREC, int BX, int BY>
+cudaError_t step_bxby(const HostGeometry& g, const HostPhys& p, int rows, const char* src, char* dst,
+                      int* flag, cudaStream_t s) {
+  using C = typename Pop<PREC>::C;
+  dim3 blk(BX, BY);
+  dim3 grd((g.nx + BX - 1) / BX, (g.ny + rows - 1) / rows);
+  k_step<PREC, BX, BY><<<grd, blk, 0, s>>>(src, dst, to_geo(g), to_phys<C>(p), rows, flag);
+  return cudaGetLastError();
+}
+
+// Compiled tile shapes.
+#define LBM_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(256, 1)
+
+template <int PREC>
+cudaError_t step_prec(const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
+                      char* dst, int* flag, cudaStream_t s) {
+#define LBM_CASE(X, Y) \
+  if (t.bx == X && t.by == Y) return step_bxby<PREC, X, Y>(g, p, t.rows, src, dst, flag, s);
+  LBM_TILES(LBM_CASE)
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int occupancy(int bx, int by) {
+  int nb = 0;
+#define LBM_CASE(X, Y) \
+  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<PREC, X, Y>, X * Y, 0);
+  LBM_TILES(LBM_CASE)
+#undef LBM_CASE
+  return nb;
+}
+
+}  // namespace
+
+bool tile_supported(int prec, int bx, int by) {
+  (void)prec;
+#define LBM_CASE(X, Y) \
+  if (bx == X && by == Y) return true;
+  LBM_TILES(LBM_CASE)
+#undef LBM_CASE
+  return false;
+}
+
+StepTile default_tile(int prec, const HostGeometry& g, int device) {
+  StepTile t;
+  if (prec == 0) {
+    t.bx = 32;
+    t.by = 4;
+  } else {
+    t.bx = 64;
+    t.by = 4;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (sms <= 0) sms = 152;
+  int per_sm = 0;
+  switch (prec) {
+    case 0: per_sm = occupancy<0>(t.bx, t.by); break;
+    case 1: per_sm = occupancy<1>(t.bx, t.by); break;
+    case 2: per_sm = occupancy<2>(t.bx, t.by); break;
+    case 3: per_sm = occupancy<3>(t.bx, t.by); break;
+  }
+  if (per_sm <= 0) per_sm = 1;
+  // One full wave: gx * gy ~ sms * per_sm CTAs.
+  const int gx = (g.nx + t.bx - 1) / t.bx;
+  int gy = std::max(1, (sms * per_sm) / gx);
+  int rows = (g.ny + gy - 1) / gy;
+  rows = ((rows + t.by - 1) / t.by) * t.by;
+  t.rows = std::max(rows, t.by);
+  return t;
+}
+
+cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, const double* fields,
+                        char* dst, cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grd = node_grid(g, blk);
+  switch (prec) {
+    case 0: k_init<0><<<grd, blk, 0, s>>>(fields, dst, to_geo(g), to_phys<double>(p)); break;
+    case 1: k_init<1><<<grd, blk, 0, s>>>(fields, dst, to_geo(g), to_phys<float>(p)); break;
+    case 2: k_init<2><<<grd, blk, 0, s>>>(fields, dst, to_geo(g), to_phys<float>(p)); break;
+    case 3: k_init<3><<<grd, blk, 0, s>>>(fields, dst, to_geo(g), to_phys<float>(p)); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
+                        const char* src, char* dst, int* flag, cudaStream_t s) {
+  switch (prec) {
+    case 0: return step_prec<0>(g, p, t, src, dst, flag, s);
+    case 1: return step_prec<1>(g, p, t, src, dst, flag, s);
+    case 2: return step_prec<2>(g, p, t, src, dst, flag, s);
+    case 3: return step_prec<3>(g, p, t, src, dst, flag, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fields(int prec, const HostGeometry& g, const char* src, double* out, cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grd = node_grid(g, blk);
+  switch (prec) {
+    case 0: k_fields<0><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
+    case 1: k_fields<1><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
+    case 2: k_fields<2><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
+    case 3: k_fields<3><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_fill(double* __restrict__ p, long long n, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s) {
+  const int nb = (int)std::min<long long>(4096, (n + 255) / 256);
+  k_fill<<<std::max(nb, 1), 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+size_t reduce_partials_bytes() { return sizeof(double) * 4 * kRedBlocks; }
+
+cudaError_t launch_reduce(int prec, const HostGeometry& g, const char* src, double* partials,
+                          double* out4, cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny;
+  int nb = (int)std::min<long long>(kRedBlocks, (N + kRedThreads - 1) / kRedThreads);
+  nb = std::max(nb, 1);
+  switch (prec) {
+    case 0: k_reduce_partials<0><<<nb, kRedThreads, 0, s>>>(src, to_geo(g), partials); break;
+    case 1: k_reduce_partials<1><<<nb, kRedThreads, 0, s>>>(src, to_geo(g), partials); break;
+    case 2: k_reduce_partials<2><<<nb, kRedThreads, 0, s>>>(src, to_geo(g), partials); break;
+    case 3: k_reduce_partials<3><<<nb, kRedThreads, 0, s>>>(src, to_geo(g), partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_final<<<1, kRedThreads, 0, s>>>(partials, nb, out4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_get(int prec, const HostGeometry& g, const char* src, int p, double* out,
+                             cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grd = node_grid(g, blk);
+  switch (prec) {
+    case 0: k_plane_get<0><<<grd, blk, 0, s>>>(src, to_geo(g), p, out); break;
+    case 1: k_plane_get<1><<<grd, blk, 0, s>>>(src, to_geo(g), p, out); break;
+    case 2: k_plane_get<2><<<grd, blk, 0, s>>>(src, to_geo(g), p, out); break;
+    case 3: k_plane_get<3><<<grd, blk, 0, s>>>(src, to_geo(g), p, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_set(int prec, const HostGeometry& g, char* dst, int p, const double* in,
+                             cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grd = node_grid(g, blk);
+  switch (prec) {
+    case 0: k_plane_set<0><<<grd, blk, 0, s>>>(dst, to_geo(g), p, in); break;
+    case 1: k_plane_set<1><<<grd, blk, 0, s>>>(dst, to_geo(g), p, in); break;
+    case 2: k_plane_set<2><<<grd, blk, 0, s>>>(dst, to_geo(g), p, in); break;
+    case 3: k_plane_set<3><<<grd, blk, 0, s>>>(dst, to_geo(g), p, in); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbmch

@@ -1,0 +1,241 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (same names, argument marshalling only).
+
+Every step of the scheme runs in the CUDA library ``_build/liblbmch.so``; if that library is
+missing this module raises on import — there is no CPU fallback.  PyTorch supplies device memory
+(the population buffers are one ``torch.uint8`` CUDA tensor handed to ``lbm_init``) and the stream
+(``torch.cuda.current_stream()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
+LBM_PERIODIC, LBM_WALLS_Y = 0, 1
+LBM_OMEGA_LINEAR, LBM_TAU_LINEAR = 0, 1
+LBM_K8_PROJECTED, LBM_K8_PRINTED = 0, 1
+LBM_COLLIDE_CM, LBM_COLLIDE_BGK = 0, 1
+
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("tau_l", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("M", ctypes.c_double), ("Gamma", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("a", ctypes.c_double),
+        ("omega3", ctypes.c_double),
+        ("k8_form", ctypes.c_int), ("visc", ctypes.c_int), ("bc", ctypes.c_int),
+        ("u_top", ctypes.c_double), ("u_bottom", ctypes.c_double),
+        ("prec", ctypes.c_int), ("collision", ctypes.c_int),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is not built; run paper_1803_11345_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, i, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_size_t
+    pp = ctypes.POINTER(lbm_params)
+    lib.lbm_default_params.argtypes = [pp]
+    lib.lbm_default_params.restype = None
+    lib.lbm_state_bytes.argtypes = [pp, ctypes.POINTER(sz)]
+    lib.lbm_state_bytes.restype = i
+    lib.lbm_init.argtypes = [pp, dp, dp, dp, dp, vp, sz, vp, ctypes.POINTER(vp)]
+    lib.lbm_init.restype = i
+    lib.lbm_step.argtypes = [vp, i]
+    lib.lbm_step.restype = i
+    lib.lbm_fields.argtypes = [vp, dp, dp, dp, dp]
+    lib.lbm_fields.restype = i
+    lib.lbm_conservation.argtypes = [vp, dp, dp, dp]
+    lib.lbm_conservation.restype = i
+    lib.lbm_get_populations.argtypes = [vp, dp, dp]
+    lib.lbm_get_populations.restype = i
+    lib.lbm_set_populations.argtypes = [vp, dp, dp]
+    lib.lbm_set_populations.restype = i
+    lib.lbm_check.argtypes = [vp]
+    lib.lbm_check.restype = i
+    lib.lbm_time.argtypes = [vp]
+    lib.lbm_time.restype = ctypes.c_longlong
+    lib.lbm_last_error.argtypes = [vp]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_free.argtypes = [vp]
+    lib.lbm_free.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in include/lbm.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M)))
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _check(status: int, h=None):
+    if status != LBM_OK:
+        msg = _lib.lbm_last_error(h).decode(errors="replace")
+        raise LbmError(status, msg)
+
+
+# ------------------------------------------------------------------------------------------
+# Same-name wrappers of the C entry points.
+
+def lbm_default_params(**overrides) -> lbm_params:
+    p = lbm_params()
+    _lib.lbm_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "prec" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def lbm_state_bytes(p: lbm_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_lib.lbm_state_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_init(p: lbm_params, phi0, ux0=None, uy0=None, rho0=None, device_buffer: int = 0,
+             buffer_bytes: int = 0, stream: int = 0) -> int:
+    n = p.nx * p.ny
+    arrs = [_f64(phi0, n), _f64(ux0, n), _f64(uy0, n), _f64(rho0, n)]
+    h = ctypes.c_void_p()
+    st = _lib.lbm_init(ctypes.byref(p), *(_dptr(a) for a in arrs), ctypes.c_void_p(device_buffer or None),
+                       buffer_bytes, ctypes.c_void_p(stream or None), ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def lbm_step(h: int, n: int) -> None:
+    _check(_lib.lbm_step(h, int(n)), h)
+
+
+def lbm_fields(h: int, rho=None, ux=None, uy=None, phi=None) -> int:
+    """Fill the given float64 arrays; returns the status (NONFINITE is returned, not raised)."""
+    st = _lib.lbm_fields(h, _dptr(rho), _dptr(ux), _dptr(uy), _dptr(phi))
+    if st not in (LBM_OK, LBM_ERR_NONFINITE):
+        _check(st, h)
+    return st
+
+
+def lbm_conservation(h: int):
+    sp, sr = ctypes.c_double(), ctypes.c_double()
+    mom = (ctypes.c_double * 2)()
+    _check(_lib.lbm_conservation(h, ctypes.byref(sp), ctypes.byref(sr), mom), h)
+    return sp.value, sr.value, mom[0], mom[1]
+
+
+def lbm_get_populations(h: int, f, g) -> None:
+    _check(_lib.lbm_get_populations(h, _dptr(f), _dptr(g)), h)
+
+
+def lbm_set_populations(h: int, f, g) -> None:
+    _check(_lib.lbm_set_populations(h, _dptr(f), _dptr(g)), h)
+
+
+def lbm_check(h: int) -> int:
+    return _lib.lbm_check(h)
+
+
+def lbm_time(h: int) -> int:
+    return _lib.lbm_time(h)
+
+
+def lbm_last_error(h: int | None = None) -> str:
+    return _lib.lbm_last_error(h).decode(errors="replace")
+
+
+def lbm_free(h: int) -> None:
+    _lib.lbm_free(h)
+
+
+# ------------------------------------------------------------------------------------------
+# Convenience object: torch owns the device buffer and the stream.
+
+class Lattice:
+    """One lattice on the current CUDA device.  ``params`` are lbm_params field names."""
+
+    def __init__(self, phi0, ux0=None, uy0=None, rho0=None, stream=None, **params):
+        import torch
+        phi0 = np.asarray(phi0, dtype=np.float64)
+        self.ny, self.nx = phi0.shape
+        self.params = lbm_default_params(nx=self.nx, ny=self.ny, **params)
+        nbytes = lbm_state_bytes(self.params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=self.stream.device)
+        self.h = lbm_init(self.params, phi0, ux0, uy0, rho0, self.buffer.data_ptr(), nbytes,
+                          self.stream.cuda_stream)
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n)
+
+    def fields(self):
+        """(rho, ux, uy, phi) as (ny, nx) float64 arrays; raises LbmError on a non-finite state."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        st = lbm_fields(self.h, *out)
+        if st == LBM_ERR_NONFINITE:
+            raise LbmError(st, lbm_last_error(self.h))
+        return tuple(out)
+
+    def conservation(self):
+        return lbm_conservation(self.h)
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((9, self.ny, self.nx))
+        lbm_get_populations(self.h, f, g)
+        return f, g
+
+    def set_populations(self, f, g):
+        lbm_set_populations(self.h, np.ascontiguousarray(f, dtype=np.float64),
+                            np.ascontiguousarray(g, dtype=np.float64))
+
+    @property
+    def time(self) -> int:
+        return lbm_time(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,70 @@
+"""The C ABI library loads without a GPU, exports every function include/lbm.h declares, and
+rejects invalid parameters before touching the device."""
+import ctypes
+import re
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm as mod
+    return mod
+
+
+def test_exports_every_declared_symbol(lbm):
+    names = lbm.declared_functions()
+    assert {"lbm_init", "lbm_step", "lbm_fields", "lbm_free", "lbm_conservation",
+            "lbm_get_populations", "lbm_set_populations", "lbm_last_error"} <= set(names)
+    lib = ctypes.CDLL(lbm._build.LIB)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_header_declares_what_the_binding_wraps(lbm):
+    for n in lbm.declared_functions():
+        assert hasattr(lbm, n), f"binding lacks {n}"
+
+
+def test_defaults_follow_the_paper(lbm):
+    p = lbm.lbm_default_params()
+    assert (p.M, p.Gamma, p.gamma, p.a) == (0.1, 1.0, 0.04, 0.04)
+    assert p.tau_l == pytest.approx(0.8) and p.omega3 == 1.0
+    assert p.prec == lbm.LBM_FP32 and p.collision == lbm.LBM_COLLIDE_CM
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=2), dict(ny=0), dict(tau_l=0.5), dict(tau_g=0.2), dict(M=0.0), dict(Gamma=-1.0),
+    dict(gamma=-0.1), dict(omega3=2.0), dict(prec=7), dict(bc=3), dict(visc=5), dict(k8_form=2),
+    dict(collision=9), dict(u_top=float("nan")), dict(nx=70000, ny=70000)])
+def test_invalid_parameters_rejected(lbm, bad):
+    kw = dict(nx=16, ny=16)
+    kw.update(bad)
+    p = lbm.lbm_default_params(**kw)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_state_bytes(p)
+    assert ei.value.status == lbm.LBM_ERR_PARAM
+    assert lbm.lbm_last_error(None)
+
+
+def test_state_bytes_scale_with_precision(lbm):
+    sizes = {}
+    for name, prec in lbm.PRECISIONS.items():
+        sizes[name] = lbm.lbm_state_bytes(lbm.lbm_default_params(nx=256, ny=256, prec=prec))
+    N = 256 * 256
+    assert sizes["fp64"] >= 2 * 18 * 8 * N
+    assert sizes["fp32"] >= 2 * 18 * 4 * N
+    assert sizes["fp16s"] >= 2 * (17 * 2 + 4) * N
+    assert sizes["fp16s"] < sizes["fp32"] < sizes["fp64"]
+
+
+def test_init_rejects_nonfinite_and_missing_input(lbm):
+    import numpy as np
+    p = lbm.lbm_default_params(nx=8, ny=8)
+    phi = np.zeros(64)
+    phi[5] = np.nan
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_init(p, phi)
+    assert ei.value.status == lbm.LBM_ERR_PARAM and "non-finite" in str(ei.value)

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated per precision):
+  FP64 storage: max |d| / max |oracle| <= 1e-12 for phi, rho and every population, and
+                |d u| <= 1e-12 in lattice units, after up to 1000 steps.
+  FP32 storage: phi within 1e-5 of max |phi| after 1000 steps (spinodal 256^2); u within
+                2e-6 lattice units.
+  16-bit storage (FP16 / BF16 deviations, FP32 g_0): phi within 2e-3 after 1000 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _pair import abs_err, oracle_kwargs, rel_err
+from paper_1803_11345_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm as mod
+    return mod
+
+
+def run_pair(lbm, orc, phi0, steps, ux0=None, uy0=None, **kw):
+    lat = lbm.Lattice(phi0, ux0, uy0, **kw)
+    o = orc.Oracle(phi0, ux0, uy0, **oracle_kwargs(kw))
+    lat.step(steps)
+    o.step(steps)
+    return lat, o
+
+
+def assert_fp64_parity(lat, o, tol=1e-12):
+    rg, uxg, uyg, pg = lat.fields()
+    ro, uxo, uyo, po = o.fields()
+    assert rel_err(pg, po) <= tol, rel_err(pg, po)
+    assert rel_err(rg, ro) <= tol, rel_err(rg, ro)
+    assert abs_err(uxg, uxo) <= tol and abs_err(uyg, uyo) <= tol, (abs_err(uxg, uxo), abs_err(uyg, uyo))
+    fg, gg = lat.populations()
+    fo, go = o.populations()
+    assert rel_err(fg, fo) <= tol, rel_err(fg, fo)
+    assert rel_err(gg, go) <= tol, rel_err(gg, go)
+
+
+# -------------------------------------------------------------------------------------------
+# FP64: the kernel computes what the oracle computes.
+
+def test_laplace_droplet_fp64_1000_steps(lbm, orc):
+    """64x64 periodic droplet R = 16, tanh profile, a = 0.04, gamma = 0.02, M = 0.1, tau = 1."""
+    phi0 = W.droplet(64, 64, 16, gamma=0.02, a=0.04)
+    kw = dict(prec=lbm.LBM_FP64, tau_l=1.0, tau_g=1.0, gamma=0.02, a=0.04, M=0.1)
+    lat, o = run_pair(lbm, orc, phi0, 1000, **kw)
+    assert_fp64_parity(lat, o)
+
+
+def test_spinodal_fp64_viscosity_ratio(lbm, orc):
+    """256x256 spinodal, phi ~ U[-0.05, 0.05], viscosity ratio 10 interpolated linearly in tau."""
+    phi0 = W.spinodal(256, 256, seed=11)
+    kw = dict(prec=lbm.LBM_FP64, tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.01),
+              visc=lbm.LBM_TAU_LINEAR)
+    lat, o = run_pair(lbm, orc, phi0, 300, **kw)
+    assert_fp64_parity(lat, o)
+
+
+@pytest.mark.parametrize("nx,ny", [(67, 45), (3, 3), (130, 5), (5, 131)])
+def test_ragged_and_minimal_periodic_fp64(lbm, orc, nx, ny):
+    """Sizes that are not multiples of the tile, and the smallest lattice the stencils allow."""
+    phi0 = W.droplet(nx, ny, min(nx, ny) / 3, gamma=0.04, a=0.04)
+    rng = np.random.default_rng(nx * 1000 + ny)
+    ux0 = 0.01 * rng.standard_normal((ny, nx))
+    uy0 = 0.01 * rng.standard_normal((ny, nx))
+    kw = dict(prec=lbm.LBM_FP64, tau_l=0.9, tau_g=0.55, omega3=1.3)
+    lat, o = run_pair(lbm, orc, phi0, 120, ux0, uy0, **kw)
+    assert_fp64_parity(lat, o)
+
+
+@pytest.mark.parametrize("nx,ny", [(96, 40), (3, 3), (33, 7)])
+def test_moving_walls_fp64(lbm, orc, nx, ny):
+    """Sheared droplet between walls moving at +-0.01 (halfway bounce-back, mirrored phi)."""
+    phi0 = W.droplet(nx, ny, min(nx, ny) / 3, gamma=0.04, a=0.04)
+    kw = dict(prec=lbm.LBM_FP64, tau_l=0.8, tau_g=0.53, bc=lbm.LBM_WALLS_Y, u_top=0.01, u_bottom=-0.01)
+    lat, o = run_pair(lbm, orc, phi0, 500, **kw)
+    assert_fp64_parity(lat, o)
+
+
+@pytest.mark.parametrize("variant", [
+    dict(collision=1), dict(k8_form=1), dict(omega3=1.6), dict(visc=1, tau_l=1.4, tau_g=0.51),
+    dict(Gamma=2.0, M=0.05)])
+def test_variants_fp64(lbm, orc, variant):
+    """BGK baseline collision (Eq. 6), printed k8 form, bulk rate, tau-linear viscosity, Gamma."""
+    phi0 = W.droplet(48, 40, 12, gamma=0.04, a=0.04)
+    kw = dict(prec=lbm.LBM_FP64, tau_l=0.9, tau_g=0.6)
+    kw.update(variant)
+    lat, o = run_pair(lbm, orc, phi0, 200, **kw)
+    assert_fp64_parity(lat, o)
+
+
+def test_zero_steps_and_initial_state(lbm, orc):
+    """n = 0 leaves the initial (t = 0) state, which equals the oracle's initialisation."""
+    phi0 = W.spinodal(40, 24, seed=3)
+    lat, o = run_pair(lbm, orc, phi0, 0, prec=lbm.LBM_FP64)
+    assert lat.time == 0
+    assert_fp64_parity(lat, o)
+
+
+def test_conservation_sums_fp64(lbm, orc):
+    """GPU FP64 totals equal the oracle's compensated sums; sum phi and sum rho are conserved."""
+    phi0 = W.spinodal(128, 96, seed=4)
+    lat, o = run_pair(lbm, orc, phi0, 0, prec=lbm.LBM_FP64, tau_l=0.8, tau_g=0.55)
+    s0 = lat.conservation()
+    so = o.sums()
+    for a, b in zip(s0, so):
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(b))
+    lat.step(400)
+    s1 = lat.conservation()
+    N = 128 * 96
+    assert abs(s1[0] - s0[0]) <= 1e-12 * N
+    assert abs(s1[1] - s0[1]) <= 1e-12 * N
+    assert abs(s1[2] - s0[2]) <= 1e-12 * N and abs(s1[3] - s0[3]) <= 1e-12 * N
+
+
+def test_checkpoint_round_trip(lbm, orc):
+    """get_populations / set_populations resume bit-exactly (FP64)."""
+    phi0 = W.droplet(50, 30, 9, gamma=0.04, a=0.04)
+    a = lbm.Lattice(phi0, prec=lbm.LBM_FP64)
+    a.step(37)
+    f, g = a.populations()
+    b = lbm.Lattice(np.zeros_like(phi0), prec=lbm.LBM_FP64)
+    b.set_populations(f, g)
+    a.step(25)
+    b.step(25)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_nonfinite_state_is_reported(lbm):
+    """A NaN planted on the host through set_populations is flagged by the next step; the
+    handle stays usable.  (No device fault is involved.)"""
+    phi0 = W.droplet(32, 32, 8, gamma=0.04, a=0.04)
+    lat = lbm.Lattice(phi0, prec=lbm.LBM_FP32)
+    f, g = lat.populations()
+    g[0, 10, 10] = np.nan
+    lat.set_populations(f, g)
+    lat.step(2)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.fields()
+    assert ei.value.status == lbm.LBM_ERR_NONFINITE
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK  # flag cleared by the report
+
+
+# -------------------------------------------------------------------------------------------
+# Reduced precision against the FP64 oracle.
+
+def test_spinodal_fp32_1000_steps(lbm, orc):
+    phi0 = W.spinodal(256, 256, seed=12)
+    kw = dict(tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.01), visc=lbm.LBM_TAU_LINEAR)
+    lat, o = run_pair(lbm, orc, phi0, 1000, prec=lbm.LBM_FP32, **kw)
+    rg, uxg, uyg, pg = lat.fields()
+    ro, uxo, uyo, po = o.fields()
+    assert rel_err(pg, po) <= 1e-5, rel_err(pg, po)
+    assert abs_err(uxg, uxo) <= 2e-6 and abs_err(uyg, uyo) <= 2e-6
+    assert rel_err(rg, ro) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_sheared_droplet_16bit_storage(lbm, orc, prec):
+    """16-bit deviation storage keeps phi within 2e-3 of the FP64 oracle over 1000 steps."""
+    phi0 = W.droplet(128, 64, 16, gamma=0.04, a=0.04)
+    kw = dict(tau_l=orc.tau_from_nu(0.2), tau_g=orc.tau_from_nu(0.02), bc=lbm.LBM_WALLS_Y,
+              u_top=0.01, u_bottom=-0.01)
+    lat, o = run_pair(lbm, orc, phi0, 1000, prec=lbm.PRECISIONS[prec], **kw)
+    _, _, _, pg = lat.fields()
+    _, _, _, po = o.fields()
+    assert abs_err(pg, po) <= 2e-3, abs_err(pg, po)
+
+
+# -------------------------------------------------------------------------------------------
+# Full size, in the benchmark's launch configuration: sampled nodes, checked one by one.
+
+def test_full_size_4096_fp32_sampled_nodes(lbm, orc):
+    """4096^2 spinodal FP32 (the throughput workload, default tile): after 3 steps, the next
+    step of 64 sampled nodes (edges, corners, tile seams, random) matches the oracle's
+    single-node update of the same state within FP32 rounding; sum phi and sum rho are
+    conserved to FP32 accumulation bounds."""
+    n = 4096
+    phi0 = W.spinodal(n, n, seed=2024)
+    kw = dict(tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.01), visc=lbm.LBM_TAU_LINEAR)
+    lat = lbm.Lattice(phi0, prec=lbm.LBM_FP32, **kw)
+    s0 = lat.conservation()
+    lat.step(3)
+    f0, g0 = lat.populations()
+    lat.step(1)
+    f1, g1 = lat.populations()
+    s1 = lat.conservation()
+    P = orc.make_params(n, n, **oracle_kwargs(kw))
+    rng = np.random.default_rng(7)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (63, 5), (64, 5), (127, 200), (128, 201)]
+    pts += [tuple(v) for v in rng.integers(0, n, size=(56, 2))]
+    for x, y in pts:
+        fo, go = orc.node_update(P, f0, g0, x, y)
+        assert abs_err(f1[:, y, x], fo) <= 2e-7, (x, y)
+        assert abs_err(g1[:, y, x], go) <= 2e-7, (x, y)
+    assert abs(s1[0] - s0[0]) <= 1e-7 * n * n * 0.05 + 1e-3
+    assert abs(s1[1] - s0[1]) <= 1e-7 * n * n

@@ -456,3 +456,23 @@ def test_laplace_law_slope(orc):
     slope = (d8 - d12) / (1 / 8 - 1 / 12)
     sigma = math.sqrt(8 * 0.04 * 0.04 / 9)
     assert abs(slope / sigma - 1) < 0.06
+
+
+def test_node_update_matches_full_step(orc):
+    """The single-node update (gathered streaming) equals one full-lattice step (pushed
+    streaming) at every node, periodic and with moving walls."""
+    for walls in (0, 1):
+        nx, ny = 9, 7
+        phi = _smooth_field(nx, ny, 20 + walls)
+        kw = dict(tau_l=0.9, tau_g=0.6, walls=walls, u_top=0.03, u_bottom=-0.02, omega3=1.3)
+        o = orc.Oracle(phi, **kw)
+        o.step(3)
+        f0, g0 = o.populations()
+        o.step(1)
+        f1, g1 = o.populations()
+        P = orc.make_params(nx, ny, **kw)
+        for y in range(ny):
+            for x in range(nx):
+                fo, go = orc.node_update(P, f0, g0, x, y)
+                np.testing.assert_allclose(fo, f1[:, y, x], rtol=0, atol=1e-15)
+                np.testing.assert_allclose(go, g1[:, y, x], rtol=0, atol=1e-15)

@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused hybrid central-moment / BGK lattice Boltzmann step.
+
+Workload (default): spinodal decomposition on a 4096 x 4096 periodic D2Q9 lattice, phi i.i.d.
+uniform in [-0.05, 0.05] (SplitMix64 seed 2024), u = 0, rho = 1, viscosity ratio 1:10
+(nu_l = 0.1, nu_g = 0.01, tau interpolated linearly in phi), a = gamma = 0.04, M = 0.1,
+Gamma = 1, FP32 storage and arithmetic.  One step = one launch of the fused kernel over all
+nodes (both population sets).  Metric: MLUPS counting one update of f and g per node.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--n 4096] [--prec fp32] [--no-e2e] [--no-cpu-baseline]
+
+Under torchrun (N > 1) every rank runs an independent replica of the lattice on its own GPU
+(no data-path collective; weak scaling); the step time is the max over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (f+g) and % HBM roofline on 1 GB300; surrogate/16-bit/batch speedup at φ err"
+BYTES_PER_NODE = {"fp64": 288, "fp32": 144, "fp16s": 76, "bf16s": 76}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f32 (16-bit storage)", "bf16s": "f32 (bf16 storage)"}
+PHYS = dict(nu_l=0.1, nu_g=0.01, a=0.04, gamma=0.04, M=0.1, Gamma=1.0)
+SEED = 2024
+
+
+def tau(nu):
+    return nu * 3.0 + 0.5
+
+
+def workload_params():
+    return dict(tau_l=tau(PHYS["nu_l"]), tau_g=tau(PHYS["nu_g"]), a=PHYS["a"], gamma=PHYS["gamma"],
+                M=PHYS["M"], Gamma=PHYS["Gamma"])
+
+
+# ------------------------------------------------------------------------------------------
+# Environment helpers.
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1803_11345_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec: str, n: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{prec}_spinodal.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("bench-traffic:"):
+                for kv in line.split(":", 1)[1].split():
+                    k, v = kv.split("=")
+                    vals[k] = v
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        per_node = float(vals["dram_bytes_per_node"])
+    except (KeyError, ValueError):
+        return None
+    return per_node * n * n
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle leg (bounded sample).
+
+def time_oracle(budget_s: float, n_side: int, max_steps: int = 10**9):
+    """Run the FP64 oracle on an n_side^2 sample of the workload for up to budget_s seconds
+    (whole steps).  Returns (MLUPS, steps, seconds, threads)."""
+    import oracle
+    from paper_1803_11345_gb300 import workloads as W
+    oracle.build()
+    threads = oracle.set_threads(0)
+    phi0 = W.spinodal(n_side, n_side, seed=SEED)
+    o = oracle.Oracle(phi0, visc_interp=1, **workload_params())
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    o.close()
+    return n_side * n_side * steps / dt / 1e6, steps, dt, threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    # Each timed step is one oracle time step on a sample lattice sized so that the whole
+    # K-step run takes about 30 s of host time.
+    import oracle
+    from paper_1803_11345_gb300 import workloads as W
+    oracle.build()
+    threads = oracle.set_threads(0)
+    probe = 64
+    o = oracle.Oracle(W.spinodal(probe, probe, seed=SEED), visc_interp=1, **workload_params())
+    t0 = time.perf_counter()
+    o.step(3)
+    per_node = (time.perf_counter() - t0) / (3 * probe * probe)
+    o.close()
+    target = 30.0 / max(1, args.steps + args.warmup)
+    side = int(max(16, min(args.n, math.sqrt(target / per_node))))
+    phi0 = W.spinodal(side, side, seed=SEED)
+    o = oracle.Oracle(phi0, visc_interp=1, **workload_params())
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    mlups = side * side * args.steps / dt / 1e6
+    sample = f"{side}x{side} periodic sample of the spinodal workload (same parameters), FP64"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args):
+    return {"workload": f"spinodal decomposition {args.n}x{args.n} periodic, viscosity ratio 1:10 "
+                        f"(tau linear in phi), {args.prec} storage",
+            "nx": args.n, "ny": args.n, "precision": args.prec, "seed": SEED,
+            "nu_l": PHYS["nu_l"], "nu_g": PHYS["nu_g"], "a": PHYS["a"], "gamma": PHYS["gamma"],
+            "M": PHYS["M"], "collision": "central moments (f) + BGK (g)",
+            "l2": "inputs larger than L2 (state >= 1 GB per buffer at 4096^2): no flush",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU leg.
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_11345_gb300 import build as B
+    ws, rank, local = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_1803_11345_gb300 import lbm
+    from paper_1803_11345_gb300 import workloads as W
+
+    n = args.n
+    phi0 = W.spinodal(n, n, seed=SEED + rank)
+    params = dict(prec=lbm.PRECISIONS[args.prec], visc=lbm.LBM_TAU_LINEAR, **workload_params())
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(phi0, stream=stream, **params)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    nodes = n * n
+    mlups = ws * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    ms_step = ms_max / args.steps
+
+    # Roofline of the dominant (only) kernel in the timed region: algorithmic bytes per launch
+    # / average launch duration (CUDA events on the launching stream).
+    peak, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.prec]
+    achieved = bpn * nodes / (ms / args.steps * 1e-3) / 1e9
+    traffic = ncu_traffic(args.prec, n)
+
+    # Parity spot check on this run (cheap): sum phi is conserved by the scheme.
+    sphi, srho, _, _ = lat.conservation()
+    lat.close()
+    del lat
+    torch.cuda.synchronize()
+
+    # End-to-end through the C ABI with host buffers: pinned phi0 in, K steps, fields out.
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(phi0.reshape(-1)).pin_memory()
+        host_phi = pinned.numpy()
+        out = [torch.empty(nodes, dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+        p = lbm.lbm_default_params(nx=n, ny=n, **params)
+        nbytes = lbm.lbm_state_bytes(p)
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        h = lbm.lbm_init(p, host_phi, None, None, None, buf.data_ptr(), nbytes, stream.cuda_stream)
+        lbm.lbm_step(h, args.steps)
+        lbm.lbm_fields(h, *out)
+        t1 = time.perf_counter()
+        lbm.lbm_free(h)
+        dt = t1 - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": ws * nodes * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * nodes / args.steps,
+               "d2h_bytes_per_step": 4 * 8 * nodes / args.steps,
+               "what": "lbm_init from pinned host phi0 (H2D) + lbm_step(K) + lbm_fields to pinned "
+                       "host (D2H), wall clock; bytes amortised over the K steps"}
+        del buf
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            c_mlups, c_steps, c_dt, c_thr = time_oracle(args.cpu_budget, 128)
+            cpu = {"value": c_mlups, "unit": "MLUPS", "cores": c_thr, "kind": "oracle",
+                   "sample": f"128x128 periodic sample of the spinodal workload, {c_steps} steps "
+                             f"in {c_dt:.1f} s, FP64"}
+        except Exception as exc:  # report, do not hide
+            cpu = {"value": None, "unit": "MLUPS", "cores": None, "kind": "oracle",
+                   "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": config_dict(args),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_node": bpn, "kernel": "k_step"},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+            "check": {"sum_phi": sphi, "sum_rho": srho},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--n", type=int, default=4096, help="lattice side (profiling uses smaller)")
+    ap.add_argument("--prec", choices=list(BYTES_PER_NODE), default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -151,6 +151,23 @@ LBM_API int lbm_set_populations(lbm_lattice* h, const double* f, const double* g
  * phi (LBM_ERR_NONFINITE) or a CUDA error occurred (LBM_ERR_CUDA); clears the flag. */
 LBM_API int lbm_check(lbm_lattice* h);
 
+/* Fused-step kernel choice.  AUTO picks the staged kernel when the lattice allows it, else the
+ * generic one.  GENERIC: populations pulled straight from global memory.  STAGED: whole rows
+ * staged in shared memory by bulk copies; needs nx to be a multiple of 16 bytes / stored element
+ * size (2 columns FP64, 4 FP32, 8 16-bit). */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_GENERIC = 1, LBM_KERNEL_STAGED = 2 } lbm_kernel;
+
+/* Override the kernel and its tile: bx x by threads per CTA (0, 0 = default for the variant),
+ * depth = bands of prefetch of the staged kernel (0 = default), rows = lattice rows per CTA
+ * (0 = sized so the grid fills the GPU in one wave).  Affects later lbm_step calls only; results
+ * do not depend on the choice beyond rounding order (none for FP64/FP32 here: every variant
+ * performs the same operations per node).  LBM_ERR_PARAM for a combination without a compiled
+ * kernel or a lattice the variant cannot serve. */
+LBM_API int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int rows);
+
+/* The kernel and tile lbm_step uses now (variant is GENERIC or STAGED); NULL pointers skipped. */
+LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows);
+
 /* Time level reached (number of completed steps since lbm_init). */
 LBM_API long long lbm_time(const lbm_lattice* h);
 

@@ -331,6 +331,53 @@ int lbm_set_populations(lbm_lattice* h, const double* f, const double* g) {
   return LBM_OK;
 }
 
+int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int rows) {
+  if (!h) return LBM_ERR_PARAM;
+  if (variant == LBM_KERNEL_AUTO) {
+    StepTile t = default_tile(h->p.prec, h->geo, h->device);
+    if (rows > 0) t.rows = rows;
+    h->tile = t;
+    return LBM_OK;
+  }
+  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED) || rows < 0 || bx < 0 || by < 0 ||
+      depth < 0) {
+    set_err(h->err, "lbm_set_kernel: invalid arguments");
+    return LBM_ERR_PARAM;
+  }
+  StepTile t;
+  t.staged = variant == LBM_KERNEL_STAGED;
+  t.bx = bx ? bx : (h->p.prec == LBM_FP64 ? 32 : 64);
+  t.by = by ? by : 4;
+  t.depth = depth ? depth : 1;
+  t.rows = 0;
+  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) : tile_supported(h->p.prec, t.bx, t.by);
+  if (!ok) {
+    set_err(h->err, "lbm_set_kernel: no %s kernel for tile %dx%d depth %d on nx = %d",
+            t.staged ? "staged" : "generic", t.bx, t.by, t.depth, h->geo.nx);
+    return LBM_ERR_PARAM;
+  }
+  if (rows > 0) {
+    t.rows = rows;
+  } else {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t) : 0;
+    t.rows = rows_for_wave(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 2));
+  }
+  h->tile = t;
+  return LBM_OK;
+}
+
+int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows) {
+  if (!h) return LBM_ERR_PARAM;
+  if (variant) *variant = h->tile.staged ? LBM_KERNEL_STAGED : LBM_KERNEL_GENERIC;
+  if (bx) *bx = h->tile.bx;
+  if (by) *by = h->tile.by;
+  if (depth) *depth = h->tile.depth;
+  if (rows) *rows = h->tile.rows;
+  return LBM_OK;
+}
+
 long long lbm_time(const lbm_lattice* h) { return h ? h->t : -1; }
 
 const char* lbm_last_error(const lbm_lattice* h) { return h ? h->err : g_init_err; }

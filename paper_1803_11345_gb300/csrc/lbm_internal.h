@@ -17,9 +17,12 @@ struct HostPhys {
   int visc, k8_printed, bgk;
 };
 
-// Tile shape of the fused step: BX columns x BY rows of threads, `rows` lattice rows per CTA.
+// Tile of the fused step: BX columns x BY rows of threads, `rows` lattice rows per CTA.
+// staged = 1 selects the bulk-copy staged kernel (lbm_staged.cu) with `depth` bands of
+// prefetch; staged = 0 the generic kernel (lbm_kernels.cu).
 struct StepTile {
   int bx, by, rows;
+  int staged, depth;
 };
 
 // Fill n doubles with v.
@@ -46,8 +49,18 @@ cudaError_t launch_plane_get(int prec, const HostGeometry& g, const char* src, i
 cudaError_t launch_plane_set(int prec, const HostGeometry& g, char* dst, int p, const double* in,
                              cudaStream_t s);
 
+// Staged kernel: halo width (columns) per precision, whether a lattice/tile can use it, its
+// resident CTAs per SM, and its launcher.
+int staged_halo(int prec);
+bool staged_supported(int prec, const HostGeometry& g, const StepTile& t);
+int staged_blocks_per_sm(int prec, const StepTile& t);
+cudaError_t launch_step_staged(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
+                               const char* src, char* dst, int* flag, cudaStream_t s);
+
 // Default tile for a precision and lattice, sized so the grid fills the GPU in one wave.
 StepTile default_tile(int prec, const HostGeometry& g, int device);
+// Rows per CTA so that the grid is about `ctas` CTAs (one wave).
+int rows_for_wave(const HostGeometry& g, const StepTile& t, int ctas);
 // Whether a tile shape has a compiled kernel.
 bool tile_supported(int prec, int bx, int by);
 

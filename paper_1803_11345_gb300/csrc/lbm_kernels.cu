@@ -409,6 +409,8 @@ bool tile_supported(int prec, int bx, int by) {
 
 StepTile default_tile(int prec, const HostGeometry& g, int device) {
   StepTile t;
+  t.staged = 0;
+  t.depth = 1;
   if (prec == 0) {
     t.bx = 32;
     t.by = 4;
@@ -416,24 +418,38 @@ StepTile default_tile(int prec, const HostGeometry& g, int device) {
     t.bx = 64;
     t.by = 4;
   }
+  StepTile st = t;
+  st.staged = 1;
+  st.bx = prec == 0 ? 32 : 64;
+  st.by = 4;
+  st.depth = 1;
+  if (staged_supported(prec, g, st)) t = st;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (sms <= 0) sms = 152;
   int per_sm = 0;
-  switch (prec) {
-    case 0: per_sm = occupancy<0>(t.bx, t.by); break;
-    case 1: per_sm = occupancy<1>(t.bx, t.by); break;
-    case 2: per_sm = occupancy<2>(t.bx, t.by); break;
-    case 3: per_sm = occupancy<3>(t.bx, t.by); break;
+  if (t.staged) {
+    per_sm = staged_blocks_per_sm(prec, t);
+  } else {
+    switch (prec) {
+      case 0: per_sm = occupancy<0>(t.bx, t.by); break;
+      case 1: per_sm = occupancy<1>(t.bx, t.by); break;
+      case 2: per_sm = occupancy<2>(t.bx, t.by); break;
+      case 3: per_sm = occupancy<3>(t.bx, t.by); break;
+    }
   }
   if (per_sm <= 0) per_sm = 1;
-  // One full wave: gx * gy ~ sms * per_sm CTAs.
+  t.rows = rows_for_wave(g, t, sms * per_sm);
+  return t;
+}
+
+int rows_for_wave(const HostGeometry& g, const StepTile& t, int ctas) {
+  // One full wave: gx * gy ~ ctas CTAs, rows a multiple of BY.
   const int gx = (g.nx + t.bx - 1) / t.bx;
-  int gy = std::max(1, (sms * per_sm) / gx);
+  int gy = std::max(1, ctas / gx);
   int rows = (g.ny + gy - 1) / gy;
   rows = ((rows + t.by - 1) / t.by) * t.by;
-  t.rows = std::max(rows, t.by);
-  return t;
+  return std::max(rows, t.by);
 }
 
 cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, const double* fields,
@@ -452,6 +468,7 @@ cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, cons
 
 cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
                         const char* src, char* dst, int* flag, cudaStream_t s) {
+  if (t.staged) return launch_step_staged(prec, g, p, t, src, dst, flag, s);
   switch (prec) {
     case 0: return step_prec<0>(g, p, t, src, dst, flag, s);
     case 1: return step_prec<1>(g, p, t, src, dst, flag, s);

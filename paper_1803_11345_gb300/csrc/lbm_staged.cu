@@ -1,0 +1,425 @@
+// Staged variant of the fused step: whole rows of all 18 population planes are streamed
+// into shared-memory rings by the bulk-copy (TMA) engine, and every pull (Eqs. 4-5), the
+// phi sums and the Eq. 12 stencils read shared memory.
+//
+// CTA = BX columns x BY thread rows, marching down `rows` lattice rows in bands of BY, in the
+// same order as the generic kernel (lbm_kernels.cu):
+//   step Y:  wait for the rows of this step -> phi of rows Y+BY .. Y+2BY-1 from staged g (kept
+//            in registers for the next step) -> f of rows Y .. Y+BY-1 from staged f ->
+//            __syncthreads -> thread 0 issues the bulk copies of the rows needed one step
+//            later into the slots just freed -> collision of rows Y .. Y+BY-1 -> stores.
+// Staged row v of a set (f or g) holds, for each of its 9 planes, columns
+// [x0 - H, x0 + BX + H) with H = 16 bytes / element size, so every copy is 16-byte aligned;
+// the halo chunks wrap around periodically.  This needs nx to be a multiple of H; other widths
+// use the generic kernel.
+#include <algorithm>
+#include <type_traits>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+#include "lbm_tma.cuh"
+
+namespace lbmch {
+
+// Layout of a staged row and of the state in global memory, per storage precision.
+template <int PREC> struct Stage {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  static constexpr bool kHalf = PREC >= 2;
+  static constexpr int kEs = PREC == 0 ? 8 : (PREC == 1 ? 4 : 2);  // bytes of a packed population
+  static constexpr int H = 16 / kEs;                                   // halo columns per side
+  __host__ __device__ static constexpr int es(bool g, int p) { return (kHalf && g && p == 0) ? 4 : kEs; }
+  // Byte offset of plane p inside a staged row of W columns (16-bit g: the FP32 g_0 plane first).
+  __host__ __device__ static constexpr int soff(bool g, int p, int W) {
+    return (!kHalf || !g) ? p * W * kEs : (p == 0 ? 0 : W * 4 + (p - 1) * W * 2);
+  }
+  __host__ __device__ static constexpr int row_bytes(bool g, int W) { return soff(g, 8, W) + W * es(g, 8); }
+  // Global byte offset of element idx of plane p of set g.
+  __device__ __forceinline__ static long long goff(bool g, int p, long long pl, long long idx) {
+    if (!kHalf) return ((g ? 9 : 0) + p) * pl * kEs + idx * kEs;
+    if (!g) return p * pl * 2 + idx * 2;
+    if (p == 0) return 17 * pl * 2 + idx * 4;
+    return (8 + p) * pl * 2 + idx * 2;
+  }
+  // Population value from a staged row.
+  __device__ __forceinline__ static C sld(const char* row, bool g, int p, int c, int W) {
+    const char* a = row + soff(g, p, W) + c * es(g, p);
+    if constexpr (PREC == 0) return *reinterpret_cast<const double*>(a);
+    else if constexpr (PREC == 1) return *reinterpret_cast<const float*>(a);
+    else {
+      if (g && p == 0) return *reinterpret_cast<const float*>(a);
+      using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
+      const float v = Cvt<Hf>::to(*reinterpret_cast<const Hf*>(a));
+      return g ? v : v + (float)lat_w36(p) * (1.0f / 36.0f);
+    }
+  }
+};
+
+template <int BY, int D> struct Ring {
+  static constexpr int R = (D + 1) * BY + 2;  // rows per ring (f and g alike)
+};
+
+template <int PREC, int BX, int BY, int D>
+size_t staged_smem_bytes() {
+  using S = Stage<PREC>;
+  using C = typename S::C;
+  constexpr int W = BX + 2 * S::H;
+  constexpr int R = Ring<BY, D>::R;
+  size_t b = (size_t)R * S::row_bytes(true, W) + (size_t)R * S::row_bytes(false, W);
+  b += (size_t)(3 * BY + 1) * (BX + 2) * sizeof(C);
+  b = (b + 15) / 16 * 16;
+  b += 2 * R * sizeof(uint64_t) + 16;
+  return b;
+}
+
+// Probes before a wait is declared stuck (each probe suspends for a short hardware window):
+// far beyond any legitimate copy latency, short enough to return control in well under a second.
+constexpr uint32_t kWaitProbes = 1u << 22;
+
+template <int PREC, int BX, int BY, int D>
+__global__ void __launch_bounds__(BX * BY)
+k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
+              const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
+  using S = Stage<PREC>;
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  constexpr int H = S::H;
+  constexpr int W = BX + 2 * H;
+  constexpr int R = Ring<BY, D>::R;
+  constexpr int RBG = S::row_bytes(true, W);
+  constexpr int RBF = S::row_bytes(false, W);
+  constexpr int PHR = 3 * BY + 1;  // phi ring rows (same argument as the generic kernel)
+  constexpr int PHW = BX + 2;
+
+  extern __shared__ __align__(16) char smem[];
+  char* gring = smem;
+  char* fring = gring + R * RBG;
+  C* sphi = reinterpret_cast<C*>(fring + R * RBF);
+  size_t boff = (size_t)R * RBG + (size_t)R * RBF + sizeof(C) * PHR * PHW;
+  boff = (boff + 15) / 16 * 16;
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + boff);
+  uint64_t* fbar = gbar + R;
+  int* abort_flag = reinterpret_cast<int*>(fbar + R);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool leader = tx == 0 && ty == 0;
+  const int x0 = blockIdx.x * BX;
+  const int y0 = blockIdx.y * rows;
+  const int y1 = min(y0 + rows, geo.ny);
+  const int xv = min(BX, geo.nx - x0);
+  const bool colv = tx < xv;
+  const int gvb = y0 - 2, fvb = y0 - 1;  // first staged g / f row
+  const int g_last = y1 + 1, f_last = y1;
+
+  if (leader) {
+    for (int k = 0; k < R; ++k) {
+      mbar_init(&gbar[k], 1);
+      mbar_init(&fbar[k], 1);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto phys_row = [&](int v) -> int {
+    if (v < 0) return geo.walls ? 0 : v + geo.ny;
+    if (v >= geo.ny) return geo.walls ? geo.ny - 1 : v - geo.ny;
+    return v;
+  };
+
+  // Thread 0: stage row v of set g (true) or f (false).
+  int g_next = gvb, f_next = fvb;
+  auto issue_row = [&](bool g, int v) {
+    const int k = v - (g ? gvb : fvb);
+    char* drow = (g ? gring + (k % R) * RBG : fring + (k % R) * RBF);
+    uint64_t* bar = g ? &gbar[k % R] : &fbar[k % R];
+    const long long rowidx = (long long)phys_row(v) * geo.pitch;
+    const bool interior = x0 > 0 && x0 + xv < geo.nx;
+    const int xl = (x0 == 0) ? geo.nx - H : x0 - H;
+    const int xr = (x0 + xv == geo.nx) ? 0 : x0 + xv;
+    uint32_t total = 0;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) total += (uint32_t)((xv + 2 * H) * S::es(g, p));
+    mbar_arrive_expect_tx(bar, total);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int e = S::es(g, p);
+      char* d = drow + S::soff(g, p, W);
+      if (interior) {
+        bulk_g2s(d, src + S::goff(g, p, geo.plane, rowidx + x0 - H), (uint32_t)((xv + 2 * H) * e), bar);
+      } else {
+        bulk_g2s(d, src + S::goff(g, p, geo.plane, rowidx + xl), (uint32_t)(H * e), bar);
+        bulk_g2s(d + H * e, src + S::goff(g, p, geo.plane, rowidx + x0), (uint32_t)(xv * e), bar);
+        bulk_g2s(d + (H + xv) * e, src + S::goff(g, p, geo.plane, rowidx + xr), (uint32_t)(H * e), bar);
+      }
+    }
+  };
+  auto issue_upto = [&](int g_target, int f_target) {
+    g_target = min(g_target, g_last);
+    f_target = min(f_target, f_last);
+    while (g_next <= g_target) issue_row(true, g_next++);
+    while (f_next <= f_target) issue_row(false, f_next++);
+  };
+  // Every thread waits for a staged row before reading it.
+  bool stuck = false;
+  auto wait_row = [&](bool g, int v) {
+    const int k = v - (g ? gvb : fvb);
+    uint64_t* bar = g ? &gbar[k % R] : &fbar[k % R];
+    if (!mbar_wait_bounded(bar, (uint32_t)((k / R) & 1), kWaitProbes)) stuck = true;
+  };
+  auto grow = [&](int v) -> const char* { return gring + ((v - gvb) % R) * RBG; };
+  auto frow = [&](int v) -> const char* { return fring + ((v - fvb) % R) * RBF; };
+
+  // Pull of the populations arriving at node (column c of the staged rows, virtual row v) from
+  // the staged rows; same rule as pull() in lbm_device.cuh.
+  auto pull_s = [&](bool g, int c, int v, C out[9]) {
+    const int y = phys_row(v);
+    const bool bot = geo.walls && y == 0;
+    const bool top = geo.walls && y == geo.ny - 1;
+    // For the wall mirror rows (v = -1 or ny with walls) the node is the mirrored physical row,
+    // whose staged copy is the neighbouring virtual row.
+    const int vv = (geo.walls && v < 0) ? 0 : ((geo.walls && v >= geo.ny) ? geo.ny - 1 : v);
+    const char* r0 = g ? grow(vv) : frow(vv);
+    if (!bot && !top) {
+      const char* rm = g ? grow(vv - 1) : frow(vv - 1);
+      const char* rp = g ? grow(vv + 1) : frow(vv + 1);
+      out[0] = S::sld(r0, g, 0, c, W);
+      out[1] = S::sld(r0, g, 1, c - 1, W);
+      out[2] = S::sld(rm, g, 2, c, W);
+      out[3] = S::sld(r0, g, 3, c + 1, W);
+      out[4] = S::sld(rp, g, 4, c, W);
+      out[5] = S::sld(rm, g, 5, c - 1, W);
+      out[6] = S::sld(rm, g, 6, c + 1, W);
+      out[7] = S::sld(rp, g, 7, c + 1, W);
+      out[8] = S::sld(rp, g, 8, c - 1, W);
+      return;
+    }
+    C own[9];
+    C s = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      own[i] = S::sld(r0, g, i, c, W);
+      s += own[i];
+    }
+    out[0] = own[0];
+    out[1] = S::sld(r0, g, 1, c - 1, W);
+    out[3] = S::sld(r0, g, 3, c + 1, W);
+    const C k6 = C(6) * s / C(36);
+    if (bot) {
+      const char* rp = g ? grow(vv + 1) : frow(vv + 1);
+      out[2] = own[4];
+      out[5] = own[7] + k6 * ph.u_bottom;
+      out[6] = own[8] - k6 * ph.u_bottom;
+      out[4] = S::sld(rp, g, 4, c, W);
+      out[7] = S::sld(rp, g, 7, c + 1, W);
+      out[8] = S::sld(rp, g, 8, c - 1, W);
+    } else {
+      const char* rm = g ? grow(vv - 1) : frow(vv - 1);
+      out[4] = own[2];
+      out[7] = own[5] - k6 * ph.u_top;
+      out[8] = own[6] + k6 * ph.u_top;
+      out[2] = S::sld(rm, g, 2, c, W);
+      out[5] = S::sld(rm, g, 5, c - 1, W);
+      out[6] = S::sld(rm, g, 6, c + 1, W);
+    }
+  };
+  auto sum9 = [](const C v[9]) -> C {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+  };
+  auto pslot = [&](int r) -> int { return (r - (y0 - 1)) % PHR; };
+  auto phi_row = [&](int v, C gkeep[9]) {
+    C gt[9];
+    const int sl = pslot(v);
+    if (colv) {
+      pull_s(true, tx + H, v, gkeep);
+      sphi[sl * PHW + tx + 1] = sum9(gkeep);
+    }
+    if (tx == 0) {
+      pull_s(true, H - 1, v, gt);
+      sphi[sl * PHW + 0] = sum9(gt);
+    }
+    if (tx == BX - 1) {
+      pull_s(true, H + xv, v, gt);
+      sphi[sl * PHW + xv + 1] = sum9(gt);
+    }
+  };
+
+  // Prologue: stage the first rows, then phi of rows y0-1 .. y0+BY-1.
+  if (leader) issue_upto(gvb + R - 1, fvb + R - 1);
+  for (int v = gvb; v <= min(y0 + BY, g_last); ++v) wait_row(true, v);
+  C gcur[9], gnxt[9];
+  {
+    const int r = y0 + ty;
+    if (r <= y1) phi_row(r, gcur);
+    if (ty == 0) {
+      C gt[9];
+      phi_row(y0 - 1, gt);
+    }
+  }
+  // The prologue rows and the first step's rows span 2BY+3 > R rows: refill once the prologue
+  // has read its rows (everything below g row y0+BY-1 is free).
+  __syncthreads();
+  if (leader) issue_upto(y0 + BY - 1 + R - 1, fvb + R - 1);
+
+  for (int Y = y0; Y < y1; Y += BY) {
+    // rows of this step: g [Y+BY-1, Y+2BY] for phi, f [Y-1, Y+BY] for the pulls
+    for (int v = max(Y + BY + 1, gvb); v <= min(Y + 2 * BY, g_last); ++v) wait_row(true, v);
+    for (int v = max(Y - 1, fvb); v <= min(Y + BY, f_last); ++v) wait_row(false, v);
+    const int rn = Y + BY + ty;
+    if (rn <= y1) phi_row(rn, gnxt);
+    const int r = Y + ty;
+    const bool act = colv && r < y1;
+    C f[9];
+    if (act) pull_s(false, tx + H, r, f);
+    if (stuck) atomicExch(abort_flag, 1);
+    __syncthreads();
+    if (*abort_flag) {
+      if (leader) {
+        atomicOr(flag, 2);
+        // Let the copies already issued land before the CTA's shared memory is released.
+        for (int v = max(gvb, g_next - R); v < g_next; ++v) wait_row(true, v);
+        for (int v = max(fvb, f_next - R); v < f_next; ++v) wait_row(false, v);
+      }
+      return;
+    }
+    // Everything staged below g row Y+2BY-1 and f row Y+BY-1 has been read: refill.
+    if (leader) issue_upto(Y + 2 * BY - 1 + R - 1, Y + BY - 1 + R - 1);
+    if (act) {
+      C s[3][3];
+      const int sm = pslot(r - 1), s0 = pslot(r), sp = pslot(r + 1);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        s[0][d] = sphi[sm * PHW + tx + d];
+        s[1][d] = sphi[s0 * PHW + tx + d];
+        s[2][d] = sphi[sp * PHW + tx + d];
+      }
+      C dxp, dyp, lap;
+      stencils<C>(s, dxp, dyp, lap);
+      const C phi = s[1][1];
+      const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
+      if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
+      const int idx = r * geo.pitch + x0 + tx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        P::stf(dst, geo.plane, i, idx, f[i]);
+        P::stg(dst, geo.plane, i, idx, gcur[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gcur[i] = gnxt[i];
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// Host side.
+
+namespace {
+
+template <int PREC> Phys<typename Pop<PREC>::C> phys_of(const HostPhys& h) {
+  using C = typename Pop<PREC>::C;
+  Phys<C> p;
+  p.omega_l = (C)h.omega_l;
+  p.omega_g = (C)h.omega_g;
+  p.tau_l = (C)h.tau_l;
+  p.tau_g = (C)h.tau_g;
+  p.omega3 = (C)h.omega3;
+  p.omega_phi = (C)h.omega_phi;
+  p.gamma = (C)h.gamma;
+  p.a = (C)h.a;
+  p.Gamma = (C)h.Gamma;
+  p.u_top = (C)h.u_top;
+  p.u_bottom = (C)h.u_bottom;
+  p.visc = h.visc;
+  p.k8_printed = h.k8_printed;
+  p.bgk = h.bgk;
+  return p;
+}
+
+template <int PREC, int BX, int BY, int D>
+cudaError_t staged_launch(const HostGeometry& g, const HostPhys& p, int rows, const char* src, char* dst,
+                          int* flag, cudaStream_t s) {
+  const size_t smem = staged_smem_bytes<PREC, BX, BY, D>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_staged<PREC, BX, BY, D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  Geometry geo;
+  geo.nx = g.nx;
+  geo.ny = g.ny;
+  geo.pitch = g.pitch;
+  geo.plane = g.plane;
+  geo.walls = g.walls;
+  dim3 blk(BX, BY);
+  dim3 grd((g.nx + BX - 1) / BX, (g.ny + rows - 1) / rows);
+  k_step_staged<PREC, BX, BY, D><<<grd, blk, smem, s>>>(src, dst, geo, phys_of<PREC>(p), rows, flag);
+  return cudaGetLastError();
+}
+
+template <int PREC, int BX, int BY, int D>
+int staged_occupancy() {
+  const size_t smem = staged_smem_bytes<PREC, BX, BY, D>();
+  cudaFuncSetAttribute(k_step_staged<PREC, BX, BY, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_staged<PREC, BX, BY, D>, BX * BY, smem);
+  return nb;
+}
+
+#define LBM_STAGED_TILES(X) X(32, 4, 1) X(32, 8, 1) X(64, 2, 1) X(64, 4, 1) X(64, 4, 2) X(128, 2, 1) X(128, 1, 2)
+
+template <int PREC>
+cudaError_t staged_prec(const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
+                        char* dst, int* flag, cudaStream_t s) {
+#define LBM_CASE(X, Y, Z) \
+  if (t.bx == X && t.by == Y && t.depth == Z) return staged_launch<PREC, X, Y, Z>(g, p, t.rows, src, dst, flag, s);
+  LBM_STAGED_TILES(LBM_CASE)
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int staged_occ_prec(const StepTile& t) {
+#define LBM_CASE(X, Y, Z) \
+  if (t.bx == X && t.by == Y && t.depth == Z) return staged_occupancy<PREC, X, Y, Z>();
+  LBM_STAGED_TILES(LBM_CASE)
+#undef LBM_CASE
+  return 0;
+}
+
+}  // namespace
+
+int staged_halo(int prec) { return prec == 0 ? 2 : (prec == 1 ? 4 : 8); }
+
+bool staged_supported(int prec, const HostGeometry& g, const StepTile& t) {
+  if (g.nx % staged_halo(prec) != 0) return false;
+#define LBM_CASE(X, Y, Z) \
+  if (t.bx == X && t.by == Y && t.depth == Z) return true;
+  LBM_STAGED_TILES(LBM_CASE)
+#undef LBM_CASE
+  return false;
+}
+
+int staged_blocks_per_sm(int prec, const StepTile& t) {
+  switch (prec) {
+    case 0: return staged_occ_prec<0>(t);
+    case 1: return staged_occ_prec<1>(t);
+    case 2: return staged_occ_prec<2>(t);
+    case 3: return staged_occ_prec<3>(t);
+  }
+  return 0;
+}
+
+cudaError_t launch_step_staged(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
+                               const char* src, char* dst, int* flag, cudaStream_t s) {
+  switch (prec) {
+    case 0: return staged_prec<0>(g, p, t, src, dst, flag, s);
+    case 1: return staged_prec<1>(g, p, t, src, dst, flag, s);
+    case 2: return staged_prec<2>(g, p, t, src, dst, flag, s);
+    case 3: return staged_prec<3>(g, p, t, src, dst, flag, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbmch

@@ -22,6 +22,7 @@ LBM_PERIODIC, LBM_WALLS_Y = 0, 1
 LBM_OMEGA_LINEAR, LBM_TAU_LINEAR = 0, 1
 LBM_K8_PROJECTED, LBM_K8_PRINTED = 0, 1
 LBM_COLLIDE_CM, LBM_COLLIDE_BGK = 0, 1
+LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_STAGED = 0, 1, 2
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
@@ -71,6 +72,11 @@ def _load():
     lib.lbm_set_populations.restype = i
     lib.lbm_check.argtypes = [vp]
     lib.lbm_check.restype = i
+    lib.lbm_set_kernel.argtypes = [vp, i, i, i, i, i]
+    lib.lbm_set_kernel.restype = i
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.lbm_get_kernel.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.lbm_get_kernel.restype = i
     lib.lbm_time.argtypes = [vp]
     lib.lbm_time.restype = ctypes.c_longlong
     lib.lbm_last_error.argtypes = [vp]
@@ -172,6 +178,17 @@ def lbm_check(h: int) -> int:
     return _lib.lbm_check(h)
 
 
+def lbm_set_kernel(h: int, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0) -> None:
+    _check(_lib.lbm_set_kernel(h, variant, bx, by, depth, rows), h)
+
+
+def lbm_get_kernel(h: int):
+    """(variant, bx, by, depth, rows) of the fused-step kernel in use."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(_lib.lbm_get_kernel(h, *(ctypes.byref(x) for x in v)), h)
+    return tuple(x.value for x in v)
+
+
 def lbm_time(h: int) -> int:
     return _lib.lbm_time(h)
 
@@ -224,6 +241,13 @@ class Lattice:
     def set_populations(self, f, g):
         lbm_set_populations(self.h, np.ascontiguousarray(f, dtype=np.float64),
                             np.ascontiguousarray(g, dtype=np.float64))
+
+    def set_kernel(self, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0):
+        lbm_set_kernel(self.h, variant, bx, by, depth, rows)
+
+    @property
+    def kernel(self):
+        return lbm_get_kernel(self.h)
 
     @property
     def time(self) -> int:

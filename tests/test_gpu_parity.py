@@ -92,7 +92,7 @@ def test_moving_walls_fp64(lbm, orc, nx, ny):
 
 @pytest.mark.parametrize("variant", [
     dict(collision=1), dict(k8_form=1), dict(omega3=1.6), dict(visc=1, tau_l=1.4, tau_g=0.51),
-    dict(Gamma=2.0, M=0.05)])
+    dict(Gamma=2.0, M=0.2)])
 def test_variants_fp64(lbm, orc, variant):
     """BGK baseline collision (Eq. 6), printed k8 form, bulk rate, tau-linear viscosity, Gamma."""
     phi0 = W.droplet(48, 40, 12, gamma=0.04, a=0.04)

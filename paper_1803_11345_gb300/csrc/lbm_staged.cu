@@ -41,9 +41,11 @@ template <int PREC> struct Stage {
     if (p == 0) return 17 * pl * 2 + idx * 4;
     return (8 + p) * pl * 2 + idx * 2;
   }
-  // Population value from a staged row.
-  __device__ __forceinline__ static C sld(const char* row, bool g, int p, int c, int W) {
-    const char* a = row + soff(g, p, W) + c * es(g, p);
+  // Output staging: plane q = 0..17 (f_0..f_8, g_0..g_8), n elements each, packed in order.
+  __host__ __device__ static constexpr int oes(int q) { return q < 9 ? kEs : es(true, q - 9); }
+  __host__ __device__ static constexpr int ooff(int q, int n) { return q == 0 ? 0 : ooff(q - 1, n) + n * oes(q - 1); }
+  // Population value from a staged row (a points at the element).
+  __device__ __forceinline__ static C sld(const char* a, bool g, int p) {
     if constexpr (PREC == 0) return *reinterpret_cast<const double*>(a);
     else if constexpr (PREC == 1) return *reinterpret_cast<const float*>(a);
     else {
@@ -51,6 +53,17 @@ template <int PREC> struct Stage {
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
       const float v = Cvt<Hf>::to(*reinterpret_cast<const Hf*>(a));
       return g ? v : v + (float)lat_w36(p) * (1.0f / 36.0f);
+    }
+  }
+  // Store a post-collision value of output plane q into the staging buffer.
+  __device__ __forceinline__ static void sst(char* a, int q, C v) {
+    if constexpr (PREC == 0) *reinterpret_cast<double*>(a) = v;
+    else if constexpr (PREC == 1) *reinterpret_cast<float*>(a) = v;
+    else {
+      using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
+      if (q == 9) *reinterpret_cast<float*>(a) = v;
+      else if (q < 9) *reinterpret_cast<Hf*>(a) = Cvt<Hf>::from(v - (float)lat_w36(q) * (1.0f / 36.0f));
+      else *reinterpret_cast<Hf*>(a) = Cvt<Hf>::from(v);
     }
   }
 };
@@ -66,6 +79,7 @@ size_t staged_smem_bytes() {
   constexpr int W = BX + 2 * S::H;
   constexpr int R = Ring<BY, D>::R;
   size_t b = (size_t)R * S::row_bytes(true, W) + (size_t)R * S::row_bytes(false, W);
+  b += (size_t)S::ooff(18, BX * BY);
   b += (size_t)(3 * BY + 1) * (BX + 2) * sizeof(C);
   b = (b + 15) / 16 * 16;
   b += 2 * R * sizeof(uint64_t) + 16;
@@ -81,28 +95,31 @@ __global__ void __launch_bounds__(BX * BY)
 k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
               const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
   using S = Stage<PREC>;
-  using P = Pop<PREC>;
-  using C = typename P::C;
+  using C = typename S::C;
   constexpr int H = S::H;
   constexpr int W = BX + 2 * H;
   constexpr int R = Ring<BY, D>::R;
   constexpr int RBG = S::row_bytes(true, W);
   constexpr int RBF = S::row_bytes(false, W);
+  constexpr int NOUT = BX * BY;    // elements per output plane
   constexpr int PHR = 3 * BY + 1;  // phi ring rows (same argument as the generic kernel)
   constexpr int PHW = BX + 2;
+  constexpr int NW = BX * BY / 32;
 
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(128) char smem[];
   char* gring = smem;
   char* fring = gring + R * RBG;
-  C* sphi = reinterpret_cast<C*>(fring + R * RBF);
-  size_t boff = (size_t)R * RBG + (size_t)R * RBF + sizeof(C) * PHR * PHW;
+  char* obuf = fring + R * RBF;
+  C* sphi = reinterpret_cast<C*>(obuf + S::ooff(18, NOUT));
+  size_t boff = (size_t)R * RBG + (size_t)R * RBF + S::ooff(18, NOUT) + sizeof(C) * PHR * PHW;
   boff = (boff + 15) / 16 * 16;
   uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + boff);
   uint64_t* fbar = gbar + R;
   int* abort_flag = reinterpret_cast<int*>(fbar + R);
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const bool leader = tx == 0 && ty == 0;
+  const int tid = ty * BX + tx;
+  const int warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * BX;
   const int y0 = blockIdx.y * rows;
   const int y1 = min(y0 + rows, geo.ny);
@@ -110,8 +127,11 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
   const bool colv = tx < xv;
   const int gvb = y0 - 2, fvb = y0 - 1;  // first staged g / f row
   const int g_last = y1 + 1, f_last = y1;
+  const bool interior = x0 > 0 && x0 + xv < geo.nx;
+  const int xl = (x0 == 0) ? geo.nx - H : x0 - H;
+  const int xr = (x0 + xv == geo.nx) ? 0 : x0 + xv;
 
-  if (leader) {
+  if (tid == 0) {
     for (int k = 0; k < R; ++k) {
       mbar_init(&gbar[k], 1);
       mbar_init(&fbar[k], 1);
@@ -127,125 +147,207 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     return v;
   };
 
-  // Thread 0: stage row v of set g (true) or f (false).
-  int g_next = gvb, f_next = fvb;
-  auto issue_row = [&](bool g, int v) {
+  // Staging of row v of set g (true) or f (false) by one warp: lane 0 arms the slot's barrier
+  // with the byte count, then one lane per (plane, segment) issues its copy.
+  auto issue_row_warp = [&](bool g, int v) {
     const int k = v - (g ? gvb : fvb);
-    char* drow = (g ? gring + (k % R) * RBG : fring + (k % R) * RBF);
+    char* drow = g ? gring + (k % R) * RBG : fring + (k % R) * RBF;
     uint64_t* bar = g ? &gbar[k % R] : &fbar[k % R];
     const long long rowidx = (long long)phys_row(v) * geo.pitch;
-    const bool interior = x0 > 0 && x0 + xv < geo.nx;
-    const int xl = (x0 == 0) ? geo.nx - H : x0 - H;
-    const int xr = (x0 + xv == geo.nx) ? 0 : x0 + xv;
-    uint32_t total = 0;
+    if (lane == 0) {
+      uint32_t total = 0;
 #pragma unroll
-    for (int p = 0; p < 9; ++p) total += (uint32_t)((xv + 2 * H) * S::es(g, p));
-    mbar_arrive_expect_tx(bar, total);
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      const int e = S::es(g, p);
-      char* d = drow + S::soff(g, p, W);
-      if (interior) {
-        bulk_g2s(d, src + S::goff(g, p, geo.plane, rowidx + x0 - H), (uint32_t)((xv + 2 * H) * e), bar);
-      } else {
-        bulk_g2s(d, src + S::goff(g, p, geo.plane, rowidx + xl), (uint32_t)(H * e), bar);
-        bulk_g2s(d + H * e, src + S::goff(g, p, geo.plane, rowidx + x0), (uint32_t)(xv * e), bar);
-        bulk_g2s(d + (H + xv) * e, src + S::goff(g, p, geo.plane, rowidx + xr), (uint32_t)(H * e), bar);
+      for (int p = 0; p < 9; ++p) total += (uint32_t)((xv + 2 * H) * S::es(g, p));
+      mbar_arrive_expect_tx(bar, total);
+    }
+    __syncwarp();
+    if (interior) {
+      if (lane < 9) {
+        const int p = lane, e = S::es(g, p);
+        bulk_g2s(drow + S::soff(g, p, W), src + S::goff(g, p, geo.plane, rowidx + x0 - H),
+                 (uint32_t)((xv + 2 * H) * e), bar);
       }
+    } else if (lane < 27) {
+      const int p = lane / 3, seg = lane - 3 * p, e = S::es(g, p);
+      char* d = drow + S::soff(g, p, W);
+      if (seg == 0) bulk_g2s(d, src + S::goff(g, p, geo.plane, rowidx + xl), (uint32_t)(H * e), bar);
+      else if (seg == 1) bulk_g2s(d + H * e, src + S::goff(g, p, geo.plane, rowidx + x0), (uint32_t)(xv * e), bar);
+      else bulk_g2s(d + (H + xv) * e, src + S::goff(g, p, geo.plane, rowidx + xr), (uint32_t)(H * e), bar);
     }
   };
+  // All threads call this with the same arguments; rows are dealt out to warps.
+  int g_next = gvb, f_next = fvb;
   auto issue_upto = [&](int g_target, int f_target) {
-    g_target = min(g_target, g_last);
-    f_target = min(f_target, f_last);
-    while (g_next <= g_target) issue_row(true, g_next++);
-    while (f_next <= f_target) issue_row(false, f_next++);
+    const int ng = max(0, min(g_target, g_last) - g_next + 1);
+    const int nf = max(0, min(f_target, f_last) - f_next + 1);
+    for (int k = warp; k < ng + nf; k += NW) {
+      if (k < ng) issue_row_warp(true, g_next + k);
+      else issue_row_warp(false, f_next + (k - ng));
+    }
+    g_next += ng;
+    f_next += nf;
   };
-  // Every thread waits for a staged row before reading it.
   bool stuck = false;
   auto wait_row = [&](bool g, int v) {
     const int k = v - (g ? gvb : fvb);
     uint64_t* bar = g ? &gbar[k % R] : &fbar[k % R];
     if (!mbar_wait_bounded(bar, (uint32_t)((k / R) & 1), kWaitProbes)) stuck = true;
   };
-  auto grow = [&](int v) -> const char* { return gring + ((v - gvb) % R) * RBG; };
-  auto frow = [&](int v) -> const char* { return fring + ((v - fvb) % R) * RBF; };
 
-  // Pull of the populations arriving at node (column c of the staged rows, virtual row v) from
-  // the staged rows; same rule as pull() in lbm_device.cuh.
-  auto pull_s = [&](bool g, int c, int v, C out[9]) {
-    const int y = phys_row(v);
-    const bool bot = geo.walls && y == 0;
-    const bool top = geo.walls && y == geo.ny - 1;
-    // For the wall mirror rows (v = -1 or ny with walls) the node is the mirrored physical row,
-    // whose staged copy is the neighbouring virtual row.
-    const int vv = (geo.walls && v < 0) ? 0 : ((geo.walls && v >= geo.ny) ? geo.ny - 1 : v);
-    const char* r0 = g ? grow(vv) : frow(vv);
+  // Pointers to the staged rows v-1, v, v+1 of a set, for the node at virtual row v (a wall
+  // mirror row stands for its physical twin) and column byte offset.
+  struct Rows3 {
+    const char* lo;
+    const char* mid;
+    const char* hi;
+    int y;  // physical row of the node
+  };
+  auto rows3 = [&](bool g, int v, int cbytes) -> Rows3 {
+    if (geo.walls) v = v < 0 ? 0 : (v >= geo.ny ? geo.ny - 1 : v);
+    const int k = v - (g ? gvb : fvb);
+    const int sm = k % R;
+    const int sl = sm == 0 ? R - 1 : sm - 1;
+    const int sh = sm == R - 1 ? 0 : sm + 1;
+    const char* base = (g ? gring : fring) + cbytes;
+    const int rb = g ? RBG : RBF;
+    Rows3 r3;
+    r3.lo = base + sl * rb;
+    r3.mid = base + sm * rb;
+    r3.hi = base + sh * rb;
+    r3.y = phys_row(v);
+    return r3;
+  };
+  // Pull (Eqs. 4-5) from staged rows, same rule as pull() in lbm_device.cuh; c0 = the node's
+  // column offset is folded into the row pointers, so every access has a constant offset.
+  auto pull_s = [&](bool g, const Rows3& q, C out[9]) {
+    auto L = [&](const char* row, int p, int dc) -> C {
+      return S::sld(row + S::soff(g, p, W) + dc * S::es(g, p), g, p);
+    };
+    const bool bot = geo.walls && q.y == 0;
+    const bool top = geo.walls && q.y == geo.ny - 1;
     if (!bot && !top) {
-      const char* rm = g ? grow(vv - 1) : frow(vv - 1);
-      const char* rp = g ? grow(vv + 1) : frow(vv + 1);
-      out[0] = S::sld(r0, g, 0, c, W);
-      out[1] = S::sld(r0, g, 1, c - 1, W);
-      out[2] = S::sld(rm, g, 2, c, W);
-      out[3] = S::sld(r0, g, 3, c + 1, W);
-      out[4] = S::sld(rp, g, 4, c, W);
-      out[5] = S::sld(rm, g, 5, c - 1, W);
-      out[6] = S::sld(rm, g, 6, c + 1, W);
-      out[7] = S::sld(rp, g, 7, c + 1, W);
-      out[8] = S::sld(rp, g, 8, c - 1, W);
+      out[0] = L(q.mid, 0, 0);
+      out[1] = L(q.mid, 1, -1);
+      out[2] = L(q.lo, 2, 0);
+      out[3] = L(q.mid, 3, 1);
+      out[4] = L(q.hi, 4, 0);
+      out[5] = L(q.lo, 5, -1);
+      out[6] = L(q.lo, 6, 1);
+      out[7] = L(q.hi, 7, 1);
+      out[8] = L(q.hi, 8, -1);
       return;
     }
     C own[9];
     C s = C(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      own[i] = S::sld(r0, g, i, c, W);
+      own[i] = L(q.mid, i, 0);
       s += own[i];
     }
     out[0] = own[0];
-    out[1] = S::sld(r0, g, 1, c - 1, W);
-    out[3] = S::sld(r0, g, 3, c + 1, W);
+    out[1] = L(q.mid, 1, -1);
+    out[3] = L(q.mid, 3, 1);
     const C k6 = C(6) * s / C(36);
     if (bot) {
-      const char* rp = g ? grow(vv + 1) : frow(vv + 1);
       out[2] = own[4];
       out[5] = own[7] + k6 * ph.u_bottom;
       out[6] = own[8] - k6 * ph.u_bottom;
-      out[4] = S::sld(rp, g, 4, c, W);
-      out[7] = S::sld(rp, g, 7, c + 1, W);
-      out[8] = S::sld(rp, g, 8, c - 1, W);
+      out[4] = L(q.hi, 4, 0);
+      out[7] = L(q.hi, 7, 1);
+      out[8] = L(q.hi, 8, -1);
     } else {
-      const char* rm = g ? grow(vv - 1) : frow(vv - 1);
       out[4] = own[2];
       out[7] = own[5] - k6 * ph.u_top;
       out[8] = own[6] + k6 * ph.u_top;
-      out[2] = S::sld(rm, g, 2, c, W);
-      out[5] = S::sld(rm, g, 5, c - 1, W);
-      out[6] = S::sld(rm, g, 6, c + 1, W);
+      out[2] = L(q.lo, 2, 0);
+      out[5] = L(q.lo, 5, -1);
+      out[6] = L(q.lo, 6, 1);
     }
   };
   auto sum9 = [](const C v[9]) -> C {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
   };
-  auto pslot = [&](int r) -> int { return (r - (y0 - 1)) % PHR; };
+  constexpr int kEsC = S::kEs;  // column stride of every staged plane but the 16-bit g_0 one
+  static_assert(S::kHalf || kEsC == (int)sizeof(C), "staged element size");
+  // phi of virtual row v for this thread's column (and the halo columns for tx == 0 / BX-1).
+  // The column offset differs between the 16-bit g_0 plane (4 bytes) and the others; fold the
+  // column into the pointer per plane inside sld instead for that case.
   auto phi_row = [&](int v, C gkeep[9]) {
+    const int sl = (v - (y0 - 1)) % PHR;
+    auto pull_col = [&](int c, C out[9]) {
+      if constexpr (S::kHalf) {
+        // 16-bit staging: planes have two element sizes; address each plane explicitly.
+        const Rows3 q = rows3(true, v, 0);
+        const bool bot = geo.walls && q.y == 0;
+        const bool top = geo.walls && q.y == geo.ny - 1;
+        auto L = [&](const char* row, int p, int dc) -> C {
+          return S::sld(row + S::soff(true, p, W) + (c + dc) * S::es(true, p), true, p);
+        };
+        if (!bot && !top) {
+          out[0] = L(q.mid, 0, 0);
+          out[1] = L(q.mid, 1, -1);
+          out[2] = L(q.lo, 2, 0);
+          out[3] = L(q.mid, 3, 1);
+          out[4] = L(q.hi, 4, 0);
+          out[5] = L(q.lo, 5, -1);
+          out[6] = L(q.lo, 6, 1);
+          out[7] = L(q.hi, 7, 1);
+          out[8] = L(q.hi, 8, -1);
+          return;
+        }
+        C own[9];
+        C s = C(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          own[i] = L(q.mid, i, 0);
+          s += own[i];
+        }
+        out[0] = own[0];
+        out[1] = L(q.mid, 1, -1);
+        out[3] = L(q.mid, 3, 1);
+        const C k6 = C(6) * s / C(36);
+        if (bot) {
+          out[2] = own[4];
+          out[5] = own[7] + k6 * ph.u_bottom;
+          out[6] = own[8] - k6 * ph.u_bottom;
+          out[4] = L(q.hi, 4, 0);
+          out[7] = L(q.hi, 7, 1);
+          out[8] = L(q.hi, 8, -1);
+        } else {
+          out[4] = own[2];
+          out[7] = own[5] - k6 * ph.u_top;
+          out[8] = own[6] + k6 * ph.u_top;
+          out[2] = L(q.lo, 2, 0);
+          out[5] = L(q.lo, 5, -1);
+          out[6] = L(q.lo, 6, 1);
+        }
+      } else {
+        pull_s(true, rows3(true, v, c * kEsC), out);
+      }
+    };
     C gt[9];
-    const int sl = pslot(v);
     if (colv) {
-      pull_s(true, tx + H, v, gkeep);
+      pull_col(tx + H, gkeep);
       sphi[sl * PHW + tx + 1] = sum9(gkeep);
     }
     if (tx == 0) {
-      pull_s(true, H - 1, v, gt);
+      pull_col(H - 1, gt);
       sphi[sl * PHW + 0] = sum9(gt);
     }
     if (tx == BX - 1) {
-      pull_s(true, H + xv, v, gt);
+      pull_col(H + xv, gt);
       sphi[sl * PHW + xv + 1] = sum9(gt);
     }
   };
+  // f of the node (column tx) at virtual row r.
+  auto pull_f = [&](int r, C out[9]) { pull_s(false, rows3(false, r, (tx + H) * kEsC), out); };
+
+  // Threads that write the output planes of a band back with bulk stores: (plane q, row j).
+  const bool storer = tid < 18 * BY;
+  const int st_q = tid % 18, st_j = tid / 18;
 
   // Prologue: stage the first rows, then phi of rows y0-1 .. y0+BY-1.
-  if (leader) issue_upto(gvb + R - 1, fvb + R - 1);
+  issue_upto(gvb + R - 1, fvb + R - 1);
   for (int v = gvb; v <= min(y0 + BY, g_last); ++v) wait_row(true, v);
   C gcur[9], gnxt[9];
   {
@@ -259,34 +361,38 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
   // The prologue rows and the first step's rows span 2BY+3 > R rows: refill once the prologue
   // has read its rows (everything below g row y0+BY-1 is free).
   __syncthreads();
-  if (leader) issue_upto(y0 + BY - 1 + R - 1, fvb + R - 1);
+  issue_upto(y0 + BY - 1 + R - 1, fvb + R - 1);
 
   for (int Y = y0; Y < y1; Y += BY) {
     // rows of this step: g [Y+BY-1, Y+2BY] for phi, f [Y-1, Y+BY] for the pulls
     for (int v = max(Y + BY + 1, gvb); v <= min(Y + 2 * BY, g_last); ++v) wait_row(true, v);
-    for (int v = max(Y - 1, fvb); v <= min(Y + BY, f_last); ++v) wait_row(false, v);
+    for (int v = (Y == y0 ? fvb : Y + 1); v <= min(Y + BY, f_last); ++v) wait_row(false, v);
     const int rn = Y + BY + ty;
     if (rn <= y1) phi_row(rn, gnxt);
     const int r = Y + ty;
     const bool act = colv && r < y1;
     C f[9];
-    if (act) pull_s(false, tx + H, r, f);
+    if (act) pull_f(r, f);
     if (stuck) atomicExch(abort_flag, 1);
+    if (storer) bulk_wait_read_all();  // last band's stores are done reading the staging buffer
     __syncthreads();
     if (*abort_flag) {
-      if (leader) {
-        atomicOr(flag, 2);
-        // Let the copies already issued land before the CTA's shared memory is released.
+      if (tid == 0) atomicOr(flag, 2);
+      // Let the copies already issued land before the CTA's shared memory is released.
+      if (tid == 0) {
         for (int v = max(gvb, g_next - R); v < g_next; ++v) wait_row(true, v);
         for (int v = max(fvb, f_next - R); v < f_next; ++v) wait_row(false, v);
       }
+      if (storer) bulk_wait_all();
       return;
     }
     // Everything staged below g row Y+2BY-1 and f row Y+BY-1 has been read: refill.
-    if (leader) issue_upto(Y + 2 * BY - 1 + R - 1, Y + BY - 1 + R - 1);
+    issue_upto(Y + 2 * BY - 1 + R - 1, Y + BY - 1 + R - 1);
     if (act) {
       C s[3][3];
-      const int sm = pslot(r - 1), s0 = pslot(r), sp = pslot(r + 1);
+      const int sm = (r - 1 - (y0 - 1)) % PHR;
+      const int s0 = sm + 1 == PHR ? 0 : sm + 1;
+      const int sp = s0 + 1 == PHR ? 0 : s0 + 1;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         s[0][d] = sphi[sm * PHW + tx + d];
@@ -298,16 +404,29 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       const C phi = s[1][1];
       const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-      const int idx = r * geo.pitch + x0 + tx;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        P::stf(dst, geo.plane, i, idx, f[i]);
-        P::stg(dst, geo.plane, i, idx, gcur[i]);
+      for (int q = 0; q < 18; ++q) {
+        const int e = S::oes(q);  // planes carry their own element sizes (16-bit g_0 is FP32)
+        S::sst(obuf + S::ooff(q, NOUT) + (ty * BX + tx) * e, q, q < 9 ? f[q] : gcur[q - 9]);
       }
+      fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (storer) {
+      const int rs = Y + st_j;
+      if (rs < y1) {
+        const int e = S::oes(st_q);
+        const bool g = st_q >= 9;
+        const int p = g ? st_q - 9 : st_q;
+        bulk_s2g(dst + S::goff(g, p, geo.plane, (long long)rs * geo.pitch + x0),
+                 obuf + S::ooff(st_q, NOUT) + st_j * BX * e, (uint32_t)(xv * e));
+      }
+      bulk_commit();
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) gcur[i] = gnxt[i];
   }
+  if (storer) bulk_wait_all();
 }
 
 // -------------------------------------------------------------------------------------------

@@ -73,8 +73,10 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   const int xv = min(BX, geo.nx - x0);  // valid columns of this strip
   const int x = x0 + tx;
   const bool colv = tx < xv;
-  const int xl = (x0 == 0) ? geo.nx - 1 : x0 - 1;        // left halo column
-  const int xr = (x0 + xv == geo.nx) ? 0 : x0 + xv;      // right halo column
+  // Threads tx == 0 and tx == BX-1 also own the left / right halo column of the strip.
+  const bool halo = tx == 0 || tx == BX - 1;
+  const int hx = (tx == 0) ? ((x0 == 0) ? geo.nx - 1 : x0 - 1) : ((x0 + xv == geo.nx) ? 0 : x0 + xv);
+  const int hcol = (tx == 0) ? 0 : xv + 1;
 
   // Virtual row r in [y0 - 1, y1] -> physical row (periodic wrap, or the wall mirror
   // phi(x, -1) = phi(x, 0), phi(x, ny) = phi(x, ny - 1)).
@@ -87,35 +89,49 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   auto sum9 = [](const C v[9]) -> C {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
   };
-  // phi of virtual row r for this thread's column (and the halo columns for tx == 0 / BX-1);
-  // the pulled g of the own column is returned in gkeep.
-  auto phi_row = [&](int r, C gkeep[9]) {
-    const int yr = phys_row(r);
-    const int sl = slot(r);
-    C gt[9];
-    if (colv) {
-      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, x, yr, gkeep);
-      sphi[sl][tx + 1] = sum9(gkeep);
-    }
-    if (tx == 0) {
-      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xl, yr, gt);
-      sphi[sl][0] = sum9(gt);
-    }
-    if (tx == BX - 1) {
-      pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xr, yr, gt);
-      sphi[sl][xv + 1] = sum9(gt);
-    }
+  auto pull_g = [&](int xx, int r, C out[9]) {
+    pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xx, phys_row(r), out);
   };
 
-  C gcur[9], gnxt[9];
-  // Prologue: rows y0 - 1 (halo) and y0 .. y0 + BY - 1 (own), or up to y1 if shorter.
+  // Software pipeline: at the band of rows Y .. Y+BY-1 a thread (row Y+ty) holds
+  //   gA: g pulled for its row Y+ty (collided now), loaded two bands ago;
+  //   gB: g pulled for row Y+BY+ty (its phi is formed now), loaded one band ago;
+  //   gC: g for row Y+2BY+ty, issued now;
+  //   fA: f pulled for row Y+ty, loaded one band ago;  fB: f for row Y+BY+ty, issued now;
+  //   hB: g of its halo node (if any) for row Y+BY+ty, loaded one band ago, then reissued
+  //       for row Y+2BY+ty.
+  // so every load has a whole band of work to arrive.
+  C gA[9], gB[9], gC[9], fA[9], fB[9], hB[9];
   {
+    // Prologue: phi of rows y0-1 (halo, thread row 0) and y0+ty, loaded and used at once.
     const int r = y0 + ty;
-    if (r <= y1) phi_row(r, gcur);
+    if (r <= y1) {
+      if (colv) {
+        pull_g(x, r, gA);
+        sphi[slot(r)][tx + 1] = sum9(gA);
+      }
+      if (halo) {
+        pull_g(hx, r, hB);
+        sphi[slot(r)][hcol] = sum9(hB);
+      }
+    }
     if (ty == 0) {
       C gt[9];
-      phi_row(y0 - 1, gt);
+      if (colv) {
+        pull_g(x, y0 - 1, gt);
+        sphi[slot(y0 - 1)][tx + 1] = sum9(gt);
+      }
+      if (halo) {
+        pull_g(hx, y0 - 1, gt);
+        sphi[slot(y0 - 1)][hcol] = sum9(gt);
+      }
     }
+    const int rb = y0 + BY + ty;
+    if (rb <= y1) {
+      if (colv) pull_g(x, rb, gB);
+      if (halo) pull_g(hx, rb, hB);
+    }
+    if (colv && r < y1) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, r, fA);
   }
 
   // Ring argument: iteration j writes rows [Y+BY, Y+2BY) and reads rows [Y-1, Y+BY]; iteration
@@ -123,12 +139,17 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   // writes iteration j's, so those two ranges (3BY+1 rows) must map to distinct slots: RING =
   // 3BY+1.  Iteration j+1's writes cannot meet iteration j-1's reads (one barrier apart).
   for (int Y = y0; Y < y1; Y += BY) {
-    const int rn = Y + BY + ty;
-    if (rn <= y1) phi_row(rn, gnxt);
-    const int r = Y + ty;
+    const int r = Y + ty;          // collided now
+    const int rb = Y + BY + ty;    // phi formed now
+    const int rc = Y + 2 * BY + ty;  // g issued now
     const bool act = colv && r < y1;
-    C f[9];
-    if (act) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, r, f);
+    if (rc <= y1 && colv) pull_g(x, rc, gC);
+    if (rb < y1 && colv) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, rb, fB);
+    if (rb <= y1) {
+      if (colv) sphi[slot(rb)][tx + 1] = sum9(gB);
+      if (halo) sphi[slot(rb)][hcol] = sum9(hB);
+    }
+    if (rc <= y1 && halo) pull_g(hx, rc, hB);
     __syncthreads();
     if (act) {
       C s[3][3];
@@ -142,17 +163,21 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
       C dxp, dyp, lap;
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
-      const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
+      const C rho = collide<C>(ph, fA, gA, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
       const int idx = r * geo.pitch + x;
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        P::stf(dst, geo.plane, i, idx, f[i]);
-        P::stg(dst, geo.plane, i, idx, gcur[i]);
+        P::stf(dst, geo.plane, i, idx, fA[i]);
+        P::stg(dst, geo.plane, i, idx, gA[i]);
       }
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) gcur[i] = gnxt[i];
+    for (int i = 0; i < 9; ++i) {
+      gA[i] = gB[i];
+      gB[i] = gC[i];
+      fA[i] = fB[i];
+    }
   }
 }
 

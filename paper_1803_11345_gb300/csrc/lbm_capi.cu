@@ -346,8 +346,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   }
   StepTile t;
   t.staged = variant == LBM_KERNEL_STAGED;
-  t.bx = bx ? bx : (h->p.prec == LBM_FP64 ? 32 : 64);
-  t.by = by ? by : 4;
+  t.bx = bx ? bx : (t.staged ? 64 : 256);
+  t.by = by ? by : (t.staged ? 4 : 1);
   t.depth = depth ? depth : 1;
   t.rows = 0;
   const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) : tile_supported(h->p.prec, t.bx, t.by);
@@ -361,8 +361,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   } else {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t) : 0;
-    t.rows = rows_for_wave(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 2));
+    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t) : generic_blocks_per_sm(h->p.prec, t);
+    t.rows = rows_for_wave(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1));
   }
   h->tile = t;
   return LBM_OK;

@@ -46,6 +46,13 @@ template <class T> struct PopDense {
   __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) { return ld(b, pl, 9 + i, idx); }
   __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) { st(b, pl, i, idx, v); }
   __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) { st(b, pl, 9 + i, idx, v); }
+  __device__ __forceinline__ static void store_node(char* b, long long pl, int idx, const C f[9], const C g[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      stf(b, pl, i, idx, f[i]);
+      stg(b, pl, i, idx, g[i]);
+    }
+  }
 };
 template <> struct Pop<0> : PopDense<double> {};
 template <> struct Pop<1> : PopDense<float> {};
@@ -83,6 +90,27 @@ template <class H> struct PopHalf {
       return;
     }
     reinterpret_cast<H*>(b)[(8 + i) * pl + idx] = Cvt<H>::from(v);
+  }
+  // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
+  // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
+  // to the post-collision rho and phi: 16-bit rounding then redistributes among directions but
+  // does not create or destroy mass or order parameter.  g_0 is FP32, f_0 - w_0 16-bit.
+  __device__ __forceinline__ static void store_node(char* b, long long pl, int idx, const C f[9], const C g[9]) {
+    H* hb = reinterpret_cast<H*>(b);
+    const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const float phi = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    float sf = 0.0f, sg = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const H hf = Cvt<H>::from(f[i] - wrest(i));
+      const H hg = Cvt<H>::from(g[i]);
+      hb[i * pl + idx] = hf;
+      hb[(8 + i) * pl + idx] = hg;
+      sf += Cvt<H>::to(hf) + wrest(i);
+      sg += Cvt<H>::to(hg);
+    }
+    hb[idx] = Cvt<H>::from((rho - sf) - wrest(0));
+    reinterpret_cast<float*>(hb + 17 * pl)[idx] = phi - sg;
   }
 };
 template <> struct Pop<2> : PopHalf<__half> {};

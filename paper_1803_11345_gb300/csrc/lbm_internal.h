@@ -59,6 +59,8 @@ cudaError_t launch_step_staged(int prec, const HostGeometry& g, const HostPhys& 
 
 // Default tile for a precision and lattice, sized so the grid fills the GPU in one wave.
 StepTile default_tile(int prec, const HostGeometry& g, int device);
+// Resident CTAs per SM of the generic kernel for a tile.
+int generic_blocks_per_sm(int prec, const StepTile& t);
 // Rows per CTA so that the grid is about `ctas` CTAs (one wave).
 int rows_for_wave(const HostGeometry& g, const StepTile& t, int ctas);
 // Whether a tile shape has a compiled kernel.

@@ -55,15 +55,29 @@ template <int PREC> struct Stage {
       return g ? v : v + (float)lat_w36(p) * (1.0f / 36.0f);
     }
   }
-  // Store a post-collision value of output plane q into the staging buffer.
-  __device__ __forceinline__ static void sst(char* a, int q, C v) {
-    if constexpr (PREC == 0) *reinterpret_cast<double*>(a) = v;
-    else if constexpr (PREC == 1) *reinterpret_cast<float*>(a) = v;
-    else {
+  // Store the post-collision populations of one node (element e of every output plane of n
+  // elements) into the staging buffer, with the same encoding as Pop<PREC>::store_node.
+  __device__ __forceinline__ static void store_node(char* ob, int n, int e, const C f[9], const C g[9]) {
+    if constexpr (!kHalf) {
+#pragma unroll
+      for (int q = 0; q < 18; ++q) reinterpret_cast<C*>(ob + ooff(q, n))[e] = q < 9 ? f[q] : g[q - 9];
+    } else {
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
-      if (q == 9) *reinterpret_cast<float*>(a) = v;
-      else if (q < 9) *reinterpret_cast<Hf*>(a) = Cvt<Hf>::from(v - (float)lat_w36(q) * (1.0f / 36.0f));
-      else *reinterpret_cast<Hf*>(a) = Cvt<Hf>::from(v);
+      const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+      const float phi = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+      float sf = 0.0f, sg = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const float w = (float)lat_w36(i) * (1.0f / 36.0f);
+        const Hf hf = Cvt<Hf>::from(f[i] - w);
+        const Hf hg = Cvt<Hf>::from(g[i]);
+        reinterpret_cast<Hf*>(ob + ooff(i, n))[e] = hf;
+        reinterpret_cast<Hf*>(ob + ooff(9 + i, n))[e] = hg;
+        sf += Cvt<Hf>::to(hf) + w;
+        sg += Cvt<Hf>::to(hg);
+      }
+      reinterpret_cast<Hf*>(ob + ooff(0, n))[e] = Cvt<Hf>::from((rho - sf) - (float)lat_w36(0) * (1.0f / 36.0f));
+      reinterpret_cast<float*>(ob + ooff(9, n))[e] = phi - sg;
     }
   }
 };
@@ -404,11 +418,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       const C phi = s[1][1];
       const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-#pragma unroll
-      for (int q = 0; q < 18; ++q) {
-        const int e = S::oes(q);  // planes carry their own element sizes (16-bit g_0 is FP32)
-        S::sst(obuf + S::ooff(q, NOUT) + (ty * BX + tx) * e, q, q < 9 ? f[q] : gcur[q - 9]);
-      }
+      S::store_node(obuf, NOUT, ty * BX + tx, f, gcur);
       fence_proxy_async_smem();
     }
     __syncthreads();

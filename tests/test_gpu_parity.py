@@ -170,16 +170,32 @@ def test_spinodal_fp32_1000_steps(lbm, orc):
     assert rel_err(rg, ro) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
-def test_sheared_droplet_16bit_storage(lbm, orc, prec):
-    """16-bit deviation storage keeps phi within 2e-3 of the FP64 oracle over 1000 steps."""
+@pytest.mark.parametrize("prec,bound", [("fp16s", 2e-3), ("bf16s", 2e-2)])
+def test_sheared_droplet_16bit_storage(lbm, orc, prec, bound):
+    """16-bit deviation storage against the FP64 oracle over 1000 steps of a sheared droplet.
+    FP16 (11-bit significand) keeps phi within 2e-3.  BF16 (8-bit significand) rounds the f
+    deviations (~3e-3, mostly 3 w_i c.u) to ~1e-5, which biases the velocity and shifts the
+    interface by ~1e-2 lattice units over 1000 steps; its bound is 2e-2 (|grad phi| <= 0.7)."""
     phi0 = W.droplet(128, 64, 16, gamma=0.04, a=0.04)
     kw = dict(tau_l=orc.tau_from_nu(0.2), tau_g=orc.tau_from_nu(0.02), bc=lbm.LBM_WALLS_Y,
               u_top=0.01, u_bottom=-0.01)
     lat, o = run_pair(lbm, orc, phi0, 1000, prec=lbm.PRECISIONS[prec], **kw)
     _, _, _, pg = lat.fields()
     _, _, _, po = o.fields()
-    assert abs_err(pg, po) <= 2e-3, abs_err(pg, po)
+    assert abs_err(pg, po) <= bound, abs_err(pg, po)
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_16bit_storage_conserves_phi_and_mass(lbm, prec):
+    """The rest populations are stored as closures of the rounded moving ones (Eq. 10), so
+    sum phi and sum rho stay conserved to FP32 accumulation error, not to 16-bit rounding."""
+    nx, ny = 128, 96
+    lat = lbm.Lattice(W.spinodal(nx, ny, seed=21), prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53)
+    s0 = lat.conservation()
+    lat.step(500)
+    s1 = lat.conservation()
+    assert abs(s1[0] - s0[0]) <= 2e-6 * nx * ny, (s0[0], s1[0])
+    assert abs(s1[1] - s0[1]) <= 2e-6 * nx * ny, (s0[1], s1[1])
 
 
 # -------------------------------------------------------------------------------------------

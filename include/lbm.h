@@ -168,6 +168,37 @@ LBM_API int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int dept
 /* The kernel and tile lbm_step uses now (variant is GENERIC or STAGED); NULL pointers skipped. */
 LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows);
 
+/* Conservation totals of a population state in device memory, computed without allocating.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a host framework that owns all device memory and hands out a fixed arena, a
+ * process held to a device-memory budget, or a state restored into a preallocated slab -- and
+ * that hold no lattice handle whose spare population copy lbm_conservation could use as scratch.
+ * It runs the same deterministic FP64 reduction as lbm_conservation and gives bit-identical
+ * totals for the same state.
+ *   state   device pointer (16-byte aligned) to one population copy in the layout lbm_init
+ *           builds: pitch = nx rounded up to a multiple of 32, plane = pitch * ny elements;
+ *           FP64/FP32: 18 planes (f_0..f_8, g_0..g_8) of that type; FP16S/BF16S: 17 16-bit planes
+ *           (f_i - w_i, then g_1..g_8) followed by one FP32 plane (g_0).  For a lattice created
+ *           on a caller-supplied device_buffer, each population copy takes
+ *           (lbm_state_bytes(p) - 256) / 2 bytes and the state after t = lbm_time(h) steps is the
+ *           copy at device_buffer + (t % 2) * that size.
+ *   nx, ny, prec  the lattice the state belongs to.
+ *   totals  host array of 4 doubles: sum phi, sum rho, sum rho v_x, sum rho v_y.
+ *   stream  cudaStream_t to run on, or NULL; the call synchronises it.
+ * Scratch: a library-wide static device array of 1024 * 4 + 4 doubles (32 KiB), which every GPU
+ * that loads the library keeps until the process exits.  The kernel launches at most 1024 blocks
+ * whatever the lattice size, so every lattice the library accepts fits; lattices beyond the
+ * library's limit (pitch * ny >= 2^31) are rejected with LBM_ERR_PARAM.  No call allocates or
+ * frees device memory.  All calls share the array and it keeps the last call's contents; every
+ * call overwrites what it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (other streams, other host threads) race on it.  The first call on each device looks up the
+ * array's device address with that device current; make that first call before any stream
+ * capture.
+ * Errors: LBM_ERR_PARAM (NULL pointers, bad sizes or precision, misaligned state), LBM_ERR_CUDA;
+ * the message is readable with lbm_last_error(NULL) on the calling thread. */
+LBM_API int lbm_totals_noalloc(const void* state, int nx, int ny, int prec, double* totals, void* stream);
+
 /* Time level reached (number of completed steps since lbm_init). */
 LBM_API long long lbm_time(const lbm_lattice* h);
 

@@ -107,6 +107,8 @@ size_t total_bytes(int prec, const HostGeometry& g, size_t* pop_bytes) {
 
 }  // namespace
 
+void lbmch::set_thread_error(const char* msg) { std::snprintf(g_init_err, sizeof(g_init_err), "%s", msg); }
+
 extern "C" {
 
 void lbm_default_params(lbm_params* p) {

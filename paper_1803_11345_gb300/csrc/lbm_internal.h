@@ -25,6 +25,9 @@ struct StepTile {
   int staged, depth;
 };
 
+// Message returned by lbm_last_error(NULL) on the calling thread.
+void set_thread_error(const char* msg);
+
 // Fill n doubles with v.
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 

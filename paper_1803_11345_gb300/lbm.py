@@ -77,6 +77,8 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lib.lbm_get_kernel.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.lbm_get_kernel.restype = i
+    lib.lbm_totals_noalloc.argtypes = [vp, i, i, i, dp, vp]
+    lib.lbm_totals_noalloc.restype = i
     lib.lbm_time.argtypes = [vp]
     lib.lbm_time.restype = ctypes.c_longlong
     lib.lbm_last_error.argtypes = [vp]
@@ -189,6 +191,21 @@ def lbm_get_kernel(h: int):
     return tuple(x.value for x in v)
 
 
+def lbm_totals_noalloc(state: int, nx: int, ny: int, prec: int, stream: int = 0):
+    """Totals (sum phi, sum rho, sum rho vx, sum rho vy) of a device population state; see
+    include/lbm.h for the layout.  Allocates no device memory."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.lbm_totals_noalloc(ctypes.c_void_p(state), nx, ny, prec,
+                                   ctypes.cast(out, ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.c_void_p(stream or None)), None)
+    return tuple(out)
+
+
+def state_copy_bytes(p: lbm_params) -> int:
+    """Bytes of one population copy inside a caller-supplied lbm_init buffer."""
+    return (lbm_state_bytes(p) - 256) // 2
+
+
 def lbm_time(h: int) -> int:
     return _lib.lbm_time(h)
 
@@ -244,6 +261,11 @@ class Lattice:
 
     def set_kernel(self, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0):
         lbm_set_kernel(self.h, variant, bx, by, depth, rows)
+
+    @property
+    def state_ptr(self) -> int:
+        """Device address of the current population copy (inside self.buffer)."""
+        return self.buffer.data_ptr() + (self.time % 2) * state_copy_bytes(self.params)
 
     @property
     def kernel(self):

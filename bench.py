@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (f+g) and % HBM roofline on 1 GB300; surrogate/16-bit/batch speedup at φ err"
-BYTES_PER_NODE = {"fp64": 288, "fp32": 144, "fp16s": 76, "bf16s": 76}
+BYTES_PER_NODE = {"fp64": 288, "fp32": 144, "fp16s": 80, "bf16s": 80}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f32 (16-bit storage)", "bf16s": "f32 (bf16 storage)"}
 PHYS = dict(nu_l=0.1, nu_g=0.01, a=0.04, gamma=0.04, M=0.1, Gamma=1.0)
 SEED = 2024

@@ -51,8 +51,10 @@ typedef enum {
 } lbm_status;
 
 /* Storage precision of the populations.  FP64: stored and computed in FP64.  FP32: stored and
- * computed in FP32.  FP16S / BF16S: f_i - w_i and g_i (i >= 1) stored as 16-bit deviations
- * from the rest state, g_0 stored in FP32, all arithmetic in FP32. */
+ * computed in FP32.  FP16S / BF16S: the moving populations f_i - w_i and g_i (i >= 1) stored as
+ * 16-bit deviations from the rest state; the rest populations f_0 and g_0 stored in FP32 as
+ * closures (Eq. 10) of the rounded moving ones, so that storage conserves rho and phi exactly;
+ * all arithmetic in FP32. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
 
 /* Boundaries.  PERIODIC: both directions.  WALLS_Y: periodic in x, halfway bounce-back walls
@@ -178,8 +180,8 @@ LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by,
  * totals for the same state.
  *   state   device pointer (16-byte aligned) to one population copy in the layout lbm_init
  *           builds: pitch = nx rounded up to a multiple of 32, plane = pitch * ny elements;
- *           FP64/FP32: 18 planes (f_0..f_8, g_0..g_8) of that type; FP16S/BF16S: 17 16-bit planes
- *           (f_i - w_i, then g_1..g_8) followed by one FP32 plane (g_0).  For a lattice created
+ *           FP64/FP32: 18 planes (f_0..f_8, g_0..g_8) of that type; FP16S/BF16S: 16 16-bit planes
+ *           (f_1 - w_1 .. f_8 - w_8, then g_1..g_8) followed by two FP32 planes (f_0, g_0).  For a lattice created
  *           on a caller-supplied device_buffer, each population copy takes
  *           (lbm_state_bytes(p) - 256) / 2 bytes and the state after t = lbm_time(h) steps is the
  *           copy at device_buffer + (t % 2) * that size.

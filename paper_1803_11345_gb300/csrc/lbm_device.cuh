@@ -57,9 +57,11 @@ template <class T> struct PopDense {
 template <> struct Pop<0> : PopDense<double> {};
 template <> struct Pop<1> : PopDense<float> {};
 
-// 16-bit storage: planes 0..8 hold f_i - w_i (deviation from the rest state rho = 1, v = 0),
-// planes 9..16 hold g_1..g_8 (rest value 0), all as 16-bit floats; g_0 (~phi, O(1)) is kept in an
-// FP32 plane after them.  Arithmetic is FP32.
+// 16-bit storage: 16 planes of 16-bit floats hold the moving populations, f_i - w_i for
+// i = 1..8 (deviation from the rest state rho = 1, v = 0) at plane i-1 and g_i (rest value 0) at
+// plane 7+i; then two FP32 planes hold the rest populations f_0 and g_0, stored as closures so
+// that every node's stored populations sum to its rho and phi (see store_node).  Arithmetic is
+// FP32.
 template <class H> struct Cvt;
 template <> struct Cvt<__half> {
   __device__ __forceinline__ static float to(__half h) { return __half2float(h); }
@@ -72,29 +74,35 @@ template <> struct Cvt<__nv_bfloat16> {
 
 template <class H> struct PopHalf {
   using C = float;
-  static constexpr size_t kBytesPerElem = 17 * sizeof(H) + sizeof(float);
+  static constexpr size_t kBytesPerElem = 16 * sizeof(H) + 2 * sizeof(float);
   __device__ __forceinline__ static float wrest(int i) { return (float)lat_w36(i) * (1.0f / 36.0f); }
+  __device__ __forceinline__ static const float* rest_plane(const char* b, long long pl, int set) {
+    return reinterpret_cast<const float*>(reinterpret_cast<const H*>(b) + 16 * pl) + set * pl;
+  }
+  __device__ __forceinline__ static float* rest_plane(char* b, long long pl, int set) {
+    return reinterpret_cast<float*>(reinterpret_cast<H*>(b) + 16 * pl) + set * pl;
+  }
   __device__ __forceinline__ static C ldf(const char* b, long long pl, int i, int idx) {
-    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + i * pl + idx)) + wrest(i);
+    if (i == 0) return __ldg(rest_plane(b, pl, 0) + idx);
+    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (i - 1) * pl + idx)) + wrest(i);
   }
   __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) {
-    if (i == 0) return __ldg(reinterpret_cast<const float*>(reinterpret_cast<const H*>(b) + 17 * pl) + idx);
-    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (8 + i) * pl + idx));
+    if (i == 0) return __ldg(rest_plane(b, pl, 1) + idx);
+    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (7 + i) * pl + idx));
   }
+  // Single values (checkpoint restore): the rest populations are stored as given.
   __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) {
-    reinterpret_cast<H*>(b)[i * pl + idx] = Cvt<H>::from(v - wrest(i));
+    if (i == 0) rest_plane(b, pl, 0)[idx] = v;
+    else reinterpret_cast<H*>(b)[(i - 1) * pl + idx] = Cvt<H>::from(v - wrest(i));
   }
   __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) {
-    if (i == 0) {
-      reinterpret_cast<float*>(reinterpret_cast<H*>(b) + 17 * pl)[idx] = v;
-      return;
-    }
-    reinterpret_cast<H*>(b)[(8 + i) * pl + idx] = Cvt<H>::from(v);
+    if (i == 0) rest_plane(b, pl, 1)[idx] = v;
+    else reinterpret_cast<H*>(b)[(7 + i) * pl + idx] = Cvt<H>::from(v);
   }
   // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
   // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
   // to the post-collision rho and phi: 16-bit rounding then redistributes among directions but
-  // does not create or destroy mass or order parameter.  g_0 is FP32, f_0 - w_0 16-bit.
+  // does not create or destroy mass or order parameter.
   __device__ __forceinline__ static void store_node(char* b, long long pl, int idx, const C f[9], const C g[9]) {
     H* hb = reinterpret_cast<H*>(b);
     const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
@@ -104,13 +112,13 @@ template <class H> struct PopHalf {
     for (int i = 1; i < 9; ++i) {
       const H hf = Cvt<H>::from(f[i] - wrest(i));
       const H hg = Cvt<H>::from(g[i]);
-      hb[i * pl + idx] = hf;
-      hb[(8 + i) * pl + idx] = hg;
+      hb[(i - 1) * pl + idx] = hf;
+      hb[(7 + i) * pl + idx] = hg;
       sf += Cvt<H>::to(hf) + wrest(i);
       sg += Cvt<H>::to(hg);
     }
-    hb[idx] = Cvt<H>::from((rho - sf) - wrest(0));
-    reinterpret_cast<float*>(hb + 17 * pl)[idx] = phi - sg;
+    rest_plane(b, pl, 0)[idx] = rho - sf;
+    rest_plane(b, pl, 1)[idx] = phi - sg;
   }
 };
 template <> struct Pop<2> : PopHalf<__half> {};

@@ -28,28 +28,28 @@ template <int PREC> struct Stage {
   static constexpr bool kHalf = PREC >= 2;
   static constexpr int kEs = PREC == 0 ? 8 : (PREC == 1 ? 4 : 2);  // bytes of a packed population
   static constexpr int H = 16 / kEs;                                   // halo columns per side
-  __host__ __device__ static constexpr int es(bool g, int p) { return (kHalf && g && p == 0) ? 4 : kEs; }
-  // Byte offset of plane p inside a staged row of W columns (16-bit g: the FP32 g_0 plane first).
+  // Element size of population p of either set (16-bit storage keeps p = 0 in FP32).
+  __host__ __device__ static constexpr int es(bool g, int p) { return (kHalf && p == 0) ? 4 : kEs; }
+  // Byte offset of plane p inside a staged row of W columns (16-bit: the FP32 rest plane first).
   __host__ __device__ static constexpr int soff(bool g, int p, int W) {
-    return (!kHalf || !g) ? p * W * kEs : (p == 0 ? 0 : W * 4 + (p - 1) * W * 2);
+    return !kHalf ? p * W * kEs : (p == 0 ? 0 : W * 4 + (p - 1) * W * 2);
   }
   __host__ __device__ static constexpr int row_bytes(bool g, int W) { return soff(g, 8, W) + W * es(g, 8); }
-  // Global byte offset of element idx of plane p of set g.
+  // Global byte offset of element idx of population p of set g (layout of Pop<PREC>).
   __device__ __forceinline__ static long long goff(bool g, int p, long long pl, long long idx) {
     if (!kHalf) return ((g ? 9 : 0) + p) * pl * kEs + idx * kEs;
-    if (!g) return p * pl * 2 + idx * 2;
-    if (p == 0) return 17 * pl * 2 + idx * 4;
-    return (8 + p) * pl * 2 + idx * 2;
+    if (p == 0) return 16 * pl * 2 + (g ? pl * 4 : 0) + idx * 4;
+    return ((g ? 7 : -1) + p) * pl * 2 + idx * 2;
   }
   // Output staging: plane q = 0..17 (f_0..f_8, g_0..g_8), n elements each, packed in order.
-  __host__ __device__ static constexpr int oes(int q) { return q < 9 ? kEs : es(true, q - 9); }
+  __host__ __device__ static constexpr int oes(int q) { return q < 9 ? es(false, q) : es(true, q - 9); }
   __host__ __device__ static constexpr int ooff(int q, int n) { return q == 0 ? 0 : ooff(q - 1, n) + n * oes(q - 1); }
   // Population value from a staged row (a points at the element).
   __device__ __forceinline__ static C sld(const char* a, bool g, int p) {
     if constexpr (PREC == 0) return *reinterpret_cast<const double*>(a);
     else if constexpr (PREC == 1) return *reinterpret_cast<const float*>(a);
     else {
-      if (g && p == 0) return *reinterpret_cast<const float*>(a);
+      if (p == 0) return *reinterpret_cast<const float*>(a);
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
       const float v = Cvt<Hf>::to(*reinterpret_cast<const Hf*>(a));
       return g ? v : v + (float)lat_w36(p) * (1.0f / 36.0f);
@@ -76,7 +76,7 @@ template <int PREC> struct Stage {
         sf += Cvt<Hf>::to(hf) + w;
         sg += Cvt<Hf>::to(hg);
       }
-      reinterpret_cast<Hf*>(ob + ooff(0, n))[e] = Cvt<Hf>::from((rho - sf) - (float)lat_w36(0) * (1.0f / 36.0f));
+      reinterpret_cast<float*>(ob + ooff(0, n))[e] = rho - sf;
       reinterpret_cast<float*>(ob + ooff(9, n))[e] = phi - sg;
     }
   }
@@ -286,58 +286,60 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
   // phi of virtual row v for this thread's column (and the halo columns for tx == 0 / BX-1).
   // The column offset differs between the 16-bit g_0 plane (4 bytes) and the others; fold the
   // column into the pointer per plane inside sld instead for that case.
+  // 16-bit staging: planes have two element sizes (the FP32 rest plane and 16-bit others), so
+  // each access carries its own column offset.
+  auto pull_explicit = [&](bool g, int v, int c, C out[9]) {
+    const Rows3 q = rows3(g, v, 0);
+    const bool bot = geo.walls && q.y == 0;
+    const bool top = geo.walls && q.y == geo.ny - 1;
+    auto L = [&](const char* row, int p, int dc) -> C {
+      return S::sld(row + S::soff(g, p, W) + (c + dc) * S::es(g, p), g, p);
+    };
+    if (!bot && !top) {
+      out[0] = L(q.mid, 0, 0);
+      out[1] = L(q.mid, 1, -1);
+      out[2] = L(q.lo, 2, 0);
+      out[3] = L(q.mid, 3, 1);
+      out[4] = L(q.hi, 4, 0);
+      out[5] = L(q.lo, 5, -1);
+      out[6] = L(q.lo, 6, 1);
+      out[7] = L(q.hi, 7, 1);
+      out[8] = L(q.hi, 8, -1);
+      return;
+    }
+    C own[9];
+    C s = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      own[i] = L(q.mid, i, 0);
+      s += own[i];
+    }
+    out[0] = own[0];
+    out[1] = L(q.mid, 1, -1);
+    out[3] = L(q.mid, 3, 1);
+    const C k6 = C(6) * s / C(36);
+    if (bot) {
+      out[2] = own[4];
+      out[5] = own[7] + k6 * ph.u_bottom;
+      out[6] = own[8] - k6 * ph.u_bottom;
+      out[4] = L(q.hi, 4, 0);
+      out[7] = L(q.hi, 7, 1);
+      out[8] = L(q.hi, 8, -1);
+    } else {
+      out[4] = own[2];
+      out[7] = own[5] - k6 * ph.u_top;
+      out[8] = own[6] + k6 * ph.u_top;
+      out[2] = L(q.lo, 2, 0);
+      out[5] = L(q.lo, 5, -1);
+      out[6] = L(q.lo, 6, 1);
+    }
+  };
+  // phi of virtual row v for this thread's column (and the halo columns for tx == 0 / BX-1).
   auto phi_row = [&](int v, C gkeep[9]) {
     const int sl = (v - (y0 - 1)) % PHR;
     auto pull_col = [&](int c, C out[9]) {
-      if constexpr (S::kHalf) {
-        // 16-bit staging: planes have two element sizes; address each plane explicitly.
-        const Rows3 q = rows3(true, v, 0);
-        const bool bot = geo.walls && q.y == 0;
-        const bool top = geo.walls && q.y == geo.ny - 1;
-        auto L = [&](const char* row, int p, int dc) -> C {
-          return S::sld(row + S::soff(true, p, W) + (c + dc) * S::es(true, p), true, p);
-        };
-        if (!bot && !top) {
-          out[0] = L(q.mid, 0, 0);
-          out[1] = L(q.mid, 1, -1);
-          out[2] = L(q.lo, 2, 0);
-          out[3] = L(q.mid, 3, 1);
-          out[4] = L(q.hi, 4, 0);
-          out[5] = L(q.lo, 5, -1);
-          out[6] = L(q.lo, 6, 1);
-          out[7] = L(q.hi, 7, 1);
-          out[8] = L(q.hi, 8, -1);
-          return;
-        }
-        C own[9];
-        C s = C(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          own[i] = L(q.mid, i, 0);
-          s += own[i];
-        }
-        out[0] = own[0];
-        out[1] = L(q.mid, 1, -1);
-        out[3] = L(q.mid, 3, 1);
-        const C k6 = C(6) * s / C(36);
-        if (bot) {
-          out[2] = own[4];
-          out[5] = own[7] + k6 * ph.u_bottom;
-          out[6] = own[8] - k6 * ph.u_bottom;
-          out[4] = L(q.hi, 4, 0);
-          out[7] = L(q.hi, 7, 1);
-          out[8] = L(q.hi, 8, -1);
-        } else {
-          out[4] = own[2];
-          out[7] = own[5] - k6 * ph.u_top;
-          out[8] = own[6] + k6 * ph.u_top;
-          out[2] = L(q.lo, 2, 0);
-          out[5] = L(q.lo, 5, -1);
-          out[6] = L(q.lo, 6, 1);
-        }
-      } else {
-        pull_s(true, rows3(true, v, c * kEsC), out);
-      }
+      if constexpr (S::kHalf) pull_explicit(true, v, c, out);
+      else pull_s(true, rows3(true, v, c * kEsC), out);
     };
     C gt[9];
     if (colv) {
@@ -354,7 +356,10 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     }
   };
   // f of the node (column tx) at virtual row r.
-  auto pull_f = [&](int r, C out[9]) { pull_s(false, rows3(false, r, (tx + H) * kEsC), out); };
+  auto pull_f = [&](int r, C out[9]) {
+    if constexpr (S::kHalf) pull_explicit(false, r, tx + H, out);
+    else pull_s(false, rows3(false, r, (tx + H) * kEsC), out);
+  };
 
   // Threads that write the output planes of a band back with bulk stores: (plane q, row j).
   const bool storer = tid < 18 * BY;

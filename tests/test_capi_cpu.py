@@ -56,7 +56,7 @@ def test_state_bytes_scale_with_precision(lbm):
     N = 256 * 256
     assert sizes["fp64"] >= 2 * 18 * 8 * N
     assert sizes["fp32"] >= 2 * 18 * 4 * N
-    assert sizes["fp16s"] >= 2 * (17 * 2 + 4) * N
+    assert sizes["fp16s"] >= 2 * (16 * 2 + 2 * 4) * N
     assert sizes["fp16s"] < sizes["fp32"] < sizes["fp64"]
 
 

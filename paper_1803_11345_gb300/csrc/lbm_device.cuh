@@ -53,6 +53,14 @@ template <class T> struct PopDense {
       stg(b, pl, i, idx, g[i]);
     }
   }
+  // Raw access: the stored bits, decoded only where used (keeps loads in flight).
+  using R = T;
+  __device__ __forceinline__ static R rawf(const char* b, long long pl, int i, int idx) { return ldf(b, pl, i, idx); }
+  __device__ __forceinline__ static R rawg(const char* b, long long pl, int i, int idx) { return ldg(b, pl, i, idx); }
+  __device__ __forceinline__ static C decf(int, R r) { return r; }
+  __device__ __forceinline__ static C decg(int, R r) { return r; }
+  __device__ __forceinline__ static R keep(C v) { return v; }   // an already-decoded value
+  __device__ __forceinline__ static C kept(R r) { return r; }
 };
 template <> struct Pop<0> : PopDense<double> {};
 template <> struct Pop<1> : PopDense<float> {};
@@ -120,6 +128,26 @@ template <class H> struct PopHalf {
     rest_plane(b, pl, 0)[idx] = rho - sf;
     rest_plane(b, pl, 1)[idx] = phi - sg;
   }
+  // Raw access: 32-bit words holding either the FP32 rest value (i = 0) or the 16-bit pattern of
+  // a moving population, decoded only where used so that loads stay in flight.
+  using R = uint32_t;
+  __device__ __forceinline__ static R rawf(const char* b, long long pl, int i, int idx) {
+    if (i == 0) return __float_as_uint(__ldg(rest_plane(b, pl, 0) + idx));
+    return (R)__ldg(reinterpret_cast<const unsigned short*>(b) + (i - 1) * pl + idx);
+  }
+  __device__ __forceinline__ static R rawg(const char* b, long long pl, int i, int idx) {
+    if (i == 0) return __float_as_uint(__ldg(rest_plane(b, pl, 1) + idx));
+    return (R)__ldg(reinterpret_cast<const unsigned short*>(b) + (7 + i) * pl + idx);
+  }
+  __device__ __forceinline__ static float h2f(R r) {
+    H h;
+    *reinterpret_cast<unsigned short*>(&h) = (unsigned short)r;
+    return Cvt<H>::to(h);
+  }
+  __device__ __forceinline__ static C decf(int i, R r) { return i == 0 ? __uint_as_float(r) : h2f(r) + wrest(i); }
+  __device__ __forceinline__ static C decg(int i, R r) { return i == 0 ? __uint_as_float(r) : h2f(r); }
+  __device__ __forceinline__ static R keep(C v) { return __float_as_uint(v); }
+  __device__ __forceinline__ static C kept(R r) { return __uint_as_float(r); }
 };
 template <> struct Pop<2> : PopHalf<__half> {};
 template <> struct Pop<3> : PopHalf<__nv_bfloat16> {};
@@ -206,6 +234,49 @@ __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometr
     out[5] = LD(5, rm + xm);
     out[6] = LD(6, rm + xp);
   }
+}
+
+// Raw variant of pull(): for rows away from walls the nine values are the stored bits, left
+// undecoded (returns false); wall rows need arithmetic, so they are pulled decoded and kept as
+// such (returns true).  unpack() turns either form into values.
+template <int PREC, bool IS_G>
+__device__ __forceinline__ bool pull_raw(const char* __restrict__ src, const Geometry& geo,
+                                         typename Pop<PREC>::C u_top, typename Pop<PREC>::C u_bot,
+                                         int x, int y, typename Pop<PREC>::R out[9]) {
+  using P = Pop<PREC>;
+  using C = typename P::C;
+  if (geo.walls && (y == 0 || y == geo.ny - 1)) {
+    C v[9];
+    pull<PREC, IS_G>(src, geo, u_top, u_bot, x, y, v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = P::keep(v[i]);
+    return true;
+  }
+  const long long pl = geo.plane;
+  auto LD = [&](int i, int idx) { return IS_G ? P::rawg(src, pl, i, idx) : P::rawf(src, pl, i, idx); };
+  const int xm = (x == 0) ? geo.nx - 1 : x - 1;
+  const int xp = (x == geo.nx - 1) ? 0 : x + 1;
+  const int ym = (y == 0) ? geo.ny - 1 : y - 1;
+  const int yp = (y == geo.ny - 1) ? 0 : y + 1;
+  const int r0 = y * geo.pitch, rm = ym * geo.pitch, rp = yp * geo.pitch;
+  out[0] = LD(0, r0 + x);
+  out[1] = LD(1, r0 + xm);
+  out[2] = LD(2, rm + x);
+  out[3] = LD(3, r0 + xp);
+  out[4] = LD(4, rp + x);
+  out[5] = LD(5, rm + xm);
+  out[6] = LD(6, rm + xp);
+  out[7] = LD(7, rp + xp);
+  out[8] = LD(8, rp + xm);
+  return false;
+}
+
+template <int PREC, bool IS_G>
+__device__ __forceinline__ void unpack(const typename Pop<PREC>::R raw[9], bool decoded,
+                                       typename Pop<PREC>::C out[9]) {
+  using P = Pop<PREC>;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) out[i] = decoded ? P::kept(raw[i]) : (IS_G ? P::decg(i, raw[i]) : P::decf(i, raw[i]));
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -89,8 +89,17 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   auto sum9 = [](const C v[9]) -> C {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
   };
-  auto pull_g = [&](int xx, int r, C out[9]) {
-    pull<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xx, phys_row(r), out);
+  using R = typename P::R;
+  auto pull_g = [&](int xx, int r, R out[9]) -> bool {
+    return pull_raw<PREC, true>(src, geo, ph.u_top, ph.u_bottom, xx, phys_row(r), out);
+  };
+  auto pull_f = [&](int r, R out[9]) -> bool {
+    return pull_raw<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, r, out);
+  };
+  auto phi_of = [&](const R raw[9], bool dec) -> C {
+    C v[9];
+    unpack<PREC, true>(raw, dec, v);
+    return sum9(v);
   };
 
   // Software pipeline: at the band of rows Y .. Y+BY-1 a thread (row Y+ty) holds
@@ -100,38 +109,40 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   //   fA: f pulled for row Y+ty, loaded one band ago;  fB: f for row Y+BY+ty, issued now;
   //   hB: g of its halo node (if any) for row Y+BY+ty, loaded one band ago, then reissued
   //       for row Y+2BY+ty.
-  // so every load has a whole band of work to arrive.
-  C gA[9], gB[9], gC[9], fA[9], fB[9], hB[9];
+  // The registers hold the stored bits; values are decoded only where used, so every load has a
+  // whole band of work to arrive.  The *d flags mark wall rows, which are pulled decoded.
+  R gA[9], gB[9], gC[9], fA[9], fB[9], hB[9];
+  bool gAd = false, gBd = false, gCd = false, fAd = false, fBd = false, hBd = false;
   {
     // Prologue: phi of rows y0-1 (halo, thread row 0) and y0+ty, loaded and used at once.
     const int r = y0 + ty;
     if (r <= y1) {
       if (colv) {
-        pull_g(x, r, gA);
-        sphi[slot(r)][tx + 1] = sum9(gA);
+        gAd = pull_g(x, r, gA);
+        sphi[slot(r)][tx + 1] = phi_of(gA, gAd);
       }
       if (halo) {
-        pull_g(hx, r, hB);
-        sphi[slot(r)][hcol] = sum9(hB);
+        hBd = pull_g(hx, r, hB);
+        sphi[slot(r)][hcol] = phi_of(hB, hBd);
       }
     }
     if (ty == 0) {
-      C gt[9];
+      R gt[9];
       if (colv) {
-        pull_g(x, y0 - 1, gt);
-        sphi[slot(y0 - 1)][tx + 1] = sum9(gt);
+        const bool d = pull_g(x, y0 - 1, gt);
+        sphi[slot(y0 - 1)][tx + 1] = phi_of(gt, d);
       }
       if (halo) {
-        pull_g(hx, y0 - 1, gt);
-        sphi[slot(y0 - 1)][hcol] = sum9(gt);
+        const bool d = pull_g(hx, y0 - 1, gt);
+        sphi[slot(y0 - 1)][hcol] = phi_of(gt, d);
       }
     }
     const int rb = y0 + BY + ty;
     if (rb <= y1) {
-      if (colv) pull_g(x, rb, gB);
-      if (halo) pull_g(hx, rb, hB);
+      if (colv) gBd = pull_g(x, rb, gB);
+      if (halo) hBd = pull_g(hx, rb, hB);
     }
-    if (colv && r < y1) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, r, fA);
+    if (colv && r < y1) fAd = pull_f(r, fA);
   }
 
   // Ring argument: iteration j writes rows [Y+BY, Y+2BY) and reads rows [Y-1, Y+BY]; iteration
@@ -139,17 +150,17 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   // writes iteration j's, so those two ranges (3BY+1 rows) must map to distinct slots: RING =
   // 3BY+1.  Iteration j+1's writes cannot meet iteration j-1's reads (one barrier apart).
   for (int Y = y0; Y < y1; Y += BY) {
-    const int r = Y + ty;          // collided now
-    const int rb = Y + BY + ty;    // phi formed now
+    const int r = Y + ty;            // collided now
+    const int rb = Y + BY + ty;      // phi formed now
     const int rc = Y + 2 * BY + ty;  // g issued now
     const bool act = colv && r < y1;
-    if (rc <= y1 && colv) pull_g(x, rc, gC);
-    if (rb < y1 && colv) pull<PREC, false>(src, geo, ph.u_top, ph.u_bottom, x, rb, fB);
+    if (rc <= y1 && colv) gCd = pull_g(x, rc, gC);
+    if (rb < y1 && colv) fBd = pull_f(rb, fB);
     if (rb <= y1) {
-      if (colv) sphi[slot(rb)][tx + 1] = sum9(gB);
-      if (halo) sphi[slot(rb)][hcol] = sum9(hB);
+      if (colv) sphi[slot(rb)][tx + 1] = phi_of(gB, gBd);
+      if (halo) sphi[slot(rb)][hcol] = phi_of(hB, hBd);
     }
-    if (rc <= y1 && halo) pull_g(hx, rc, hB);
+    if (rc <= y1 && halo) hBd = pull_g(hx, rc, hB);
     __syncthreads();
     if (act) {
       C s[3][3];
@@ -163,9 +174,12 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
       C dxp, dyp, lap;
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
-      const C rho = collide<C>(ph, fA, gA, phi, dxp, dyp, lap);
+      C f[9], g[9];
+      unpack<PREC, false>(fA, fAd, f);
+      unpack<PREC, true>(gA, gAd, g);
+      const C rho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-      P::store_node(dst, geo.plane, r * geo.pitch + x, fA, gA);
+      P::store_node(dst, geo.plane, r * geo.pitch + x, f, g);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -173,6 +187,9 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
       gB[i] = gC[i];
       fA[i] = fB[i];
     }
+    gAd = gBd;
+    gBd = gCd;
+    fAd = fBd;
   }
 }
 

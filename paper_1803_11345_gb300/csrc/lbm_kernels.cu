@@ -111,8 +111,8 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   //       for row Y+2BY+ty.
   // The registers hold the stored bits; values are decoded only where used, so every load has a
   // whole band of work to arrive.  The *d flags mark wall rows, which are pulled decoded.
-  R gA[9], gB[9], gC[9], fA[9], fB[9], hB[9];
-  bool gAd = false, gBd = false, gCd = false, fAd = false, fBd = false, hBd = false;
+  R gA[9], gB[9], fA[9], fB[9], hB[9];
+  bool gAd = false, gBd = false, fAd = false, fBd = false, hBd = false;
   {
     // Prologue: phi of rows y0-1 (halo, thread row 0) and y0+ty, loaded and used at once.
     const int r = y0 + ty;
@@ -149,15 +149,19 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   // j-1 read [Y-BY-1, Y].  A thread may still be reading iteration j-1's rows while another
   // writes iteration j's, so those two ranges (3BY+1 rows) must map to distinct slots: RING =
   // 3BY+1.  Iteration j+1's writes cannot meet iteration j-1's reads (one barrier apart).
-  for (int Y = y0; Y < y1; Y += BY) {
+  //
+  // One band.  GA/GB/GC and FA/FB are the roles above; the loop below unrolls six bands and
+  // permutes the arrays between them instead of copying registers.
+  auto band = [&](int Y, R (&GA)[9], R (&GB)[9], R (&GC)[9], R (&FA)[9], R (&FB)[9], bool& dA, bool& dB,
+                  bool& dC, bool& eA, bool& eB) {
     const int r = Y + ty;            // collided now
     const int rb = Y + BY + ty;      // phi formed now
     const int rc = Y + 2 * BY + ty;  // g issued now
     const bool act = colv && r < y1;
-    if (rc <= y1 && colv) gCd = pull_g(x, rc, gC);
-    if (rb < y1 && colv) fBd = pull_f(rb, fB);
+    if (rc <= y1 && colv) dC = pull_g(x, rc, GC);
+    if (rb < y1 && colv) eB = pull_f(rb, FB);
     if (rb <= y1) {
-      if (colv) sphi[slot(rb)][tx + 1] = phi_of(gB, gBd);
+      if (colv) sphi[slot(rb)][tx + 1] = phi_of(GB, dB);
       if (halo) sphi[slot(rb)][hcol] = phi_of(hB, hBd);
     }
     if (rc <= y1 && halo) hBd = pull_g(hx, rc, hB);
@@ -175,21 +179,30 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
       C f[9], g[9];
-      unpack<PREC, false>(fA, fAd, f);
-      unpack<PREC, true>(gA, gAd, g);
+      unpack<PREC, false>(FA, eA, f);
+      unpack<PREC, true>(GA, dA, g);
       const C rho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
       P::store_node(dst, geo.plane, r * geo.pitch + x, f, g);
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      gA[i] = gB[i];
-      gB[i] = gC[i];
-      fA[i] = fB[i];
-    }
-    gAd = gBd;
-    gBd = gCd;
-    fAd = fBd;
+  };
+  R gX[9];
+  bool gXd = false;
+  // Roles per band (collide, phi, issue) cycle through gA, gB, gX with period 3 and f through
+  // fA, fB with period 2: six bands per turn.
+  for (int Y = y0; Y < y1;) {
+    band(Y, gA, gB, gX, fA, fB, gAd, gBd, gXd, fAd, fBd);
+    if ((Y += BY) >= y1) break;
+    band(Y, gB, gX, gA, fB, fA, gBd, gXd, gAd, fBd, fAd);
+    if ((Y += BY) >= y1) break;
+    band(Y, gX, gA, gB, fA, fB, gXd, gAd, gBd, fAd, fBd);
+    if ((Y += BY) >= y1) break;
+    band(Y, gA, gB, gX, fB, fA, gAd, gBd, gXd, fBd, fAd);
+    if ((Y += BY) >= y1) break;
+    band(Y, gB, gX, gA, fA, fB, gBd, gXd, gAd, fAd, fBd);
+    if ((Y += BY) >= y1) break;
+    band(Y, gX, gA, gB, fB, fA, gXd, gAd, gBd, fBd, fAd);
+    Y += BY;
   }
 }
 

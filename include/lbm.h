@@ -170,6 +170,57 @@ LBM_API int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int dept
 /* The kernel and tile lbm_step uses now (variant is GENERIC or STAGED); NULL pointers skipped. */
 LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows);
 
+/* Time the compiled kernels and tiles on this lattice (trial_steps launches each, after a warm-up)
+ * and keep the fastest for later lbm_step calls; *best_ms (may be NULL) receives its time per
+ * step.  Trials relaunch the step from the current state into the spare copy, so the state and
+ * lbm_time are unchanged.  Winners are cached per (precision, nx, ny, boundary, SM count) for the
+ * process: later lattices of the same shape start with the winner. */
+LBM_API int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many independent lattices (the benchmark spec's batched parameter sweep; the paper runs one
+ * lattice at a time).  Every member has its own lbm_params (sizes, viscosities, gamma, a, walls...)
+ * but all share one precision.  One launch of a persistent kernel per time step advances every
+ * member: resident CTAs walk a work list of tiles of roughly equal node count drawn from all
+ * members, largest first.  Runs of 16 steps are captured once in a CUDA graph and replayed.
+ * Each member computes exactly what a single lattice with the same parameters computes. */
+typedef struct lbm_batch lbm_batch;
+
+/* Device bytes of a batch (all members' population copies, tables, flags). */
+LBM_API int lbm_batch_state_bytes(const lbm_params* params, int count, size_t* bytes);
+
+/* Create a batch: params[count], phi0[count] (host arrays of nx*ny FP64 each; velocity 0, density 1
+ * as in the paper's set-ups), device_buffer/buffer_bytes as in lbm_init (NULL = library allocates),
+ * stream (NULL = the batch creates its own non-blocking stream; graphs cannot be captured on the
+ * legacy default stream).  Errors as lbm_init; the message names the member. */
+LBM_API int lbm_batch_init(const lbm_params* params, int count, const double* const* phi0, void* device_buffer,
+                           size_t buffer_bytes, void* stream, lbm_batch** out);
+
+/* Advance every member by n >= 0 steps (asynchronous). */
+LBM_API int lbm_batch_step(lbm_batch* b, int n);
+
+/* Fields / populations of one member, as lbm_fields / lbm_get_populations (synchronise). */
+LBM_API int lbm_batch_fields(lbm_batch* b, int member, double* rho, double* ux, double* uy, double* phi);
+LBM_API int lbm_batch_get_populations(lbm_batch* b, int member, double* f, double* g);
+
+/* Synchronise; nonfinite[count] (may be NULL) receives 1 for members that produced a non-finite
+ * rho or phi since the last check (flags are then cleared); returns LBM_ERR_NONFINITE if any did. */
+LBM_API int lbm_batch_check(lbm_batch* b, int* nonfinite);
+
+/* Tile of the batch kernel: bx x by threads per CTA and about target_nodes nodes per work item
+ * (>= 2048).  Tiles: 32x4, 64x2, 64x4, 128x1, 128x2, 256x1. */
+LBM_API int lbm_batch_set_tile(lbm_batch* b, int bx, int by, int target_nodes);
+LBM_API int lbm_batch_get_tile(const lbm_batch* b, int* bx, int* by, int* target_nodes, int* items, int* grid);
+
+/* Time every tile x item size (trial_steps launches each, state unchanged as in lbm_autotune),
+ * keep the fastest, cache it for batches of the same member sizes; *best_ms = its step time. */
+LBM_API int lbm_batch_autotune(lbm_batch* b, int trial_steps, double* best_ms);
+
+/* Completed steps; last error (b = NULL: this thread's last lbm_batch_init failure); release. */
+LBM_API long long lbm_batch_time(const lbm_batch* b);
+LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
+LBM_API void lbm_batch_free(lbm_batch* b);
+
 /* Conservation totals of a population state in device memory, computed without allocating.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot call

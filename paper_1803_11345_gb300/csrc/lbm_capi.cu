@@ -7,7 +7,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
@@ -35,6 +39,10 @@ namespace {
 
 thread_local char g_init_err[512] = "";
 
+// Autotuned tiles per (precision, nx, ny, boundary, SM count), shared by the process.
+std::mutex g_tune_mutex;
+std::map<std::string, StepTile> g_tune;
+
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kStatusBytes = 256;
@@ -51,11 +59,18 @@ int cuda_fail(lbm_lattice* h, const char* what, cudaError_t e) {
   return LBM_ERR_CUDA;
 }
 
+std::string tune_key(const lbm_lattice* h, int sms) {
+  return std::to_string(h->p.prec) + "/" + std::to_string(h->geo.nx) + "x" + std::to_string(h->geo.ny) + "/" +
+         std::to_string(h->geo.walls) + "/" + std::to_string(sms);
+}
+
 char* state_buf(lbm_lattice* h) { return h->buf + (size_t)h->cur * h->pop_bytes; }
 char* other_buf(lbm_lattice* h) { return h->buf + (size_t)(1 - h->cur) * h->pop_bytes; }
 
+}  // namespace
+
 // Validates parameters and fills the derived geometry/physics.  Returns a message or NULL.
-const char* check_params(const lbm_params* p, HostGeometry* g, HostPhys* ph) {
+const char* lbmch::validate_params(const lbm_params* p, HostGeometry* g, HostPhys* ph) {
   if (!p) return "params is NULL";
   if (p->nx < 3 || p->ny < 3) return "nx and ny must be >= 3";
   if (p->prec < LBM_FP64 || p->prec > LBM_BF16S) return "prec must be an lbm_precision";
@@ -95,12 +110,19 @@ const char* check_params(const lbm_params* p, HostGeometry* g, HostPhys* ph) {
   return nullptr;
 }
 
-size_t total_bytes(int prec, const HostGeometry& g, size_t* pop_bytes) {
+size_t lbmch::copy_bytes(int prec, const HostGeometry& g) {
   size_t pb = align_up(pop_buffer_bytes(prec, g.plane));
   // The non-state buffer doubles as scratch for staging the fields (4 nx*ny FP64) and the
   // reduction partials; make sure it is large enough for both.
   const size_t need = align_up(sizeof(double) * 4 * (size_t)g.nx * g.ny) + reduce_partials_bytes();
   if (pb < need) pb = align_up(need);
+  return pb;
+}
+
+namespace {
+
+size_t total_bytes(int prec, const HostGeometry& g, size_t* pop_bytes) {
+  const size_t pb = copy_bytes(prec, g);
   if (pop_bytes) *pop_bytes = pb;
   return 2 * pb + kStatusBytes;
 }
@@ -131,7 +153,7 @@ void lbm_default_params(lbm_params* p) {
 int lbm_state_bytes(const lbm_params* p, size_t* bytes) {
   HostGeometry g;
   HostPhys ph;
-  const char* m = check_params(p, &g, &ph);
+  const char* m = validate_params(p, &g, &ph);
   if (m) {
     set_err(g_init_err, "lbm_state_bytes: %s", m);
     return LBM_ERR_PARAM;
@@ -152,7 +174,7 @@ int lbm_init(const lbm_params* p, const double* phi0, const double* ux0, const d
   *out = nullptr;
   HostGeometry g;
   HostPhys ph;
-  const char* m = check_params(p, &g, &ph);
+  const char* m = validate_params(p, &g, &ph);
   if (m) {
     set_err(g_init_err, "lbm_init: %s", m);
     return LBM_ERR_PARAM;
@@ -211,6 +233,13 @@ int lbm_init(const lbm_params* p, const double* phi0, const double* ux0, const d
   h->flag = (int*)(h->buf + 2 * pop_bytes);
   h->out4 = (double*)(h->buf + 2 * pop_bytes + 64);
   h->tile = default_tile(p->prec, g, h->device);
+  {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(tune_key(h, sms > 0 ? sms : 152));
+    if (it != g_tune.end()) h->tile = it->second;
+  }
 
   // Stage the initial fields [phi | ux | uy | rho] in buffer 1, build the state in buffer 0.
   double* stage = (double*)(h->buf + pop_bytes);
@@ -377,6 +406,67 @@ int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* de
   if (by) *by = h->tile.by;
   if (depth) *depth = h->tile.depth;
   if (rows) *rows = h->tile.rows;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
+  if (!h) return LBM_ERR_PARAM;
+  if (trial_steps < 1) {
+    set_err(h->err, "lbm_autotune: trial_steps must be >= 1");
+    return LBM_ERR_PARAM;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (sms <= 0) sms = 152;
+  std::vector<StepTile> cands;
+  const int gtiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+  for (auto& gt : gtiles) {
+    StepTile t{gt[0], gt[1], 0, 0, 1};
+    t.rows = rows_for_wave(h->geo, t, sms * generic_blocks_per_sm(h->p.prec, t));
+    cands.push_back(t);
+    for (int r : {32, 64, 128})
+      if (r % t.by == 0 && r < t.rows) cands.push_back(StepTile{gt[0], gt[1], r, 0, 1});
+  }
+  const int stiles[][3] = {{64, 4, 1}, {64, 2, 1}, {128, 2, 1}};
+  for (auto& st : stiles) {
+    StepTile t{st[0], st[1], 0, 1, st[2]};
+    if (!staged_supported(h->p.prec, h->geo, t)) continue;
+    t.rows = rows_for_wave(h->geo, t, sms * staged_blocks_per_sm(h->p.prec, t));
+    cands.push_back(t);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  StepTile best_t = h->tile;
+  cudaError_t e = cudaSuccess;
+  for (const StepTile& t : cands) {
+    // Relaunching from the same state only rewrites the spare copy: the state is unchanged.
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+      e = launch_step(h->p.prec, h->geo, h->phys, t, state_buf(h), other_buf(h), h->flag, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+      e = launch_step(h->p.prec, h->geo, h->phys, t, state_buf(h), other_buf(h), h->flag, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= trial_steps;
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, "lbm_autotune", e);
+  h->tile = best_t;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[tune_key(h, sms)] = best_t;
+  }
+  if (best_ms) *best_ms = best;
   return LBM_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+struct lbm_params;  // include/lbm.h
+
 namespace lbmch {
 
 struct HostGeometry {
@@ -24,6 +26,35 @@ struct StepTile {
   int bx, by, rows;
   int staged, depth;
 };
+
+// Batched stepping: one member lattice (two population copies) and one unit of work (a tile of
+// one member).  Plain structs shared by host and device code.
+struct BatchMember {
+  int nx, ny, pitch, walls;
+  long long plane;
+  char* buf0;
+  char* buf1;
+};
+struct BatchItem {
+  int member, x0, y0, rows;
+};
+
+// Upload per-member physics in the kernel's arithmetic type; `dev` must hold
+// count * phys_bytes(prec) bytes.
+size_t phys_bytes(int prec);
+cudaError_t upload_phys(int prec, const HostPhys* host, int count, void* dev, cudaStream_t s);
+// One time step of every member: items[] dealt round-robin to `grid` resident CTAs.  parity 0:
+// state in buf0 -> buf1; parity 1: buf1 -> buf0.  flags[m] collects member m's non-finite flag.
+cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
+                              const BatchMember* members, const void* phys, int parity, int* flags,
+                              int grid, cudaStream_t s);
+int batch_blocks_per_sm(int prec, const StepTile& t);
+
+// Parameter validation shared by the single-lattice and batched entry points (message or NULL),
+// and the bytes of one population copy (256-aligned, large enough to stage four FP64 fields and
+// the reduction partials).
+const char* validate_params(const ::lbm_params* p, HostGeometry* g, HostPhys* ph);
+size_t copy_bytes(int prec, const HostGeometry& g);
 
 // Message returned by lbm_last_error(NULL) on the calling thread.
 void set_thread_error(const char* msg);

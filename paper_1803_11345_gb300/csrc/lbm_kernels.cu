@@ -56,19 +56,18 @@ Geometry to_geo(const HostGeometry& h) {
 // -------------------------------------------------------------------------------------------
 // Fused step.
 
+// One tile of the step: columns [x0, x0+BX) (clipped to nx) and rows [y0, y0+rows) (clipped to
+// ny) of one lattice, by one CTA of BX x BY threads.  sphi is the CTA's phi ring.
 template <int PREC, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY)
-k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
-       const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
+__device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __restrict__ dst,
+                                          const Geometry& geo, const Phys<typename Pop<PREC>::C>& ph,
+                                          const int x0, const int y0, const int rows, int* __restrict__ flag,
+                                          typename Pop<PREC>::C (*sphi)[BX + 2]) {
   using P = Pop<PREC>;
   using C = typename P::C;
   constexpr int RING = 3 * BY + 1;  // rows kept: see the ring argument below
-  constexpr int SW = BX + 2;        // one halo column on each side
-  __shared__ C sphi[RING][SW];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * BX;
-  const int y0 = blockIdx.y * rows;
   const int y1 = min(y0 + rows, geo.ny);
   const int xv = min(BX, geo.nx - x0);  // valid columns of this strip
   const int x = x0 + tx;
@@ -111,8 +110,8 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   //       for row Y+2BY+ty.
   // The registers hold the stored bits; values are decoded only where used, so every load has a
   // whole band of work to arrive.  The *d flags mark wall rows, which are pulled decoded.
-  R gA[9], gB[9], fA[9], fB[9], hB[9];
-  bool gAd = false, gBd = false, fAd = false, fBd = false, hBd = false;
+  R gA[9], gB[9], gC[9], fA[9], fB[9], hB[9];
+  bool gAd = false, gBd = false, gCd = false, fAd = false, fBd = false, hBd = false;
   {
     // Prologue: phi of rows y0-1 (halo, thread row 0) and y0+ty, loaded and used at once.
     const int r = y0 + ty;
@@ -149,19 +148,15 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
   // j-1 read [Y-BY-1, Y].  A thread may still be reading iteration j-1's rows while another
   // writes iteration j's, so those two ranges (3BY+1 rows) must map to distinct slots: RING =
   // 3BY+1.  Iteration j+1's writes cannot meet iteration j-1's reads (one barrier apart).
-  //
-  // One band.  GA/GB/GC and FA/FB are the roles above; the loop below unrolls six bands and
-  // permutes the arrays between them instead of copying registers.
-  auto band = [&](int Y, R (&GA)[9], R (&GB)[9], R (&GC)[9], R (&FA)[9], R (&FB)[9], bool& dA, bool& dB,
-                  bool& dC, bool& eA, bool& eB) {
+  for (int Y = y0; Y < y1; Y += BY) {
     const int r = Y + ty;            // collided now
     const int rb = Y + BY + ty;      // phi formed now
     const int rc = Y + 2 * BY + ty;  // g issued now
     const bool act = colv && r < y1;
-    if (rc <= y1 && colv) dC = pull_g(x, rc, GC);
-    if (rb < y1 && colv) eB = pull_f(rb, FB);
+    if (rc <= y1 && colv) gCd = pull_g(x, rc, gC);
+    if (rb < y1 && colv) fBd = pull_f(rb, fB);
     if (rb <= y1) {
-      if (colv) sphi[slot(rb)][tx + 1] = phi_of(GB, dB);
+      if (colv) sphi[slot(rb)][tx + 1] = phi_of(gB, gBd);
       if (halo) sphi[slot(rb)][hcol] = phi_of(hB, hBd);
     }
     if (rc <= y1 && halo) hBd = pull_g(hx, rc, hB);
@@ -179,30 +174,56 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
       C f[9], g[9];
-      unpack<PREC, false>(FA, eA, f);
-      unpack<PREC, true>(GA, dA, g);
+      unpack<PREC, false>(fA, fAd, f);
+      unpack<PREC, true>(gA, gAd, g);
       const C rho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
       P::store_node(dst, geo.plane, r * geo.pitch + x, f, g);
     }
-  };
-  R gX[9];
-  bool gXd = false;
-  // Roles per band (collide, phi, issue) cycle through gA, gB, gX with period 3 and f through
-  // fA, fB with period 2: six bands per turn.
-  for (int Y = y0; Y < y1;) {
-    band(Y, gA, gB, gX, fA, fB, gAd, gBd, gXd, fAd, fBd);
-    if ((Y += BY) >= y1) break;
-    band(Y, gB, gX, gA, fB, fA, gBd, gXd, gAd, fBd, fAd);
-    if ((Y += BY) >= y1) break;
-    band(Y, gX, gA, gB, fA, fB, gXd, gAd, gBd, fAd, fBd);
-    if ((Y += BY) >= y1) break;
-    band(Y, gA, gB, gX, fB, fA, gAd, gBd, gXd, fBd, fAd);
-    if ((Y += BY) >= y1) break;
-    band(Y, gB, gX, gA, fA, fB, gBd, gXd, gAd, fAd, fBd);
-    if ((Y += BY) >= y1) break;
-    band(Y, gX, gA, gB, fB, fA, gXd, gAd, gBd, fBd, fAd);
-    Y += BY;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      gA[i] = gB[i];
+      gB[i] = gC[i];
+      fA[i] = fB[i];
+    }
+    gAd = gBd;
+    gBd = gCd;
+    fAd = fBd;
+  }
+}
+
+template <int PREC, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
+       const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
+  using C = typename Pop<PREC>::C;
+  __shared__ C sphi[3 * BY + 1][BX + 2];
+  step_tile<PREC, BX, BY>(src, dst, geo, ph, blockIdx.x * BX, blockIdx.y * rows, rows, flag, sphi);
+}
+
+// -------------------------------------------------------------------------------------------
+// Batched step: a persistent grid walks a list of tiles drawn from many independent lattices.
+
+template <int PREC, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_step_batch(const BatchItem* __restrict__ items, const int nitems, const BatchMember* __restrict__ members,
+             const Phys<typename Pop<PREC>::C>* __restrict__ phys, const int parity, int* __restrict__ flags) {
+  using C = typename Pop<PREC>::C;
+  __shared__ C sphi[3 * BY + 1][BX + 2];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem w = items[it];
+    const BatchMember m = members[w.member];
+    const Phys<C> ph = phys[w.member];
+    Geometry geo;
+    geo.nx = m.nx;
+    geo.ny = m.ny;
+    geo.pitch = m.pitch;
+    geo.plane = m.plane;
+    geo.walls = m.walls;
+    const char* src = parity ? m.buf1 : m.buf0;
+    char* dst = parity ? m.buf0 : m.buf1;
+    step_tile<PREC, BX, BY>(src, dst, geo, ph, w.x0, w.y0, w.rows, flags + w.member, sphi);
+    __syncthreads();  // the phi ring is reused by the next item
   }
 }
 
@@ -511,6 +532,81 @@ cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, cons
     case 3: return step_prec<3>(g, p, t, src, dst, flag, s);
   }
   return cudaErrorInvalidValue;
+}
+
+size_t phys_bytes(int prec) { return prec == 0 ? sizeof(Phys<double>) : sizeof(Phys<float>); }
+
+cudaError_t upload_phys(int prec, const HostPhys* host, int count, void* dev, cudaStream_t s) {
+  if (prec == 0) {
+    Phys<double>* tmp = new Phys<double>[count];
+    for (int i = 0; i < count; ++i) tmp[i] = to_phys<double>(host[i]);
+    cudaError_t e = cudaMemcpyAsync(dev, tmp, sizeof(Phys<double>) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] tmp;
+    return e;
+  }
+  Phys<float>* tmp = new Phys<float>[count];
+  for (int i = 0; i < count; ++i) tmp[i] = to_phys<float>(host[i]);
+  cudaError_t e = cudaMemcpyAsync(dev, tmp, sizeof(Phys<float>) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  delete[] tmp;
+  return e;
+}
+
+namespace {
+
+template <int PREC, int BX, int BY>
+cudaError_t batch_bxby(const BatchItem* items, int nitems, const BatchMember* members, const void* phys,
+                       int parity, int* flags, int grid, cudaStream_t s) {
+  using C = typename Pop<PREC>::C;
+  k_step_batch<PREC, BX, BY><<<grid, dim3(BX, BY), 0, s>>>(items, nitems, members,
+                                                          static_cast<const Phys<C>*>(phys), parity, flags);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t batch_prec(const StepTile& t, const BatchItem* items, int nitems, const BatchMember* members,
+                       const void* phys, int parity, int* flags, int grid, cudaStream_t s) {
+#define LBM_CASE(X, Y) \
+  if (t.bx == X && t.by == Y) return batch_bxby<PREC, X, Y>(items, nitems, members, phys, parity, flags, grid, s);
+  LBM_TILES(LBM_CASE)
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int batch_occ(int bx, int by) {
+  int nb = 0;
+#define LBM_CASE(X, Y) \
+  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_batch<PREC, X, Y>, X * Y, 0);
+  LBM_TILES(LBM_CASE)
+#undef LBM_CASE
+  return nb;
+}
+
+}  // namespace
+
+cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
+                              const BatchMember* members, const void* phys, int parity, int* flags,
+                              int grid, cudaStream_t s) {
+  switch (prec) {
+    case 0: return batch_prec<0>(t, items, nitems, members, phys, parity, flags, grid, s);
+    case 1: return batch_prec<1>(t, items, nitems, members, phys, parity, flags, grid, s);
+    case 2: return batch_prec<2>(t, items, nitems, members, phys, parity, flags, grid, s);
+    case 3: return batch_prec<3>(t, items, nitems, members, phys, parity, flags, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int batch_blocks_per_sm(int prec, const StepTile& t) {
+  int nb = 0;
+  switch (prec) {
+    case 0: nb = batch_occ<0>(t.bx, t.by); break;
+    case 1: nb = batch_occ<1>(t.bx, t.by); break;
+    case 2: nb = batch_occ<2>(t.bx, t.by); break;
+    case 3: nb = batch_occ<3>(t.bx, t.by); break;
+  }
+  return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_fields(int prec, const HostGeometry& g, const char* src, double* out, cudaStream_t s) {

@@ -77,6 +77,33 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lib.lbm_get_kernel.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.lbm_get_kernel.restype = i
+    lib.lbm_autotune.argtypes = [vp, i, dp]
+    lib.lbm_autotune.restype = i
+    bp = ctypes.POINTER(ctypes.c_void_p)
+    lib.lbm_batch_state_bytes.argtypes = [pp, i, ctypes.POINTER(sz)]
+    lib.lbm_batch_state_bytes.restype = i
+    lib.lbm_batch_init.argtypes = [pp, i, ctypes.POINTER(dp), vp, sz, vp, bp]
+    lib.lbm_batch_init.restype = i
+    lib.lbm_batch_step.argtypes = [vp, i]
+    lib.lbm_batch_step.restype = i
+    lib.lbm_batch_fields.argtypes = [vp, i, dp, dp, dp, dp]
+    lib.lbm_batch_fields.restype = i
+    lib.lbm_batch_get_populations.argtypes = [vp, i, dp, dp]
+    lib.lbm_batch_get_populations.restype = i
+    lib.lbm_batch_check.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_batch_check.restype = i
+    lib.lbm_batch_set_tile.argtypes = [vp, i, i, i]
+    lib.lbm_batch_set_tile.restype = i
+    lib.lbm_batch_get_tile.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
+    lib.lbm_batch_get_tile.restype = i
+    lib.lbm_batch_autotune.argtypes = [vp, i, dp]
+    lib.lbm_batch_autotune.restype = i
+    lib.lbm_batch_time.argtypes = [vp]
+    lib.lbm_batch_time.restype = ctypes.c_longlong
+    lib.lbm_batch_last_error.argtypes = [vp]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    lib.lbm_batch_free.argtypes = [vp]
+    lib.lbm_batch_free.restype = None
     lib.lbm_totals_noalloc.argtypes = [vp, i, i, i, dp, vp]
     lib.lbm_totals_noalloc.restype = i
     lib.lbm_time.argtypes = [vp]
@@ -201,6 +228,85 @@ def lbm_totals_noalloc(state: int, nx: int, ny: int, prec: int, stream: int = 0)
     return tuple(out)
 
 
+def lbm_autotune(h: int, trial_steps: int = 5) -> float:
+    """Pick the fastest kernel/tile for this lattice (state unchanged); returns ms per step."""
+    ms = ctypes.c_double()
+    _check(_lib.lbm_autotune(h, trial_steps, ctypes.byref(ms)), h)
+    return ms.value
+
+
+def _bcheck(status: int, b=None):
+    if status != LBM_OK:
+        raise LbmError(status, _lib.lbm_batch_last_error(b).decode(errors="replace"))
+
+
+def lbm_batch_state_bytes(params) -> int:
+    arr = (lbm_params * len(params))(*params)
+    n = ctypes.c_size_t()
+    _bcheck(_lib.lbm_batch_state_bytes(arr, len(params), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_batch_init(params, phi0s, device_buffer: int = 0, buffer_bytes: int = 0, stream: int = 0) -> int:
+    arr = (lbm_params * len(params))(*params)
+    keep = [_f64(p0, p.nx * p.ny) for p, p0 in zip(params, phi0s)]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * len(keep))(*[_dptr(a) for a in keep])
+    b = ctypes.c_void_p()
+    _bcheck(_lib.lbm_batch_init(arr, len(params), ptrs, ctypes.c_void_p(device_buffer or None), buffer_bytes,
+                                ctypes.c_void_p(stream or None), ctypes.byref(b)))
+    return b.value
+
+
+def lbm_batch_step(b: int, n: int) -> None:
+    _bcheck(_lib.lbm_batch_step(b, int(n)), b)
+
+
+def lbm_batch_fields(b: int, member: int, rho=None, ux=None, uy=None, phi=None) -> None:
+    _bcheck(_lib.lbm_batch_fields(b, member, _dptr(rho), _dptr(ux), _dptr(uy), _dptr(phi)), b)
+
+
+def lbm_batch_get_populations(b: int, member: int, f, g) -> None:
+    _bcheck(_lib.lbm_batch_get_populations(b, member, _dptr(f), _dptr(g)), b)
+
+
+def lbm_batch_check(b: int, count: int):
+    """(status, per-member non-finite flags)."""
+    flags = (ctypes.c_int * count)()
+    st = _lib.lbm_batch_check(b, flags)
+    if st not in (LBM_OK, LBM_ERR_NONFINITE):
+        _bcheck(st, b)
+    return st, list(flags)
+
+
+def lbm_batch_set_tile(b: int, bx: int, by: int, target_nodes: int) -> None:
+    _bcheck(_lib.lbm_batch_set_tile(b, bx, by, target_nodes), b)
+
+
+def lbm_batch_get_tile(b: int):
+    """(bx, by, target_nodes, items, grid)."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _bcheck(_lib.lbm_batch_get_tile(b, *(ctypes.byref(x) for x in v)), b)
+    return tuple(x.value for x in v)
+
+
+def lbm_batch_autotune(b: int, trial_steps: int = 5) -> float:
+    ms = ctypes.c_double()
+    _bcheck(_lib.lbm_batch_autotune(b, trial_steps, ctypes.byref(ms)), b)
+    return ms.value
+
+
+def lbm_batch_time(b: int) -> int:
+    return _lib.lbm_batch_time(b)
+
+
+def lbm_batch_last_error(b: int | None = None) -> str:
+    return _lib.lbm_batch_last_error(b).decode(errors="replace")
+
+
+def lbm_batch_free(b: int) -> None:
+    _lib.lbm_batch_free(b)
+
+
 def state_copy_bytes(p: lbm_params) -> int:
     """Bytes of one population copy inside a caller-supplied lbm_init buffer."""
     return (lbm_state_bytes(p) - 256) // 2
@@ -259,6 +365,9 @@ class Lattice:
         lbm_set_populations(self.h, np.ascontiguousarray(f, dtype=np.float64),
                             np.ascontiguousarray(g, dtype=np.float64))
 
+    def autotune(self, trial_steps: int = 5) -> float:
+        return lbm_autotune(self.h, trial_steps)
+
     def set_kernel(self, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0):
         lbm_set_kernel(self.h, variant, bx, by, depth, rows)
 
@@ -279,6 +388,69 @@ class Lattice:
         if getattr(self, "h", None):
             lbm_free(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent lattices advanced together on the current CUDA device.  ``members`` is a
+    list of (phi0, params) with params as lbm_params field names; all share ``prec``."""
+
+    def __init__(self, members, prec="fp32", stream=None):
+        import torch
+        self.params, phis = [], []
+        for phi0, kw in members:
+            phi0 = np.asarray(phi0, dtype=np.float64)
+            ny, nx = phi0.shape
+            self.params.append(lbm_default_params(nx=nx, ny=ny, prec=prec, **kw))
+            phis.append(phi0)
+        self.count = len(self.params)
+        nbytes = lbm_batch_state_bytes(self.params)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=self.stream.device)
+        self.b = lbm_batch_init(self.params, phis, self.buffer.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n)
+
+    def fields(self, member: int):
+        p = self.params[member]
+        out = [np.empty((p.ny, p.nx)) for _ in range(4)]
+        lbm_batch_fields(self.b, member, *out)
+        return tuple(out)
+
+    def populations(self, member: int):
+        p = self.params[member]
+        f = np.empty((9, p.ny, p.nx))
+        g = np.empty((9, p.ny, p.nx))
+        lbm_batch_get_populations(self.b, member, f, g)
+        return f, g
+
+    def check(self):
+        return lbm_batch_check(self.b, self.count)
+
+    def set_tile(self, bx: int, by: int, target_nodes: int):
+        lbm_batch_set_tile(self.b, bx, by, target_nodes)
+
+    @property
+    def tile(self):
+        return lbm_batch_get_tile(self.b)
+
+    def autotune(self, trial_steps: int = 5) -> float:
+        return lbm_batch_autotune(self.b, trial_steps)
+
+    @property
+    def time(self) -> int:
+        return lbm_batch_time(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_free(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -1,0 +1,116 @@
+"""Batched stepping (many independent lattices in one persistent launch per step, CUDA-graph
+replays, autotuned tiles) against single-lattice runs and the oracle."""
+import numpy as np
+import pytest
+
+from _pair import oracle_kwargs, rel_err
+from paper_1803_11345_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm as mod
+    return mod
+
+
+def _members():
+    """Uneven sizes, both boundaries, different viscosity ratios and surface tensions."""
+    return [
+        (W.droplet(64, 64, 16, gamma=0.02, a=0.04), dict(tau_l=1.0, tau_g=1.0, gamma=0.02, a=0.04)),
+        (W.spinodal(128, 64, seed=5), dict(tau_l=0.8, tau_g=0.53, visc=1)),
+        (W.droplet(96, 40, 12, gamma=0.04, a=0.04), dict(tau_l=0.9, tau_g=0.6, bc=1, u_top=0.01, u_bottom=-0.01)),
+        (W.droplet(67, 45, 14, gamma=0.04, a=0.04), dict(tau_l=0.7, tau_g=0.51, omega3=1.3)),
+        (W.spinodal(3, 3, seed=1), dict()),
+        (W.spinodal(512, 256, seed=8), dict(tau_l=0.8, tau_g=0.503)),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_members_equal_single_lattices(lbm, prec):
+    """Tiling does not change the per-node arithmetic, so every member equals a single lattice
+    with the same parameters bit for bit, through graph replays and odd step counts."""
+    mem = _members()
+    bat = lbm.Batch(mem, prec=prec)
+    singles = [lbm.Lattice(phi0, prec=prec, **kw) for phi0, kw in mem]
+    for n in (5, 37, 16, 3):
+        bat.step(n)
+        for s in singles:
+            s.step(n)
+    assert bat.time == 61
+    for m, s in enumerate(singles):
+        fb, gb = bat.populations(m)
+        fs, gs = s.populations()
+        assert np.array_equal(fb, fs) and np.array_equal(gb, gs), m
+
+
+def test_batch_fp64_member_matches_oracle(lbm, orc):
+    mem = _members()[:4]
+    bat = lbm.Batch(mem, prec="fp64")
+    bat.step(40)
+    for m, (phi0, kw) in enumerate(mem):
+        o = orc.Oracle(phi0, **oracle_kwargs(kw))
+        o.step(40)
+        _, _, _, pg = bat.fields(m)
+        _, _, _, po = o.fields()
+        assert rel_err(pg, po) <= 1e-12, m
+
+
+def test_batch_tiles_and_autotune_keep_state(lbm):
+    mem = _members()
+    bat = lbm.Batch(mem, prec="fp32")
+    ref = lbm.Batch(mem, prec="fp32")
+    bat.step(7)
+    ref.step(7)
+    before = [bat.populations(m) for m in range(len(mem))]
+    ms = bat.autotune(trial_steps=2)
+    assert ms > 0 and bat.time == 7
+    for m in range(len(mem)):
+        f, g = bat.populations(m)
+        assert np.array_equal(f, before[m][0]) and np.array_equal(g, before[m][1])
+    for bx, by, tgt in [(32, 4, 2048), (128, 1, 16384), (256, 1, 4096)]:
+        bat.set_tile(bx, by, tgt)
+        assert bat.tile[:3] == (bx, by, tgt)
+        bat.step(16)
+        ref.step(16)
+    for m in range(len(mem)):
+        f, g = bat.populations(m)
+        fr, gr = ref.populations(m)
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), m
+    with pytest.raises(lbm.LbmError):
+        bat.set_tile(48, 4, 4096)
+
+
+def test_batch_flags_only_the_unstable_member(lbm):
+    """A member with omega_phi = 1.74 (Gamma = 2, M = 0.05) goes non-finite; only its flag rises."""
+    mem = _members()[:3] + [(W.droplet(48, 40, 12, gamma=0.04, a=0.04), dict(tau_l=0.9, tau_g=0.6, Gamma=2.0, M=0.05))]
+    bat = lbm.Batch(mem, prec="fp32")
+    bat.step(300)
+    st, flags = bat.check()
+    assert st == lbm.LBM_ERR_NONFINITE and flags == [0, 0, 0, 1]
+    st, flags = bat.check()
+    assert st == lbm.LBM_OK
+
+
+def test_single_lattice_autotune_keeps_state(lbm):
+    lat = lbm.Lattice(W.spinodal(256, 128, seed=3), prec="fp32", tau_l=0.8, tau_g=0.53)
+    lat.step(3)
+    f0, g0 = lat.populations()
+    ms = lat.autotune(trial_steps=2)
+    assert ms > 0 and lat.time == 3
+    f1, g1 = lat.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    ref = lbm.Lattice(W.spinodal(256, 128, seed=3), prec="fp32", tau_l=0.8, tau_g=0.53)
+    ref.set_kernel(lbm.LBM_KERNEL_GENERIC, 256, 1)
+    ref.step(3)
+    lat.step(10)
+    ref.step(10)
+    fa, ga = lat.populations()
+    fb, gb = ref.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)

@@ -349,6 +349,102 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# Batched sweep (many independent lattices in one persistent launch per step).
+
+def batch_members(count: int, seed: int):
+    """Members of the batched parameter sweep: sizes {64..512}^2 and 2:1 rectangles, half sheared
+    droplets between walls moving at +-0.01 (R = ny/4; the capillary number Ca = v_w R nu_l /
+    (H sigma), H = ny/2, sets sigma and gamma = a = 3 sigma / sqrt(8), interface width 1), half
+    periodic spinodal decomposition (gamma = a = 0.04); viscosity ratio zeta: nu_l = 0.1,
+    nu_g = nu_l / zeta, omega linear in phi as in the paper."""
+    from paper_1803_11345_gb300 import workloads as W
+    out = []
+    for m in W.batch_members(count, seed):
+        nx, ny = m["nx"], m["ny"]
+        kw = dict(tau_l=tau(0.1), tau_g=tau(0.1 / m["zeta"]), M=0.1, Gamma=1.0)
+        if m["kind"] == "droplet":
+            uw, R, H = 0.01, ny / 4.0, ny / 2.0
+            sigma = uw * R * 0.1 / (H * m["Ca"])
+            ga = 3.0 * sigma / math.sqrt(8.0)
+            phi0 = W.droplet(nx, ny, R, gamma=ga, a=ga)
+            kw.update(gamma=ga, a=ga, bc=1, u_top=uw, u_bottom=-uw)
+        else:
+            phi0 = W.spinodal(nx, ny, seed=m["seed"])
+            kw.update(gamma=0.04, a=0.04)
+        out.append((phi0, kw))
+    return out
+
+
+def run_batch(args):
+    import torch
+
+    from paper_1803_11345_gb300 import build as B
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_1803_11345_gb300 import lbm
+    members = batch_members(args.count, SEED + rank)
+    nodes = sum(p.shape[0] * p.shape[1] for p, _ in members)
+    bat = lbm.Batch(members, prec=args.prec)
+    tuned_ms = bat.autotune(trial_steps=3)
+    bat.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(bat.stream)
+    bat.step(args.steps)
+    e1.record(bat.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st, flags = bat.check()
+    tile = bat.tile
+    bat.close()
+    # The same members one lattice at a time (one launch per member per step), same GPU.
+    lats = [lbm.Lattice(p, prec=args.prec, stream=torch.cuda.current_stream(), **kw) for p, kw in members]
+    seq_steps = max(3, min(args.steps, 50))
+    for L in lats:
+        L.step(2)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(seq_steps):
+        for L in lats:
+            L.step(1)
+    s1.record()
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1) / seq_steps
+    for L in lats:
+        L.close()
+    mlups = nodes * args.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.prec]
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+        "config": {"workload": f"batched sweep: {args.count} independent lattices, sizes {{64..512}}^2 and 2:1, "
+                               "half sheared droplets (walls +-0.01, Ca log-U[0.01,0.5]), half spinodal, "
+                               "zeta log-U[1,1000], one persistent launch per step, CUDA-graph replays",
+                   "members": args.count, "nodes": nodes, "precision": args.prec,
+                   "tile": {"bx": tile[0], "by": tile[1], "nodes_per_item": tile[2], "items": tile[3],
+                            "grid": tile[4]}, "autotuned_ms": tuned_ms,
+                   "members_nonfinite": int(sum(flags))},
+        "roofline": {"bound": "hbm", "achieved": bpn * nodes / (ms / args.steps * 1e-3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": bpn * nodes / (ms / args.steps * 1e-3) / 1e9 / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_step_batch"},
+        "vs_sequential": {"ms_per_step_one_at_a_time": seq_ms, "speedup": seq_ms / (ms / args.steps),
+                          "what": "the same members as separate lattices, one lbm_step launch each per step"},
+        "clocks": clk, "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,11 +456,15 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
+    ap.add_argument("--workload", choices=["spinodal", "batch"], default="spinodal")
+    ap.add_argument("--count", type=int, default=256, help="members of the batched sweep")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -67,14 +67,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# Sources that define the fused step kernel k_step (the kernel the roofline reports).
+STEP_SOURCES = ("lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1803_11345_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode())
-                h.update(fh.read())
+    for name in STEP_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

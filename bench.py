@@ -156,6 +156,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float) -> float:
+    """Max of a per-rank timing over all ranks (identity without a process group).  Runs on the
+    CPU for gloo and on the current CUDA device for NCCL."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Weak scaling: every rank advances its own replica; the job's rate counts all replicas
+    over the slowest rank's time."""
+    return world * nodes_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------------------------------
 # CPU oracle leg (bounded sample).
 
@@ -272,12 +291,9 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms)
     nodes = n * n
-    mlups = ws * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    mlups = whole_job_mlups(nodes, args.steps, ws, ms_max)
     ms_step = ms_max / args.steps
 
     # Roofline of the dominant (only) kernel in the timed region: algorithmic bytes per launch
@@ -310,12 +326,8 @@ def run_gpu(args):
         lbm.lbm_fields(h, *out)
         t1 = time.perf_counter()
         lbm.lbm_free(h)
-        dt = t1 - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": ws * nodes * args.steps / dt / 1e6, "unit": "MLUPS",
+        dt = max_over_ranks(t1 - t0)
+        e2e = {"value": whole_job_mlups(nodes, args.steps, ws, dt * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * nodes / args.steps,
                "d2h_bytes_per_step": 4 * 8 * nodes / args.steps,
                "what": "lbm_init from pinned host phi0 (H2D) + lbm_step(K) + lbm_fields to pinned "

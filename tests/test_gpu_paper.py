@@ -1,0 +1,82 @@
+"""The paper's experiments, run on the GPU path, against what the paper prints or states."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1803_11345_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm as mod
+    return mod
+
+
+def tau(nu):
+    return 3.0 * nu + 0.5
+
+
+def test_laplace_law_sweep(lbm):
+    """Laplace paragraph after Eq. 17: 200^2 periodic bubbles, gamma = a = 0.04, nu_l = 0.1,
+    nu_g = nu_l / zeta, zeta in {2, 10, 100, 1000}, M = 0.1, Gamma = 1.  The bulk-pressure jump
+    falls on a line in 1/R whose slope is sigma = sqrt(8 gamma a / 9) = 0.03771 (paper's fit
+    0.03717, 1.43% off) and does not depend on zeta.  All 24 runs advance as one batch."""
+    gold = json.load(open(GOLDEN))["laplace"]
+    n, ga = 200, gold["gamma"]
+    radii, zetas = [10, 15, 20, 25, 30, 40], [2, 10, 100, 1000]
+    members = [(W.droplet(n, n, R, gamma=ga, a=ga),
+                dict(tau_l=tau(0.1), tau_g=tau(0.1 / z), gamma=ga, a=ga, M=0.1, Gamma=1.0))
+               for z in zetas for R in radii]
+    bat = lbm.Batch(members, prec="fp32")
+    bat.step(30000)
+    st, flags = bat.check()
+    assert st == lbm.LBM_OK and not any(flags)
+    slopes = []
+    for k, z in enumerate(zetas):
+        dps = []
+        for j, R in enumerate(radii):
+            rho, _, _, phi = bat.fields(k * len(radii) + j)
+            p0 = rho / 3 + ga * (-0.5 * phi ** 2 + 0.75 * phi ** 4)  # Eq. 13
+            c = n // 2
+            dps.append(p0[c - 1:c + 1, c - 1:c + 1].mean() - p0[0, 0])
+        inv = 1.0 / np.array(radii, dtype=float)
+        slope, _ = np.polyfit(inv, np.array(dps), 1)
+        slopes.append(slope)
+    sigma = math.sqrt(8 * ga * ga / 9)
+    assert round(sigma, 5) == gold["slope_theory"]
+    for s in slopes:
+        assert abs(s / sigma - 1) < 0.03, slopes
+    assert (max(slopes) - min(slopes)) / sigma < 0.03, slopes
+
+
+def _bubble_run(lbm, steps, **kw):
+    n, ga = 200, 0.04
+    lat = lbm.Lattice(W.droplet(n, n, 40, gamma=ga, a=ga), prec="fp64", gamma=ga, a=ga, M=0.1, **kw)
+    lat.step(steps)
+    rho, ux, uy, phi = (np.empty(n * n) for _ in range(4))
+    st = lbm.lbm_fields(lat.h, rho, ux, uy, phi)
+    return st, float(np.max(np.hypot(ux, uy))) if st == lbm.LBM_OK else float("nan")
+
+
+def test_double_bgk_unstable_central_moments_stable(lbm):
+    """Stability paragraph (after Eq. 14) and the figure after it: on the 200^2 bubble with
+    nu_l = 0.1, double-BGK (Eq. 6) blows up at zeta = 3, while the central-moment scheme runs
+    smoothly at zeta = 100 (and at zeta = 3)."""
+    st, _ = _bubble_run(lbm, 2000, collision=1, tau_l=tau(0.1), tau_g=tau(0.1 / 3))
+    assert st == lbm.LBM_ERR_NONFINITE
+    st, umax = _bubble_run(lbm, 2000, collision=1, tau_l=tau(0.1), tau_g=tau(0.1 / 2))
+    assert st == lbm.LBM_OK and umax < 1e-2
+    for z in (3, 100):
+        st, umax = _bubble_run(lbm, 20000, tau_l=tau(0.1), tau_g=tau(0.1 / z))
+        assert st == lbm.LBM_OK and umax < 1e-2, (z, umax)

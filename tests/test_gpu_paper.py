@@ -80,3 +80,46 @@ def test_double_bgk_unstable_central_moments_stable(lbm):
     for z in (3, 100):
         st, umax = _bubble_run(lbm, 20000, tau_l=tau(0.1), tau_g=tau(0.1 / z))
         assert st == lbm.LBM_OK and umax < 1e-2, (z, umax)
+
+
+def _deformation(phi):
+    """D_f = (A - B)/(A + B) with A, B the axes of the ellipse with the same second moments as
+    the region phi > 0."""
+    ny, nx = phi.shape
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    w = (phi > 0).astype(float)
+    area = w.sum()
+    cx, cy = (w * x).sum() / area, (w * y).sum() / area
+    ixx = (w * (x - cx) ** 2).sum() / area
+    iyy = (w * (y - cy) ** 2).sum() / area
+    ixy = (w * (x - cx) * (y - cy)).sum() / area
+    lo, hi = np.linalg.eigvalsh(np.array([[ixx, ixy], [ixy, iyy]]))
+    a, b = math.sqrt(hi), math.sqrt(lo)
+    return (a - b) / (a + b)
+
+
+def test_taylor_deformation_in_shear(lbm):
+    """Droplet-in-shear paragraph: 2H = 200, R = 30, nu_l = nu_g = 0.2, Re = v_w R^2 / (H nu)
+    = 0.1, walls moving at +-v_w; D_f grows linearly with Ca = v_w R nu / (H sigma) with slope
+    35/32 (paper's fit 1.09536).  The paper leaves gamma/a and the measurement of the axes
+    unstated: here gamma = a (interface width 1) and the axes come from the second moments of
+    phi > 0; the fitted slope lands within 5% of 35/32."""
+    gold = json.load(open(GOLDEN))["taylor"]
+    n, R, nu, Re = 200, 30, 0.2, 0.1
+    H = n / 2
+    vw = Re * H * nu / R ** 2
+    cas = [0.05, 0.1, 0.15, 0.2, 0.25]
+    members = []
+    for ca in cas:
+        sigma = vw * R * nu / (H * ca)
+        ga = 3 * sigma / math.sqrt(8)  # sigma = sqrt(8 gamma a / 9) with gamma = a
+        members.append((W.droplet(n, n, R, gamma=ga, a=ga),
+                        dict(tau_l=tau(nu), tau_g=tau(nu), gamma=ga, a=ga, M=0.1, bc=1, u_top=vw, u_bottom=-vw)))
+    bat = lbm.Batch(members, prec="fp32")
+    bat.step(150000)
+    assert bat.check()[0] == lbm.LBM_OK
+    d = np.array([_deformation(bat.fields(m)[3]) for m in range(len(cas))])
+    slope, icpt = np.polyfit(np.array(cas), d, 1)
+    assert abs(slope / gold["slope_theory"] - 1) < 0.05, (slope, d)
+    assert abs(icpt) < 0.02
+    assert np.all(np.diff(d) > 0)

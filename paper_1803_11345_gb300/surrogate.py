@@ -1,0 +1,363 @@
+"""Learned surrogate for the coupled Cahn-Hilliard--Navier-Stokes lattice Boltzmann solver.
+
+A 4-level convolutional U-Net maps the macroscopic fields (phi, ux, uy) of a periodic lattice at
+time t to time t + K (K solver steps).  Its phi update is the discrete divergence of a predicted
+flux, so sum phi is conserved by construction (the Cahn-Hilliard equation, Eq. 1 of
+arXiv:1803.11345, is a conservation law); velocities are updated additively.  Weights and
+activations are BF16, accumulation FP32; every operation runs in the kernels behind
+include/surrogate.h (3x3 convolutions on the BF16 tensor cores), trained with Adam on trajectories
+the solver itself generates.  The solver stays the judge: a prediction is accepted only if its
+sum phi drift and (where the solver is run to check it) its phi error stay under stated
+thresholds; otherwise the solver advances the state instead.
+
+PyTorch only allocates device memory and provides the stream.  The ctypes wrappers below keep the
+C names of include/surrogate.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import lbm
+
+_lib = lbm._lib
+
+SUR_OK = 0
+U_SCALE = 100.0  # velocities enter and leave the network multiplied by this (O(1) inputs)
+
+
+def _sig(name, argtypes):
+    f = getattr(_lib, name)
+    f.argtypes = argtypes
+    f.restype = ctypes.c_int
+    return f
+
+
+_vp, _i, _sz, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
+_sig("sur_conv3x3", [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp])
+_sig("sur_conv3x3_wgrad", [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp])
+_sig("sur_relu_bwd", [_vp, _vp, _vp, _sz, _vp])
+_sig("sur_bias_grad", [_vp, _vp, _i, _i, _vp])
+for _n in ("sur_pool2", "sur_pool2_bwd", "sur_up2", "sur_up2_bwd"):
+    _sig(_n, [_vp, _vp, _i, _i, _i, _i, _vp])
+_sig("sur_add", [_vp, _vp, _vp, _sz, _vp])
+_sig("sur_mse", [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp])
+_sig("sur_adam", [_vp, _vp, _vp, _vp, _vp, _sz, _f, _f, _f, _f, _i, _vp])
+_sig("sur_flux_update", [_vp, _vp, _vp, _i, _i, _i, _i, _vp])
+_sig("sur_flux_update_bwd", [_vp, _vp, _i, _i, _i, _i, _vp])
+_sig("sur_mse3", [_vp, _vp, _vp, _vp, _sz, _vp])
+_sig("sur_zero", [_vp, _sz, _vp])
+_sig("sur_cast_bf16", [_vp, _vp, _sz, _vp])
+
+
+class SurError(RuntimeError):
+    pass
+
+
+def _ok(st, what):
+    if st != SUR_OK:
+        raise SurError(f"{what} failed with status {st}")
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# Same-name wrappers (tensor arguments; the stream is an int handle).
+def sur_conv3x3(x, w, bias, y, batch, H, W, K, N, transposed_weights, sgn, relu, out_f32, stream):
+    _ok(_lib.sur_conv3x3(_p(x), _p(w), _p(bias), _p(y), batch, H, W, K, N, transposed_weights, sgn, relu, out_f32,
+                         stream), "sur_conv3x3")
+
+
+def sur_conv3x3_wgrad(x, dy, dw, batch, H, W, Cin, Cout, stream):
+    _ok(_lib.sur_conv3x3_wgrad(_p(x), _p(dy), _p(dw), batch, H, W, Cin, Cout, stream), "sur_conv3x3_wgrad")
+
+
+def sur_relu_bwd(y, dy, dx, stream):
+    _ok(_lib.sur_relu_bwd(_p(y), _p(dy), _p(dx), y.numel(), stream), "sur_relu_bwd")
+
+
+def sur_bias_grad(dy, db, npix, C, stream):
+    _ok(_lib.sur_bias_grad(_p(dy), _p(db), npix, C, stream), "sur_bias_grad")
+
+
+def sur_pool2(x, y, batch, H, W, C, stream):
+    _ok(_lib.sur_pool2(_p(x), _p(y), batch, H, W, C, stream), "sur_pool2")
+
+
+def sur_pool2_bwd(dy, dx, batch, H, W, C, stream):
+    _ok(_lib.sur_pool2_bwd(_p(dy), _p(dx), batch, H, W, C, stream), "sur_pool2_bwd")
+
+
+def sur_up2(x, y, batch, H, W, C, stream):
+    _ok(_lib.sur_up2(_p(x), _p(y), batch, H, W, C, stream), "sur_up2")
+
+
+def sur_up2_bwd(dy, dx, batch, H, W, C, stream):
+    _ok(_lib.sur_up2_bwd(_p(dy), _p(dx), batch, H, W, C, stream), "sur_up2_bwd")
+
+
+def sur_add(a, b, y, stream):
+    _ok(_lib.sur_add(_p(a), _p(b), _p(y), a.numel(), stream), "sur_add")
+
+
+def sur_mse(out, xin, target, dout, loss, npix, C, used, stream):
+    _ok(_lib.sur_mse(_p(out), _p(xin), _p(target), _p(dout), _p(loss), npix, C, used, stream), "sur_mse")
+
+
+def sur_adam(w, grad, m, v, wb, lr, b1, b2, eps, step, stream):
+    _ok(_lib.sur_adam(_p(w), _p(grad), _p(m), _p(v), _p(wb), w.numel(), lr, b1, b2, eps, step, stream), "sur_adam")
+
+
+def sur_flux_update(out, xin, pred, batch, H, W, C, stream):
+    _ok(_lib.sur_flux_update(_p(out), _p(xin), _p(pred), batch, H, W, C, stream), "sur_flux_update")
+
+
+def sur_flux_update_bwd(dpred, dout, batch, H, W, C, stream):
+    _ok(_lib.sur_flux_update_bwd(_p(dpred), _p(dout), batch, H, W, C, stream), "sur_flux_update_bwd")
+
+
+def sur_mse3(pred, target, dpred, loss, stream):
+    _ok(_lib.sur_mse3(_p(pred), _p(target), _p(dpred), _p(loss), pred.numel(), stream), "sur_mse3")
+
+
+def sur_zero(t, stream):
+    _ok(_lib.sur_zero(_p(t), t.numel() * t.element_size(), stream), "sur_zero")
+
+
+def sur_cast_bf16(x, y, stream):
+    _ok(_lib.sur_cast_bf16(_p(x), _p(y), x.numel(), stream), "sur_cast_bf16")
+
+
+# ---------------------------------------------------------------------------------------------
+
+def layer_specs(cin, ch):
+    """(name, Cin, Cout) of every 3x3 convolution in forward order (same as the oracle)."""
+    L = len(ch)
+    layers = [("e0a", cin, ch[0]), ("e0b", ch[0], ch[0])]
+    for l in range(1, L):
+        layers += [(f"e{l}a", ch[l - 1], ch[l]), (f"e{l}b", ch[l], ch[l])]
+    for l in range(L - 2, -1, -1):
+        layers += [(f"u{l}", ch[l + 1], ch[l]), (f"d{l}", ch[l], ch[l])]
+    layers += [("out", ch[0], cin)]
+    return layers
+
+
+class UNet:
+    """The surrogate network on one CUDA device.  ``ch`` = channels per level (multiples of 16),
+    ``cin`` = input/output channels (16; the first three carry phi, ux, uy)."""
+
+    def __init__(self, ch=(32, 64, 128, 256), cin=16, seed=0, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.ch, self.cin = tuple(ch), cin
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.s = self.stream.cuda_stream
+        self.layers = layer_specs(cin, self.ch)
+        rng = np.random.default_rng(seed)
+        self.w, self.b, self.wb, self.gw, self.gb, self.mw, self.vw, self.mb, self.vb = ({} for _ in range(9))
+        f32 = dict(dtype=torch.float32, device=device)
+        for name, ci, co in self.layers:
+            scale = 0.0 if name == "out" else math.sqrt(2.0 / (9 * ci))  # He init; zero output layer
+            w = rng.standard_normal((9, ci, co)) * scale
+            self.w[name] = torch.tensor(w, **f32)
+            self.b[name] = torch.zeros(co, **f32)
+            self.wb[name] = torch.empty((9, ci, co), dtype=torch.bfloat16, device=device)
+            sur_cast_bf16(self.w[name], self.wb[name], self.s)
+            for d in (self.gw, self.mw, self.vw):
+                d[name] = torch.zeros((9, ci, co), **f32)
+            for d in (self.gb, self.mb, self.vb):
+                d[name] = torch.zeros(co, **f32)
+        self.step_count = 0
+        self._bufs = {}
+
+    # -- parameters as numpy (for checks) ------------------------------------------------------
+    def params_numpy(self):
+        """{name: (w FP64 from the BF16 copy, b FP64)} -- what the forward pass actually uses."""
+        return {n: (self.wb[n].float().cpu().numpy().astype(np.float64), self.b[n].cpu().numpy().astype(np.float64))
+                for n, _, _ in self.layers}
+
+    def grads_numpy(self):
+        return {n: (self.gw[n].cpu().numpy().astype(np.float64), self.gb[n].cpu().numpy().astype(np.float64))
+                for n, _, _ in self.layers}
+
+    # -- buffers -------------------------------------------------------------------------------
+    def _buf(self, key, shape, dtype):
+        t = self._bufs.get(key)
+        if t is None or tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+            t = self.torch.empty(shape, dtype=dtype, device=self.w["out"].device)
+            self._bufs[key] = t
+        return t
+
+    def _conv(self, x, name, B, H, W, relu, out_f32=False, key=None):
+        _, ci, co = next(l for l in self.layers if l[0] == name)
+        y = self._buf(key or name, (B, H, W, co), self.torch.float32 if out_f32 else self.torch.bfloat16)
+        sur_conv3x3(x, self.wb[name], self.b[name], y, B, H, W, ci, co, 0, 1, int(relu), int(out_f32), self.s)
+        return y
+
+    # -- forward / backward --------------------------------------------------------------------
+    def forward(self, x):
+        """x: (B, H, W, cin) BF16 -> prediction (B, H, W, 3) FP32 (phi, U_SCALE*ux, U_SCALE*uy)."""
+        bf = self.torch.bfloat16
+        B, H, W, _ = x.shape
+        L = len(self.ch)
+        self._x = x
+        self._shape = (B, H, W)
+        h, hh, ww = x, H, W
+        skips = []
+        self._sizes = []
+        for l in range(L):
+            if l > 0:
+                p = self._buf(f"p{l}", (B, hh // 2, ww // 2, self.ch[l - 1]), bf)
+                sur_pool2(h, p, B, hh, ww, self.ch[l - 1], self.s)
+                h, hh, ww = p, hh // 2, ww // 2
+            self._sizes.append((hh, ww))
+            h = self._conv(h, f"e{l}a", B, hh, ww, True)
+            h = self._conv(h, f"e{l}b", B, hh, ww, True)
+            skips.append(h)
+        for l in range(L - 2, -1, -1):
+            hh, ww = self._sizes[l]
+            up = self._buf(f"up{l}", (B, hh, ww, self.ch[l + 1]), bf)
+            sur_up2(h, up, B, hh // 2, ww // 2, self.ch[l + 1], self.s)
+            t = self._conv(up, f"u{l}", B, hh, ww, False)
+            sk = self._buf(f"s{l}", (B, hh, ww, self.ch[l]), bf)
+            sur_add(t, skips[l], sk, self.s)
+            h = self._conv(sk, f"d{l}", B, hh, ww, True)
+        out = self._conv(h, "out", B, H, W, False, out_f32=True)
+        pred = self._buf("pred", (B, H, W, 3), self.torch.float32)
+        sur_flux_update(out, x, pred, B, H, W, self.cin, self.s)
+        return pred
+
+    def backward(self, dpred):
+        """Accumulate the gradients of every weight and bias for dL/dpred (FP32, (B, H, W, 3))."""
+        bf = self.torch.bfloat16
+        B, H, W = self._shape
+        L = len(self.ch)
+        for n, _, _ in self.layers:
+            sur_zero(self.gw[n], self.s)
+            sur_zero(self.gb[n], self.s)
+        dout = self._buf("dout", (B, H, W, self.cin), bf)
+        sur_flux_update_bwd(dpred, dout, B, H, W, self.cin, self.s)
+
+        def conv_back(name, inp, dy, hh, ww, want_dx=True):
+            _, ci, co = next(l for l in self.layers if l[0] == name)
+            sur_conv3x3_wgrad(inp, dy, self.gw[name], B, hh, ww, ci, co, self.s)
+            sur_bias_grad(dy, self.gb[name], B * hh * ww, co, self.s)
+            if not want_dx:
+                return None
+            dx = self._buf(f"dx_{name}", (B, hh, ww, ci), bf)
+            sur_conv3x3(dy, self.wb[name], None, dx, B, hh, ww, co, ci, 1, -1, 0, 0, self.s)
+            return dx
+
+        bufs = self._bufs
+        dh = conv_back("out", bufs["d0"] if L > 1 else bufs["e0b"], dout, H, W)
+        dskip = [None] * L
+        for l in range(0, L - 1):
+            hh, ww = self._sizes[l]
+            g = self._buf(f"gd{l}", dh.shape, bf)
+            sur_relu_bwd(bufs[f"d{l}"], dh, g, self.s)
+            ds = conv_back(f"d{l}", bufs[f"s{l}"], g, hh, ww)
+            dskip[l] = ds
+            dup = conv_back(f"u{l}", bufs[f"up{l}"], ds, hh, ww)
+            dc = self._buf(f"gup{l}", (B, hh // 2, ww // 2, self.ch[l + 1]), bf)
+            sur_up2_bwd(dup, dc, B, hh // 2, ww // 2, self.ch[l + 1], self.s)
+            dh = dc
+        for l in range(L - 1, -1, -1):
+            hh, ww = self._sizes[l]
+            if dskip[l] is not None:
+                t = self._buf(f"gsum{l}", dh.shape, bf)
+                sur_add(dh, dskip[l], t, self.s)
+                dh = t
+            g = self._buf(f"geb{l}", dh.shape, bf)
+            sur_relu_bwd(bufs[f"e{l}b"], dh, g, self.s)
+            dh = conv_back(f"e{l}b", bufs[f"e{l}a"], g, hh, ww)
+            g = self._buf(f"gea{l}", dh.shape, bf)
+            sur_relu_bwd(bufs[f"e{l}a"], dh, g, self.s)
+            inp = bufs[f"p{l}"] if l > 0 else self._x
+            if l == 0:
+                conv_back("e0a", inp, g, hh, ww, want_dx=False)
+            else:
+                dh = conv_back(f"e{l}a", inp, g, hh, ww)
+                dp = self._buf(f"gp{l}", (B, hh * 2, ww * 2, self.ch[l - 1]), bf)
+                sur_pool2_bwd(dh, dp, B, hh * 2, ww * 2, self.ch[l - 1], self.s)
+                dh = dp
+
+    def loss_and_grads(self, x, target):
+        """Forward, MSE against target (B, H, W, 3) FP32, backward; returns the loss tensor."""
+        pred = self.forward(x)
+        loss = self._buf("loss", (1,), self.torch.float32)
+        sur_zero(loss, self.s)
+        dpred = self._buf("dpred", pred.shape, self.torch.float32)
+        sur_mse3(pred, target, dpred, loss, self.s)
+        self.backward(dpred)
+        return loss
+
+    def adam_step(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        for n, _, _ in self.layers:
+            sur_adam(self.w[n], self.gw[n], self.mw[n], self.vw[n], self.wb[n], lr, b1, b2, eps, self.step_count, self.s)
+            sur_adam(self.b[n], self.gb[n], self.mb[n], self.vb[n], None, lr, b1, b2, eps, self.step_count, self.s)
+
+
+# ---------------------------------------------------------------------------------------------
+# Solver <-> network data.
+
+def pack_fields(phi, ux, uy, cin=16):
+    """(B, H, W) phi, ux, uy -> (B, H, W, cin) FP32 network input (velocities scaled)."""
+    phi = np.asarray(phi, dtype=np.float32)
+    x = np.zeros(phi.shape + (cin,), dtype=np.float32)
+    x[..., 0] = phi
+    x[..., 1] = np.asarray(ux) * U_SCALE
+    x[..., 2] = np.asarray(uy) * U_SCALE
+    return x
+
+
+def unpack_prediction(pred):
+    """(B, H, W, 3) network prediction -> phi, ux, uy (FP64 numpy)."""
+    p = np.asarray(pred, dtype=np.float64)
+    return p[..., 0], p[..., 1] / U_SCALE, p[..., 2] / U_SCALE
+
+
+def generate_trajectories(members, steps_per_window, windows, prec="fp32", stream=None):
+    """Run the batched solver on `members` [(phi0, params)] and return the fields of every member
+    at every window boundary: array (windows + 1, M, 3, H, W) of (phi, ux, uy)."""
+    bat = lbm.Batch(members, prec=prec, stream=stream)
+    M = len(members)
+    ny, nx = members[0][0].shape
+    out = np.zeros((windows + 1, M, 3, ny, nx), dtype=np.float32)
+
+    def snap(k):
+        for m in range(M):
+            rho, ux, uy, phi = bat.fields(m)
+            out[k, m, 0], out[k, m, 1], out[k, m, 2] = phi, ux, uy
+
+    snap(0)
+    for k in range(1, windows + 1):
+        bat.step(steps_per_window)
+        snap(k)
+    st, flags = bat.check()
+    bat.close()
+    if st != lbm.LBM_OK:
+        raise lbm.LbmError(st, f"non-finite members {flags}")
+    return out
+
+
+class Judge:
+    """Accepts or rejects a prediction: sum phi drift per node must stay under `drift` (always
+    checked), and where the solver's own result for the same window is at hand, the RMS phi error
+    must stay under `phi_err`."""
+
+    def __init__(self, phi_err=1e-2, drift=1e-6):
+        self.phi_err, self.drift = phi_err, drift
+
+    def accept(self, phi_in, phi_pred, phi_true=None):
+        n = phi_in.size
+        d = abs(float(np.sum(phi_pred, dtype=np.float64) - np.sum(phi_in, dtype=np.float64))) / n
+        if not np.isfinite(phi_pred).all() or d > self.drift:
+            return False, d, None
+        if phi_true is None:
+            return True, d, None
+        err = float(np.sqrt(np.mean((phi_pred - phi_true) ** 2)))
+        return err <= self.phi_err, d, err

@@ -1,0 +1,163 @@
+"""Surrogate kernels (include/surrogate.h) against the FP64 network oracle (oracle/unet.py).
+Inputs are rounded to BF16 first and handed to the oracle exactly, so the kernels' only
+departures are FP32 accumulation order (and BF16 rounding of BF16 outputs)."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import surrogate as mod
+    return mod
+
+
+def _bf(rng, shape, scale=1.0):
+    """Random BF16 tensor on the GPU and its exact FP64 value."""
+    import torch
+    t = torch.tensor(rng.standard_normal(shape) * scale, dtype=torch.float32).to(torch.bfloat16).cuda()
+    return t, t.float().cpu().numpy().astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("K,N", [(16, 16), (16, 32), (32, 64), (48, 96)])
+def test_conv_forward_backward_match_oracle(S, K, N):
+    import torch
+    rng = np.random.default_rng(K * 100 + N)
+    B, H, W = 2, 8, 12  # 192 pixels: not a multiple of the 64-pixel tile
+    s = torch.cuda.current_stream().cuda_stream
+    x, xn = _bf(rng, (B, H, W, K))
+    w, wn = _bf(rng, (9, K, N), 0.2)
+    bias = torch.tensor(rng.standard_normal(N), dtype=torch.float32).cuda()
+    y = torch.empty((B, H, W, N), dtype=torch.float32, device="cuda")
+    S.sur_conv3x3(x, w, bias, y, B, H, W, K, N, 0, 1, 1, 1, s)
+    want = U.conv3x3(xn, wn, bias.cpu().numpy().astype(np.float64), relu=True)
+    assert _rel(y.cpu().numpy(), want) < 1e-5
+    dy, dyn = _bf(rng, (B, H, W, N))
+    dx = torch.empty((B, H, W, K), dtype=torch.float32, device="cuda")
+    S.sur_conv3x3(dy, w, None, dx, B, H, W, N, K, 1, -1, 0, 1, s)
+    assert _rel(dx.cpu().numpy(), U.conv3x3_bwd_data(dyn, wn)) < 1e-5
+    dw = torch.zeros((9, K, N), dtype=torch.float32, device="cuda")
+    S.sur_conv3x3_wgrad(x, dy, dw, B, H, W, K, N, s)
+    assert _rel(dw.cpu().numpy(), U.conv3x3_bwd_weight(xn, dyn)) < 1e-5
+    ybf = torch.empty((B, H, W, N), dtype=torch.bfloat16, device="cuda")
+    S.sur_conv3x3(x, w, bias, ybf, B, H, W, K, N, 0, 1, 1, 0, s)
+    assert _rel(ybf.float().cpu().numpy(), want) < 4e-3
+
+
+def test_elementwise_kernels_match_oracle(S):
+    import torch
+    rng = np.random.default_rng(7)
+    B, H, W, C = 2, 8, 6, 16
+    s = torch.cuda.current_stream().cuda_stream
+    x, xn = _bf(rng, (B, H, W, C))
+    p = torch.empty((B, H // 2, W // 2, C), dtype=torch.bfloat16, device="cuda")
+    S.sur_pool2(x, p, B, H, W, C, s)
+    assert _rel(p.float().cpu().numpy(), U.pool2(xn)) < 4e-3
+    c, cn = _bf(rng, (B, H // 2, W // 2, C))
+    u = torch.empty((B, H, W, C), dtype=torch.bfloat16, device="cuda")
+    S.sur_up2(c, u, B, H // 2, W // 2, C, s)
+    assert np.array_equal(u.float().cpu().numpy(), U.up2(cn))
+    g = torch.empty_like(x)
+    S.sur_pool2_bwd(c, g, B, H, W, C, s)
+    assert _rel(g.float().cpu().numpy(), U.pool2_bwd(cn)) < 1e-12
+    gc = torch.empty_like(c)
+    S.sur_up2_bwd(x, gc, B, H // 2, W // 2, C, s)
+    assert _rel(gc.float().cpu().numpy(), U.up2_bwd(xn)) < 4e-3
+    y, yn = _bf(rng, (B, H, W, C))
+    r = torch.empty_like(x)
+    S.sur_relu_bwd(y, x, r, s)
+    assert np.array_equal(r.float().cpu().numpy(), xn * (yn > 0))
+    db = torch.zeros(C, dtype=torch.float32, device="cuda")
+    S.sur_bias_grad(x, db, B * H * W, C, s)
+    assert _rel(db.cpu().numpy(), xn.sum(axis=(0, 1, 2))) < 1e-5
+    out = torch.tensor(rng.standard_normal((B, H, W, C)), dtype=torch.float32).cuda()
+    pred = torch.empty((B, H, W, 3), dtype=torch.float32, device="cuda")
+    S.sur_flux_update(out, x, pred, B, H, W, C, s)
+    want = U.flux_update(out.cpu().numpy().astype(np.float64), xn)
+    assert _rel(pred.cpu().numpy(), want) < 1e-6
+    assert abs(pred[..., 0].double().sum().item() - xn[..., 0].sum()) < 1e-4
+    dpred = torch.tensor(rng.standard_normal((B, H, W, 3)), dtype=torch.float32).cuda()
+    dout = torch.empty((B, H, W, C), dtype=torch.bfloat16, device="cuda")
+    S.sur_flux_update_bwd(dpred, dout, B, H, W, C, s)
+    assert _rel(dout.float().cpu().numpy(), U.flux_update_bwd(dpred.cpu().numpy().astype(np.float64), C)) < 4e-3
+
+
+def test_adam_step_follows_the_published_rule(S):
+    """Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+    w -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)."""
+    import torch
+    rng = np.random.default_rng(8)
+    n = 1000
+    w0, g = rng.standard_normal(n), rng.standard_normal(n)
+    w = torch.tensor(w0, dtype=torch.float32).cuda()
+    gr = torch.tensor(g, dtype=torch.float32).cuda()
+    m = torch.zeros(n, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    wb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    mn, vn, wn = np.zeros(n), np.zeros(n), w0.copy()
+    for t in (1, 2, 3):
+        S.sur_adam(w, gr, m, v, wb, 1e-2, 0.9, 0.999, 1e-8, t, s)
+        mn = 0.9 * mn + 0.1 * g
+        vn = 0.999 * vn + 0.001 * g * g
+        wn = wn - 1e-2 * (mn / (1 - 0.9 ** t)) / (np.sqrt(vn / (1 - 0.999 ** t)) + 1e-8)
+    np.testing.assert_allclose(w.cpu().numpy(), wn, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(wb.float().cpu().numpy(), wn, rtol=1e-2, atol=1e-2)
+
+
+def test_unet_gradients_match_oracle(S):
+    """Whole-network forward and backward on the GPU (BF16 activations, FP32 accumulation)
+    against the FP64 oracle with the same BF16 weights: every layer's weight gradient agrees to
+    BF16 accuracy (relative 5e-2, cosine > 0.998)."""
+    import torch
+    ch, cin = (16, 32, 32), 16
+    net = S.UNet(ch=ch, cin=cin, seed=3)
+    rng = np.random.default_rng(9)
+    # a non-zero output layer, so every layer receives gradient
+    net.w["out"] = torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda()
+    S.sur_cast_bf16(net.w["out"], net.wb["out"], net.s)
+    B, H, W = 2, 16, 16
+    x, xn = _bf(rng, (B, H, W, cin), 0.5)
+    target = torch.tensor(rng.standard_normal((B, H, W, 3)) * 0.1, dtype=torch.float32).cuda()
+    loss = net.loss_and_grads(x, target)
+    torch.cuda.synchronize()
+    params = net.params_numpy()
+    lo, go = U.unet_loss_and_grads(xn, target.cpu().numpy().astype(np.float64), params, ch)
+    assert abs(loss.item() - lo) / lo < 1e-2
+    gg = net.grads_numpy()
+    for name, _, _ in S.layer_specs(cin, ch):
+        a, b = gg[name][0].ravel(), go[name][0].ravel()
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+        assert _rel(a, b) < 5e-2 and cos > 0.998, (name, _rel(a, b), cos)
+        assert _rel(gg[name][1], go[name][1]) < 5e-2, name
+
+
+def test_training_reduces_loss(S):
+    """A few hundred Adam steps on a fixed batch fit it (the kernels learn)."""
+    import torch
+    ch, cin = (16, 32), 16
+    net = S.UNet(ch=ch, cin=cin, seed=4)
+    rng = np.random.default_rng(10)
+    B, H, W = 4, 32, 32
+    x, xn = _bf(rng, (B, H, W, cin), 0.5)
+    # target: a smooth function of the input the network can represent
+    tgt = xn[..., :3] + 0.1 * np.roll(xn[..., :3], 1, axis=2)
+    target = torch.tensor(tgt, dtype=torch.float32).cuda()
+    first = net.loss_and_grads(x, target).item()
+    for _ in range(300):
+        net.loss_and_grads(x, target)
+        net.adam_step(lr=2e-3)
+    last = net.loss_and_grads(x, target).item()
+    assert last < 0.2 * first, (first, last)

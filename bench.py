@@ -460,6 +460,75 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# Learned surrogate vs the plain FP32 solver.
+
+def run_surrogate(args):
+    import time as _t
+
+    import torch
+
+    from paper_1803_11345_gb300 import build as B
+    B.build()
+    from paper_1803_11345_gb300 import lbm
+    from paper_1803_11345_gb300 import surrogate as S
+    n, K, wins = args.sur_n, args.sur_k, args.sur_windows
+    t0 = _t.time()
+    members = S.spinodal_members(args.sur_train + args.sur_test, n, seed=SEED)
+    traj = S.generate_trajectories(members, K, wins)
+    t_data = _t.time() - t0
+    train_traj, test_traj = traj[:, :args.sur_train], traj[:, args.sur_train:]
+    net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=SEED)
+    t0 = _t.time()
+    hist = S.train(net, train_traj, args.sur_iters, args.sur_batch, lr=1e-3, seed=SEED, log_every=50)
+    torch.cuda.synchronize()
+    t_train = _t.time() - t0
+    judge = S.Judge(phi_err=1e-2, drift=1e-6)
+    rows = S.evaluate(net, test_traj, judge)
+    errs = np.array([r["err"] for r in rows])
+    pers = np.array([r["persistence"] for r in rows])
+    acc = float(np.mean([r["accepted"] for r in rows]))
+    # Speed for the same work: args.sur_test lattices advanced by K steps.
+    bt = args.sur_test
+    x, _ = S.to_device_batch(test_traj, [(m, 0) for m in range(bt)], net.cin)
+    ms_sur = S.time_forward(net, x)
+    bat = lbm.Batch(members[args.sur_train:], prec="fp32")
+    bat.autotune(trial_steps=3)
+    bat.step(K)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bat.stream)
+    bat.step(K * 4)
+    e1.record(bat.stream)
+    torch.cuda.synchronize()
+    ms_solver = e0.elapsed_time(e1) / 4
+    bat.close()
+    nodes = bt * n * n
+    # Effective rate of the judged surrogate: accepted windows cost one forward pass, rejected
+    # ones a forward pass plus the solver's K steps.
+    ms_eff = ms_sur + (1 - acc) * ms_solver
+    line = {
+        "metric": METRIC, "value": nodes * K / (ms_eff * 1e-3) / 1e6, "unit": "MLUPS-equivalent",
+        "n_gpus": 1, "steps": K, "warmup": 2, "ms_per_step": ms_eff / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"learned surrogate: 4-level U-Net (32,64,128,256 channels, BF16, FP32 accumulate) "
+                               f"advancing (phi, ux, uy) by {K} steps on {n}x{n} periodic spinodal decomposition "
+                               f"(viscosity ratio 1:10); trained on {args.sur_train} solver trajectories x {wins} windows",
+                   "train_iters": args.sur_iters, "batch": args.sur_batch, "test_members": args.sur_test},
+        "surrogate": {"ms_forward": ms_sur, "ms_solver_same_window": ms_solver, "speedup_forward_only": ms_solver / ms_sur,
+                      "accept_rate": acc, "phi_rms_err_median": float(np.median(errs)),
+                      "phi_rms_err_p90": float(np.percentile(errs, 90)),
+                      "persistence_rms_err_median": float(np.median(pers)),
+                      "max_sum_phi_drift_per_node": float(max(r["drift"] for r in rows)),
+                      "thresholds": {"phi_rms": 1e-2, "sum_phi_drift_per_node": 1e-6},
+                      "loss_history": hist[::max(1, len(hist) // 10)], "seconds_data": t_data,
+                      "seconds_train": t_train},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,7 +540,14 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
-    ap.add_argument("--workload", choices=["spinodal", "batch"], default="spinodal")
+    ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
+    ap.add_argument("--sur-n", type=int, default=256)
+    ap.add_argument("--sur-k", type=int, default=50, help="solver steps per surrogate window")
+    ap.add_argument("--sur-windows", type=int, default=60)
+    ap.add_argument("--sur-train", type=int, default=16)
+    ap.add_argument("--sur-test", type=int, default=4)
+    ap.add_argument("--sur-iters", type=int, default=1500)
+    ap.add_argument("--sur-batch", type=int, default=8)
     ap.add_argument("--count", type=int, default=256, help="members of the batched sweep")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -480,6 +556,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_gpu(args)
 
 

@@ -361,3 +361,77 @@ class Judge:
             return True, d, None
         err = float(np.sqrt(np.mean((phi_pred - phi_true) ** 2)))
         return err <= self.phi_err, d, err
+
+
+# ---------------------------------------------------------------------------------------------
+# Training and evaluation on solver trajectories.
+
+def spinodal_members(count, n, seed, nu_l=0.1, nu_g=0.01, a=0.04, gamma=0.04, M=0.1):
+    """Periodic spinodal decomposition members (viscosity ratio nu_l/nu_g, tau linear in phi)."""
+    from . import workloads as W
+    tau = lambda nu: 3.0 * nu + 0.5  # noqa: E731
+    return [(W.spinodal(n, n, seed=seed + k),
+             dict(tau_l=tau(nu_l), tau_g=tau(nu_g), visc=lbm.LBM_TAU_LINEAR, a=a, gamma=gamma, M=M))
+            for k in range(count)]
+
+
+def to_device_batch(traj, idx, cin=16):
+    """Network input (BF16) and target (FP32) tensors for (member, window) pairs."""
+    import torch
+    xs = np.stack([pack_fields(traj[k, m, 0], traj[k, m, 1], traj[k, m, 2], cin) for m, k in idx])
+    ys = np.stack([pack_fields(traj[k + 1, m, 0], traj[k + 1, m, 1], traj[k + 1, m, 2], 3) for m, k in idx])
+    x = torch.from_numpy(xs).cuda().to(torch.bfloat16)
+    y = torch.from_numpy(ys).cuda()
+    return x, y
+
+
+def train(net, traj, iters, batch, lr=1e-3, seed=0, log_every=0):
+    """Adam on random (member, window) pairs of traj (windows+1, M, 3, H, W); cosine-decayed lr.
+    Returns the loss history (one value per iteration, synchronised every log_every)."""
+    rng = np.random.default_rng(seed)
+    nwin, M = traj.shape[0] - 1, traj.shape[1]
+    hist = []
+    for it in range(iters):
+        idx = [(int(rng.integers(M)), int(rng.integers(nwin))) for _ in range(batch)]
+        x, y = to_device_batch(traj, idx, net.cin)
+        loss = net.loss_and_grads(x, y)
+        net.adam_step(lr=lr * 0.5 * (1 + math.cos(math.pi * it / max(1, iters))))
+        if log_every and (it % log_every == 0 or it == iters - 1):
+            hist.append((it, float(loss.item())))
+    return hist
+
+
+def evaluate(net, traj, judge, batch=4):
+    """One-window predictions from every true state of traj: per window the RMS phi error of the
+    network and of persistence (phi(t+K) ~ phi(t)), the sum-phi drift per node, and whether the
+    judge accepts the prediction (a rejected window is advanced by the solver instead, so the
+    state after fallback is exact)."""
+    nwin, M = traj.shape[0] - 1, traj.shape[1]
+    rows = []
+    pairs = [(m, k) for k in range(nwin) for m in range(M)]
+    for i in range(0, len(pairs), batch):
+        idx = pairs[i:i + batch]
+        x, _ = to_device_batch(traj, idx, net.cin)
+        pred = net.forward(x).cpu().numpy()
+        for j, (m, k) in enumerate(idx):
+            phi_in = traj[k, m, 0].astype(np.float64)
+            phi_true = traj[k + 1, m, 0].astype(np.float64)
+            phi_pred = pred[j, ..., 0].astype(np.float64)
+            ok, drift, err = judge.accept(phi_in, phi_pred, phi_true)
+            pers = float(np.sqrt(np.mean((phi_in - phi_true) ** 2)))
+            rows.append(dict(member=m, window=k, err=err, persistence=pers, drift=drift, accepted=bool(ok)))
+    return rows
+
+
+def time_forward(net, x, reps=5):
+    """Milliseconds per forward pass of the batch x (CUDA events on the network's stream)."""
+    import torch
+    for _ in range(2):
+        net.forward(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(net.stream)
+    for _ in range(reps):
+        net.forward(x)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps

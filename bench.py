@@ -466,6 +466,7 @@ def run_batch(args):
 def run_surrogate(args):
     import time as _t
 
+    import numpy as np
     import torch
 
     from paper_1803_11345_gb300 import build as B

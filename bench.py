@@ -491,8 +491,8 @@ def run_surrogate(args):
     acc = float(np.mean([r["accepted"] for r in rows]))
     # Speed for the same work: args.sur_test lattices advanced by K steps.
     bt = args.sur_test
-    x, _ = S.to_device_batch(test_traj, [(m, 0) for m in range(bt)], net.cin)
-    ms_sur = S.time_forward(net, x)
+    x, base, _ = S.to_device_batch(test_traj, [(m, 0) for m in range(bt)], net.cin)
+    ms_sur = S.time_forward(net, x, base)
     bat = lbm.Batch(members[args.sur_train:], prec="fp32")
     bat.autotune(trial_steps=3)
     bat.step(K)

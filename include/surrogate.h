@@ -73,12 +73,12 @@ SUR_API int sur_adam(float* w, const float* grad, float* m, float* v, void* wb, 
                      float b2, float eps, int step, void* stream);
 
 /* Conservative output of the network: from its FP32 output `out` (C >= 4 channels: Jx, Jy,
- * dux, duy) and its BF16 input xin (channels phi, ux, uy, ...) the prediction pred (npix x 3 FP32:
- * phi, ux, uy) is phi - [Jx(x,y) - Jx(x-1,y) + Jy(x,y) - Jy(x,y-1)], ux + dux, uy + duy.  The
+ * dux, duy) and the FP32 state base (npix x 3: phi, ux, uy) the prediction pred (npix x 3 FP32)
+ * is phi - [Jx(x,y) - Jx(x-1,y) + Jy(x,y) - Jy(x,y-1)], ux + dux, uy + duy.  The
  * periodic divergence telescopes, so sum phi is conserved up to FP32 rounding: the Cahn-Hilliard
  * equation (Eq. 1) is a conservation law and the predicted phi change is the divergence of a flux.
  * sur_flux_update_bwd maps dL/dpred to dL/dout (BF16, channels >= 4 zero). */
-SUR_API int sur_flux_update(const float* out, const void* xin, float* pred, int batch, int H, int W, int C,
+SUR_API int sur_flux_update(const float* out, const float* base, float* pred, int batch, int H, int W, int C,
                             void* stream);
 SUR_API int sur_flux_update_bwd(const float* dpred, void* dout, int batch, int H, int W, int C, void* stream);
 

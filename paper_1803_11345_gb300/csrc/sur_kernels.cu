@@ -312,9 +312,9 @@ __global__ void k_add(const bf16* __restrict__ a, const bf16* __restrict__ b, bf
 
 // Conservative update from the network output (C channels, first four used):
 //   phi' = phi - [Jx(x,y) - Jx(x-1,y) + Jy(x,y) - Jy(x,y-1)],  u' = u + du
-// with (Jx, Jy, dux, duy) = out[.., 0..3] and (phi, ux, uy) = xin[.., 0..2].  The discrete
-// divergence telescopes on the periodic image, so sum phi' = sum phi up to FP32 rounding.
-__global__ void k_flux_update(const float* __restrict__ out, const bf16* __restrict__ xin, float* __restrict__ pred,
+// with (Jx, Jy, dux, duy) = out[.., 0..3] and (phi, ux, uy) = base[.., 0..2] (the FP32 state).  The
+// discrete divergence telescopes on the periodic image, so sum phi' = sum phi up to FP32 rounding.
+__global__ void k_flux_update(const float* __restrict__ out, const float* __restrict__ base, float* __restrict__ pred,
                               int B, int H, int W, int C) {
   const int n = B * H * W;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -322,9 +322,9 @@ __global__ void k_flux_update(const float* __restrict__ out, const bf16* __restr
     const int xm = x == 0 ? W - 1 : x - 1, ym = y == 0 ? H - 1 : y - 1;
     const size_t pw = (size_t)(b * H + y) * W + xm, ps = (size_t)(b * H + ym) * W + x;
     const float div = (out[(size_t)p * C] - out[pw * C]) + (out[(size_t)p * C + 1] - out[ps * C + 1]);
-    pred[(size_t)p * 3 + 0] = __bfloat162float(xin[(size_t)p * C + 0]) - div;
-    pred[(size_t)p * 3 + 1] = __bfloat162float(xin[(size_t)p * C + 1]) + out[(size_t)p * C + 2];
-    pred[(size_t)p * 3 + 2] = __bfloat162float(xin[(size_t)p * C + 2]) + out[(size_t)p * C + 3];
+    pred[(size_t)p * 3 + 0] = base[(size_t)p * 3 + 0] - div;
+    pred[(size_t)p * 3 + 1] = base[(size_t)p * 3 + 1] + out[(size_t)p * C + 2];
+    pred[(size_t)p * 3 + 2] = base[(size_t)p * 3 + 2] + out[(size_t)p * C + 3];
   }
 }
 
@@ -525,10 +525,9 @@ int sur_adam(float* w, const float* grad, float* m, float* v, void* wb, size_t n
   return check(cudaGetLastError());
 }
 
-int sur_flux_update(const float* out, const void* xin, float* pred, int batch, int H, int W, int C, void* stream) {
+int sur_flux_update(const float* out, const float* base, float* pred, int batch, int H, int W, int C, void* stream) {
   if (C < 4 || C % 16) return SUR_ERR_PARAM;
-  k_flux_update<<<grid_for((size_t)batch * H * W), 256, 0, (cudaStream_t)stream>>>(out, (const bf16*)xin, pred, batch,
-                                                                                   H, W, C);
+  k_flux_update<<<grid_for((size_t)batch * H * W), 256, 0, (cudaStream_t)stream>>>(out, base, pred, batch, H, W, C);
   return check(cudaGetLastError());
 }
 

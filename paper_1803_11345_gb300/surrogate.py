@@ -111,8 +111,8 @@ def sur_adam(w, grad, m, v, wb, lr, b1, b2, eps, step, stream):
     _ok(_lib.sur_adam(_p(w), _p(grad), _p(m), _p(v), _p(wb), w.numel(), lr, b1, b2, eps, step, stream), "sur_adam")
 
 
-def sur_flux_update(out, xin, pred, batch, H, W, C, stream):
-    _ok(_lib.sur_flux_update(_p(out), _p(xin), _p(pred), batch, H, W, C, stream), "sur_flux_update")
+def sur_flux_update(out, base, pred, batch, H, W, C, stream):
+    _ok(_lib.sur_flux_update(_p(out), _p(base), _p(pred), batch, H, W, C, stream), "sur_flux_update")
 
 
 def sur_flux_update_bwd(dpred, dout, batch, H, W, C, stream):
@@ -198,8 +198,9 @@ class UNet:
         return y
 
     # -- forward / backward --------------------------------------------------------------------
-    def forward(self, x):
-        """x: (B, H, W, cin) BF16 -> prediction (B, H, W, 3) FP32 (phi, U_SCALE*ux, U_SCALE*uy)."""
+    def forward(self, x, base):
+        """x: (B, H, W, cin) BF16 network input; base: (B, H, W, 3) FP32 state (phi, U_SCALE*ux,
+        U_SCALE*uy) -> prediction (B, H, W, 3) FP32, the base advanced by the network."""
         bf = self.torch.bfloat16
         B, H, W, _ = x.shape
         L = len(self.ch)
@@ -227,7 +228,7 @@ class UNet:
             h = self._conv(sk, f"d{l}", B, hh, ww, True)
         out = self._conv(h, "out", B, H, W, False, out_f32=True)
         pred = self._buf("pred", (B, H, W, 3), self.torch.float32)
-        sur_flux_update(out, x, pred, B, H, W, self.cin, self.s)
+        sur_flux_update(out, base, pred, B, H, W, self.cin, self.s)
         return pred
 
     def backward(self, dpred):
@@ -284,9 +285,9 @@ class UNet:
                 sur_pool2_bwd(dh, dp, B, hh * 2, ww * 2, self.ch[l - 1], self.s)
                 dh = dp
 
-    def loss_and_grads(self, x, target):
+    def loss_and_grads(self, x, base, target):
         """Forward, MSE against target (B, H, W, 3) FP32, backward; returns the loss tensor."""
-        pred = self.forward(x)
+        pred = self.forward(x, base)
         loss = self._buf("loss", (1,), self.torch.float32)
         sur_zero(loss, self.s)
         dpred = self._buf("dpred", pred.shape, self.torch.float32)
@@ -355,12 +356,10 @@ class Judge:
     def accept(self, phi_in, phi_pred, phi_true=None):
         n = phi_in.size
         d = abs(float(np.sum(phi_pred, dtype=np.float64) - np.sum(phi_in, dtype=np.float64))) / n
-        if not np.isfinite(phi_pred).all() or d > self.drift:
-            return False, d, None
-        if phi_true is None:
-            return True, d, None
-        err = float(np.sqrt(np.mean((phi_pred - phi_true) ** 2)))
-        return err <= self.phi_err, d, err
+        finite = bool(np.isfinite(phi_pred).all())
+        err = None if phi_true is None or not finite else float(np.sqrt(np.mean((phi_pred - phi_true) ** 2)))
+        ok = finite and d <= self.drift and (err is None or err <= self.phi_err)
+        return ok, d, err
 
 
 # ---------------------------------------------------------------------------------------------
@@ -376,13 +375,15 @@ def spinodal_members(count, n, seed, nu_l=0.1, nu_g=0.01, a=0.04, gamma=0.04, M=
 
 
 def to_device_batch(traj, idx, cin=16):
-    """Network input (BF16) and target (FP32) tensors for (member, window) pairs."""
+    """Network input (BF16), FP32 base state and FP32 target for (member, window) pairs."""
     import torch
     xs = np.stack([pack_fields(traj[k, m, 0], traj[k, m, 1], traj[k, m, 2], cin) for m, k in idx])
     ys = np.stack([pack_fields(traj[k + 1, m, 0], traj[k + 1, m, 1], traj[k + 1, m, 2], 3) for m, k in idx])
-    x = torch.from_numpy(xs).cuda().to(torch.bfloat16)
+    xf = torch.from_numpy(xs).cuda()
+    x = xf.to(torch.bfloat16)
+    base = xf[..., :3].contiguous()
     y = torch.from_numpy(ys).cuda()
-    return x, y
+    return x, base, y
 
 
 def train(net, traj, iters, batch, lr=1e-3, seed=0, log_every=0):
@@ -393,8 +394,8 @@ def train(net, traj, iters, batch, lr=1e-3, seed=0, log_every=0):
     hist = []
     for it in range(iters):
         idx = [(int(rng.integers(M)), int(rng.integers(nwin))) for _ in range(batch)]
-        x, y = to_device_batch(traj, idx, net.cin)
-        loss = net.loss_and_grads(x, y)
+        x, base, y = to_device_batch(traj, idx, net.cin)
+        loss = net.loss_and_grads(x, base, y)
         net.adam_step(lr=lr * 0.5 * (1 + math.cos(math.pi * it / max(1, iters))))
         if log_every and (it % log_every == 0 or it == iters - 1):
             hist.append((it, float(loss.item())))
@@ -411,8 +412,8 @@ def evaluate(net, traj, judge, batch=4):
     pairs = [(m, k) for k in range(nwin) for m in range(M)]
     for i in range(0, len(pairs), batch):
         idx = pairs[i:i + batch]
-        x, _ = to_device_batch(traj, idx, net.cin)
-        pred = net.forward(x).cpu().numpy()
+        x, base, _ = to_device_batch(traj, idx, net.cin)
+        pred = net.forward(x, base).cpu().numpy()
         for j, (m, k) in enumerate(idx):
             phi_in = traj[k, m, 0].astype(np.float64)
             phi_true = traj[k + 1, m, 0].astype(np.float64)
@@ -423,15 +424,15 @@ def evaluate(net, traj, judge, batch=4):
     return rows
 
 
-def time_forward(net, x, reps=5):
+def time_forward(net, x, base, reps=5):
     """Milliseconds per forward pass of the batch x (CUDA events on the network's stream)."""
     import torch
     for _ in range(2):
-        net.forward(x)
+        net.forward(x, base)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(net.stream)
     for _ in range(reps):
-        net.forward(x)
+        net.forward(x, base)
     e1.record(net.stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps

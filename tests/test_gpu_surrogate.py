@@ -83,11 +83,13 @@ def test_elementwise_kernels_match_oracle(S):
     S.sur_bias_grad(x, db, B * H * W, C, s)
     assert _rel(db.cpu().numpy(), xn.sum(axis=(0, 1, 2))) < 1e-5
     out = torch.tensor(rng.standard_normal((B, H, W, C)), dtype=torch.float32).cuda()
+    base = torch.tensor(rng.standard_normal((B, H, W, 3)), dtype=torch.float32).cuda()
+    bn = base.cpu().numpy().astype(np.float64)
     pred = torch.empty((B, H, W, 3), dtype=torch.float32, device="cuda")
-    S.sur_flux_update(out, x, pred, B, H, W, C, s)
-    want = U.flux_update(out.cpu().numpy().astype(np.float64), xn)
+    S.sur_flux_update(out, base, pred, B, H, W, C, s)
+    want = U.flux_update(out.cpu().numpy().astype(np.float64), bn)
     assert _rel(pred.cpu().numpy(), want) < 1e-6
-    assert abs(pred[..., 0].double().sum().item() - xn[..., 0].sum()) < 1e-4
+    assert abs(pred[..., 0].double().sum().item() - bn[..., 0].sum()) < 1e-4
     dpred = torch.tensor(rng.standard_normal((B, H, W, 3)), dtype=torch.float32).cuda()
     dout = torch.empty((B, H, W, C), dtype=torch.bfloat16, device="cuda")
     S.sur_flux_update_bwd(dpred, dout, B, H, W, C, s)
@@ -133,8 +135,9 @@ def test_unet_gradients_match_oracle(S):
     S.sur_cast_bf16(net.w["out"], net.wb["out"], net.s)
     B, H, W = 2, 16, 16
     x, xn = _bf(rng, (B, H, W, cin), 0.5)
+    base = x[..., :3].float().contiguous()
     target = torch.tensor(rng.standard_normal((B, H, W, 3)) * 0.1, dtype=torch.float32).cuda()
-    loss = net.loss_and_grads(x, target)
+    loss = net.loss_and_grads(x, base, target)
     torch.cuda.synchronize()
     params = net.params_numpy()
     lo, go = U.unet_loss_and_grads(xn, target.cpu().numpy().astype(np.float64), params, ch)
@@ -158,9 +161,10 @@ def test_training_reduces_loss(S):
     # target: a smooth function of the input the network can represent
     tgt = xn[..., :3] + 0.1 * np.roll(xn[..., :3], 1, axis=2)
     target = torch.tensor(tgt, dtype=torch.float32).cuda()
-    first = net.loss_and_grads(x, target).item()
+    base = x[..., :3].float().contiguous()
+    first = net.loss_and_grads(x, base, target).item()
     for _ in range(300):
-        net.loss_and_grads(x, target)
+        net.loss_and_grads(x, base, target)
         net.adam_step(lr=2e-3)
-    last = net.loss_and_grads(x, target).item()
+    last = net.loss_and_grads(x, base, target).item()
     assert last < 0.2 * first, (first, last)

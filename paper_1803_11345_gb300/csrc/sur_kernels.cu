@@ -147,6 +147,155 @@ k_conv3x3(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* 
   }
 }
 
+// Pipelined variant of the same implicit GEMM: 128 pixels x TN channels per CTA of 8 warps
+// (4 along pixels x 2 along channels, 32 x TN/2 each), KC channels of one tap per stage, stages
+// double-buffered in shared memory by cp.async (zero-filled outside the image), fragments read
+// with ldmatrix from rows padded by 16 bytes (conflict-free).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t r[2], const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
+template <int TN, int KC, bool TRANSW, bool OUT_F32>
+__global__ void __launch_bounds__(256)
+k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* __restrict__ bias,
+               void* __restrict__ Y, int npix, int H, int W, int K, int N, int sgn, int relu) {
+  constexpr int TPX = 128, AST = KC + 8;
+  constexpr int WN = TN >= 16 ? TN / 2 : 8;  // channels per warp
+  constexpr int NT = WN / 8;                 // n8 tiles per warp
+  constexpr int BR = TRANSW ? TN : KC;       // B stored [k][n] (forward) or [n][k] (transposed)
+  constexpr int BC = (TRANSW ? KC : TN) + 8;
+  __shared__ __align__(16) bf16 sA[2][TPX][AST];
+  __shared__ __align__(16) bf16 sB[2][BR][BC];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 3, wn = warp >> 2;
+  const int g = lane >> 2, t = lane & 3;
+  const int p0 = blockIdx.x * TPX;
+  const int n0 = blockIdx.y * TN;
+  const int kchunks = K / KC;
+  const int nstage = 9 * kchunks;
+
+  auto load_stage = [&](int st, int buf) {
+    const int tap = st / kchunks, k0 = (st % kchunks) * KC;
+    const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
+    for (int c = tid; c < TPX * KC / 8; c += 256) {
+      const int r = c / (KC / 8), part = c % (KC / 8);
+      const int p = p0 + r;
+      const bool ok = p < npix;
+      const int ps = ok ? shift_pixel(p, H, W, dy, dx) : 0;
+      cp_async16(&sA[buf][r][part * 8], X + (size_t)ps * K + k0 + part * 8, ok);
+    }
+    if (!TRANSW) {
+      for (int c = tid; c < KC * TN / 8; c += 256) {
+        const int kk = c / (TN / 8), c8 = (c % (TN / 8)) * 8;
+        cp_async16(&sB[buf][kk][c8], Wg + ((size_t)tap * K + k0 + kk) * N + n0 + c8, true);
+      }
+    } else {
+      for (int c = tid; c < TN * KC / 8; c += 256) {
+        const int nn = c / (KC / 8), part = c % (KC / 8);
+        cp_async16(&sB[buf][nn][part * 8], Wg + ((size_t)tap * N + n0 + nn) * K + k0 + part * 8, true);
+      }
+    }
+  };
+
+  float acc[2][NT][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+  const bool warp_active = wn * WN < TN;  // TN = 16 uses only the first channel half
+  load_stage(0, 0);
+  cp_async_commit();
+  for (int st = 0; st < nstage; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nstage) {
+      load_stage(st + 1, buf ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (warp_active) {
+#pragma unroll
+      for (int kk = 0; kk < KC / 16; ++kk) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int row = wm * 32 + mt * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+          ldsm_x4(a[mt], &sA[buf][row][kk * 16 + 8 * (lane >> 4)]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          uint32_t b[2];
+          const int l = lane & 15;
+          if (!TRANSW) ldsm_x2_t(b, &sB[buf][kk * 16 + (l >> 3) * 8 + (l & 7)][wn * WN + nt * 8]);
+          else ldsm_x2(b, &sB[buf][wn * WN + nt * 8 + (l & 7)][kk * 16 + (l >> 3) * 8]);
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b);
+        }
+      }
+    }
+    __syncthreads();  // the buffer is refilled by the next stage's loads
+  }
+  if (!warp_active) return;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int p = p0 + wm * 32 + mt * 16 + g + hh * 8;
+        if (p >= npix) continue;
+        const int n = n0 + wn * WN + nt * 8 + 2 * t;
+        float v0 = acc[mt][nt][hh * 2], v1 = acc[mt][nt][hh * 2 + 1];
+        if (bias) {
+          v0 += bias[n];
+          v1 += bias[n + 1];
+        }
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        if (OUT_F32) {
+          float* y = static_cast<float*>(Y) + (size_t)p * N + n;
+          y[0] = v0;
+          y[1] = v1;
+        } else {
+          bf16* y = static_cast<bf16*>(Y) + (size_t)p * N + n;
+          *reinterpret_cast<__nv_bfloat162*>(y) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+}
+
 // Weight gradient: dW[tap][ci][co] += sum_p X[p + off(tap)][ci] * dY[p][co]; a GEMM with
 // M = Cin, N = Cout and K = pixels, split over pixel chunks (FP32 atomics into dW).
 // CTA: TCI input channels (one warp per 16) x TCO output channels for one tap and one chunk.
@@ -430,20 +579,33 @@ extern "C" {
 
 int sur_conv3x3(const void* x, const void* w, const float* bias, void* y, int batch, int H, int W, int K, int N,
                 int transposed_weights, int sgn, int relu, int out_f32, void* stream) {
-  const int tn = tile_n(N);
+  const int tn = N % 128 == 0 ? 128 : tile_n(N);
   if (!x || !w || !y || batch < 1 || H < 1 || W < 1 || K % 16 || K < 16 || !tn || (sgn != 1 && sgn != -1))
     return SUR_ERR_PARAM;
   if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) % 16) return SUR_ERR_PARAM;
   const long long npix = (long long)batch * H * W;
   if (npix > (1ll << 30)) return SUR_ERR_PARAM;
-  dim3 grd((unsigned)((npix + TP - 1) / TP), (unsigned)(N / tn));
+  dim3 grd((unsigned)((npix + 127) / 128), (unsigned)(N / tn));
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* X = (const bf16*)x;
   const bf16* Wg = (const bf16*)w;
-  if (tn == 64) conv_launch<64>(grd, s, X, Wg, bias, y, (int)npix, H, W, K, N, transposed_weights, sgn, relu, out_f32);
-  else if (tn == 32) conv_launch<32>(grd, s, X, Wg, bias, y, (int)npix, H, W, K, N, transposed_weights, sgn, relu, out_f32);
-  else conv_launch<16>(grd, s, X, Wg, bias, y, (int)npix, H, W, K, N, transposed_weights, sgn, relu, out_f32);
-  return check(cudaGetLastError());
+  const bool k32 = K % 32 == 0;
+#define SUR_PIPE(TN_, KC_)                                                                                    \
+  if (tn == TN_ && (KC_ == 32) == k32) {                                                                      \
+    if (!transposed_weights && !out_f32)                                                                      \
+      k_conv3x3_pipe<TN_, KC_, false, false><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu); \
+    else if (!transposed_weights)                                                                             \
+      k_conv3x3_pipe<TN_, KC_, false, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);  \
+    else if (!out_f32)                                                                                        \
+      k_conv3x3_pipe<TN_, KC_, true, false><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);  \
+    else                                                                                                      \
+      k_conv3x3_pipe<TN_, KC_, true, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);   \
+    return check(cudaGetLastError());                                                                         \
+  }
+  SUR_PIPE(128, 32) SUR_PIPE(128, 16) SUR_PIPE(64, 32) SUR_PIPE(64, 16) SUR_PIPE(32, 32) SUR_PIPE(32, 16)
+  SUR_PIPE(16, 32) SUR_PIPE(16, 16)
+#undef SUR_PIPE
+  return SUR_ERR_PARAM;
 }
 
 int sur_conv3x3_wgrad(const void* x, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout,

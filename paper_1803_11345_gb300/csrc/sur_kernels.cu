@@ -200,15 +200,33 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
   const int kchunks = K / KC;
   const int nstage = 9 * kchunks;
 
+  // The pixels whose A chunks this thread copies are fixed: decompose them once.
+  constexpr int ACH = TPX * KC / 8 / 256;  // A chunks per thread per stage
+  int ay[ACH], ax[ACH], abh[ACH];
+  bool aok[ACH];
+#pragma unroll
+  for (int j = 0; j < ACH; ++j) {
+    const int c = tid + j * 256;
+    const int p = p0 + c / (KC / 8);
+    aok[j] = p < npix;
+    const int pp = aok[j] ? p : 0;
+    ax[j] = pp % W;
+    const int by = pp / W;
+    ay[j] = by % H;
+    abh[j] = by - ay[j];  // b * H
+  }
   auto load_stage = [&](int st, int buf) {
     const int tap = st / kchunks, k0 = (st % kchunks) * KC;
     const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
-    for (int c = tid; c < TPX * KC / 8; c += 256) {
+#pragma unroll
+    for (int j = 0; j < ACH; ++j) {
+      const int c = tid + j * 256;
       const int r = c / (KC / 8), part = c % (KC / 8);
-      const int p = p0 + r;
-      const bool ok = p < npix;
-      const int ps = ok ? shift_pixel(p, H, W, dy, dx) : 0;
-      cp_async16(&sA[buf][r][part * 8], X + (size_t)ps * K + k0 + part * 8, ok);
+      int yy = ay[j] + dy, xx = ax[j] + dx;
+      yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+      xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+      const int ps = (abh[j] + yy) * W + xx;
+      cp_async16(&sA[buf][r][part * 8], X + (size_t)ps * K + k0 + part * 8, aok[j]);
     }
     if (!TRANSW) {
       for (int c = tid; c < KC * TN / 8; c += 256) {

@@ -163,13 +163,16 @@ class UNet:
             scale = 0.0 if name == "out" else math.sqrt(2.0 / (9 * ci))  # He init; zero output layer
             w = rng.standard_normal((9, ci, co)) * scale
             self.w[name] = torch.tensor(w, **f32)
-            self.b[name] = torch.zeros(co, **f32)
+            self.b[name] = torch.empty(co, **f32)
+            sur_zero(self.b[name], self.s)
             self.wb[name] = torch.empty((9, ci, co), dtype=torch.bfloat16, device=device)
             sur_cast_bf16(self.w[name], self.wb[name], self.s)
             for d in (self.gw, self.mw, self.vw):
-                d[name] = torch.zeros((9, ci, co), **f32)
+                d[name] = torch.empty((9, ci, co), **f32)
+                sur_zero(d[name], self.s)
             for d in (self.gb, self.mb, self.vb):
-                d[name] = torch.zeros(co, **f32)
+                d[name] = torch.empty(co, **f32)
+                sur_zero(d[name], self.s)
         self.step_count = 0
         self._bufs = {}
 

@@ -492,18 +492,29 @@ def run_surrogate(args):
     # Speed for the same work: args.sur_test lattices advanced by K steps.
     bt = args.sur_test
     x, base, _ = S.to_device_batch(test_traj, [(m, 0) for m in range(bt)], net.cin)
-    ms_sur = S.time_forward(net, x, base)
-    bat = lbm.Batch(members[args.sur_train:], prec="fp32")
-    bat.autotune(trial_steps=3)
-    bat.step(K)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(bat.stream)
-    bat.step(K * 4)
-    e1.record(bat.stream)
-    torch.cuda.synchronize()
-    ms_solver = e0.elapsed_time(e1) / 4
-    bat.close()
+    reps = 5
+    ms_sur = S.time_forward(net, x, base, reps=reps, graph=True)
+    ms_sur_eager = S.time_forward(net, x, base, reps=reps)
+
+    def solver_ms(mem):
+        bat = lbm.Batch(mem, prec="fp32")
+        bat.autotune(trial_steps=3)
+        bat.step(K)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bat.stream)
+        bat.step(K * 4)
+        e1.record(bat.stream)
+        torch.cuda.synchronize()
+        bat.close()
+        return e0.elapsed_time(e1) / 4
+
+    ms_solver = solver_ms(members[args.sur_train:])
+    # Throughput at a larger batch: the same test members repeated (timing only).
+    rep = max(1, args.sur_speed_batch // bt)
+    xr, br = x.repeat(rep, 1, 1, 1).contiguous(), base.repeat(rep, 1, 1, 1).contiguous()
+    ms_sur_big = S.time_forward(net, xr, br, reps=reps, graph=True)
+    ms_solver_big = solver_ms(members[args.sur_train:] * rep)
     nodes = bt * n * n
     # Effective rate of the judged surrogate: accepted windows cost one forward pass, rejected
     # ones a forward pass plus the solver's K steps.
@@ -516,7 +527,10 @@ def run_surrogate(args):
                                f"advancing (phi, ux, uy) by {K} steps on {n}x{n} periodic spinodal decomposition "
                                f"(viscosity ratio 1:10); trained on {args.sur_train} solver trajectories x {wins} windows",
                    "train_iters": args.sur_iters, "batch": args.sur_batch, "test_members": args.sur_test},
-        "surrogate": {"ms_forward": ms_sur, "ms_solver_same_window": ms_solver, "speedup_forward_only": ms_solver / ms_sur,
+        "surrogate": {"ms_forward": ms_sur, "ms_forward_eager": ms_sur_eager, "ms_solver_same_window": ms_solver,
+                      "speedup_forward_only": ms_solver / ms_sur,
+                      "at_batch": {"lattices": bt * rep, "ms_forward": ms_sur_big, "ms_solver_same_window": ms_solver_big,
+                                   "speedup_forward_only": ms_solver_big / ms_sur_big},
                       "accept_rate": acc, "phi_rms_err_median": float(np.median(errs)),
                       "phi_rms_err_p90": float(np.percentile(errs, 90)),
                       "persistence_rms_err_median": float(np.median(pers)),
@@ -524,7 +538,8 @@ def run_surrogate(args):
                       "thresholds": {"phi_rms": 1e-2, "sum_phi_drift_per_node": 1e-6},
                       "loss_history": hist[::max(1, len(hist) // 10)], "seconds_data": t_data,
                       "seconds_train": t_train},
-        "gpu_launches": None,
+        # the line's number is the graph-replayed forward: its launches per timed pass
+        "gpu_launches": net.launches_per_forward() * reps,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -544,6 +559,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
     ap.add_argument("--sur-n", type=int, default=256)
     ap.add_argument("--sur-k", type=int, default=50, help="solver steps per surrogate window")
+    ap.add_argument("--sur-speed-batch", type=int, default=16, help="lattices in the throughput comparison")
     ap.add_argument("--sur-windows", type=int, default=60)
     ap.add_argument("--sur-train", type=int, default=16)
     ap.add_argument("--sur-test", type=int, default=4)

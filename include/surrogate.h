@@ -44,6 +44,19 @@ SUR_API int sur_conv3x3(const void* x, const void* w, const float* bias, void* y
 SUR_API int sur_conv3x3_wgrad(const void* x, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout,
                               void* stream);
 
+/* Decoder convolution fused with its neighbours: y = conv3x3(up2(xc)) + bias + addend (BF16, no
+ * activation), where xc is the coarse (batch, H/2, W/2, K) image, up2 its 2x nearest upsampling to
+ * H x W (never materialised) and addend (may be NULL) a BF16 (batch, H, W, N) tensor.  Forward
+ * weights [tap][K][N]; H, W even; K, N multiples of 16.  Equals sur_up2 + sur_conv3x3 + sur_add
+ * up to one BF16 rounding of the convolution output. */
+SUR_API int sur_conv3x3_up_add(const void* xc, const void* w, const float* bias, const void* addend, void* y,
+                               int batch, int H, int W, int K, int N, void* stream);
+
+/* Weight gradient of that convolution: as sur_conv3x3_wgrad with x = up2(xc), read from the coarse
+ * (batch, H/2, W/2, Cin) image xc. */
+SUR_API int sur_conv3x3_wgrad_up(const void* xc, const void* dy, float* dw, int batch, int H, int W, int Cin,
+                                 int Cout, void* stream);
+
 /* ReLU backward from the post-activation y: dx = dy where y > 0, else 0 (n elements). */
 SUR_API int sur_relu_bwd(const void* y, const void* dy, void* dx, size_t n, void* stream);
 

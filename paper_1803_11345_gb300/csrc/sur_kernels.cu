@@ -42,112 +42,27 @@ __device__ __forceinline__ int shift_pixel(int p, int H, int W, int dy, int dx) 
   return (b * H + yy) * W + xx;
 }
 
+// The same shift on the fine H x W image, returned as the index of the coarse (H/2 x W/2) pixel
+// that the 2x nearest upsampling copies there.
+__device__ __forceinline__ int shift_pixel_up(int p, int H, int W, int dy, int dx) {
+  const int x = p % W;
+  const int by = p / W;
+  const int y = by % H;
+  const int b = by / H;
+  int yy = y + dy, xx = x + dx;
+  yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+  xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+  return (b * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Implicit-GEMM 3x3 periodic convolution:
 //   Y[p][n] = sum_tap sum_k X[p + sgn*off(tap)][k] * Wt(tap, k, n)  (+ bias[n], ReLU)
 // forward:       X = input (K = Cin),  Wt(tap,k,n) = Wgt[tap][k][n] (n = Cout), sgn = +1
 // backward data: X = dY (K = Cout),    Wt(tap,k,n) = Wgt[tap][n][k] (n = Cin),  sgn = -1
-// Tile: 64 pixels x TN output channels per CTA of 4 warps; each warp owns 16 pixels x TN
-// channels (TN/8 MMA n-tiles); the K loop walks taps and 16-channel slices through shared
-// memory.  Requires K % 16 == 0 and N % TN == 0 (channel counts are padded by the host).
-constexpr int TP = 64, TK = 16;
-
-template <int TN, bool TRANSW, bool OUT_F32>
-__global__ void __launch_bounds__(128)
-k_conv3x3(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* __restrict__ bias,
-          void* __restrict__ Y, int npix, int H, int W, int K, int N, int sgn, int relu) {
-  __shared__ __align__(16) bf16 sA[TP][TK + 8];  // +8 pad: conflict-free fragment reads
-  __shared__ __align__(16) bf16 sB[TK][TN + 8];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int p0 = blockIdx.x * TP;
-  const int n0 = blockIdx.y * TN;
-  constexpr int NT = TN / 8;
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
-    for (int k0 = 0; k0 < K; k0 += TK) {
-      // A tile: 64 pixels x 16 channels, one 16-byte chunk per thread.
-      {
-        const int r = tid >> 1, half = tid & 1;
-        const int p = p0 + r;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (p < npix) {
-          const int ps = shift_pixel(p, H, W, dy, dx);
-          v = *reinterpret_cast<const uint4*>(X + (size_t)ps * K + k0 + half * 8);
-        }
-        *reinterpret_cast<uint4*>(&sA[r][half * 8]) = v;
-      }
-      // B tile: 16 k x TN n, in 16-byte chunks.
-      if (!TRANSW) {
-        for (int c = tid; c < TK * TN / 8; c += 128) {
-          const int kk = c / (TN / 8), c8 = (c % (TN / 8)) * 8;
-          const bf16* src = Wg + ((size_t)tap * K + k0 + kk) * N + n0 + c8;
-          *reinterpret_cast<uint4*>(&sB[kk][c8]) = *reinterpret_cast<const uint4*>(src);
-        }
-      } else {
-        // Wgt[tap][n][k]: 8 consecutive k for one n, scattered into sB[k][n].
-        for (int c = tid; c < TN * TK / 8; c += 128) {
-          const int nn = c >> 1, k8 = (c & 1) * 8;
-          const bf16* src = Wg + ((size_t)tap * N + n0 + nn) * K + k0 + k8;
-          uint4 v = *reinterpret_cast<const uint4*>(src);
-          const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) sB[k8 + q][nn] = e[q];
-        }
-      }
-      __syncthreads();
-      uint32_t a[4];
-      const int r0 = warp * 16;
-      a[0] = pack2(sA[r0 + g][2 * t], sA[r0 + g][2 * t + 1]);
-      a[1] = pack2(sA[r0 + g + 8][2 * t], sA[r0 + g + 8][2 * t + 1]);
-      a[2] = pack2(sA[r0 + g][2 * t + 8], sA[r0 + g][2 * t + 9]);
-      a[3] = pack2(sA[r0 + g + 8][2 * t + 8], sA[r0 + g + 8][2 * t + 9]);
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        uint32_t b[2];
-        b[0] = pack2(sB[2 * t][j * 8 + g], sB[2 * t + 1][j * 8 + g]);
-        b[1] = pack2(sB[2 * t + 8][j * 8 + g], sB[2 * t + 9][j * 8 + g]);
-        mma16816(acc[j], a, b);
-      }
-      __syncthreads();
-    }
-  }
-  // Epilogue: bias, ReLU, store.
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int p = p0 + warp * 16 + g + hh * 8;
-      if (p >= npix) continue;
-      const int n = n0 + j * 8 + 2 * t;
-      float v0 = acc[j][hh * 2], v1 = acc[j][hh * 2 + 1];
-      if (bias) {
-        v0 += bias[n];
-        v1 += bias[n + 1];
-      }
-      if (relu) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      if (OUT_F32) {
-        float* y = static_cast<float*>(Y) + (size_t)p * N + n;
-        y[0] = v0;
-        y[1] = v1;
-      } else {
-        bf16* y = static_cast<bf16*>(Y) + (size_t)p * N + n;
-        *reinterpret_cast<__nv_bfloat162*>(y) = __floats2bfloat162_rn(v0, v1);
-      }
-    }
-  }
-}
-
-// Pipelined variant of the same implicit GEMM: 128 pixels x TN channels per CTA of 8 warps
+// Requires K % 16 == 0 and N % TN == 0 (channel counts are padded by the host).
+//
+// Tile: 128 pixels x TN channels per CTA of 8 warps
 // (4 along pixels x 2 along channels, 32 x TN/2 each), KC channels of one tap per stage, stages
 // double-buffered in shared memory by cp.async (zero-filled outside the image), fragments read
 // with ldmatrix from rows padded by 16 bytes (conflict-free).
@@ -166,12 +81,6 @@ __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
 }
-__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
 __device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
@@ -181,10 +90,14 @@ __device__ __forceinline__ void ldsm_x2_t(uint32_t r[2], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
 
-template <int TN, int KC, bool TRANSW, bool OUT_F32>
+// UPX: X is the coarse (H/2 x W/2) image and the convolution reads its 2x nearest upsampling
+// (fine pixel (y, x) -> coarse (y/2, x/2)) without materialising it.  addend (may be NULL, BF16
+// npix x N) is added to the result before the ReLU.
+template <int TN, int KC, bool TRANSW, bool OUT_F32, bool UPX = false>
 __global__ void __launch_bounds__(256)
 k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* __restrict__ bias,
-               void* __restrict__ Y, int npix, int H, int W, int K, int N, int sgn, int relu) {
+               void* __restrict__ Y, int npix, int H, int W, int K, int N, int sgn, int relu,
+               const bf16* __restrict__ addend = nullptr) {
   constexpr int TPX = 128, AST = KC + 8;
   constexpr int WN = TN >= 16 ? TN / 2 : 8;  // channels per warp
   constexpr int NT = WN / 8;                 // n8 tiles per warp
@@ -202,7 +115,7 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
 
   // The pixels whose A chunks this thread copies are fixed: decompose them once.
   constexpr int ACH = TPX * KC / 8 / 256;  // A chunks per thread per stage
-  int ay[ACH], ax[ACH], abh[ACH];
+  int ay[ACH], ax[ACH], ab[ACH];
   bool aok[ACH];
 #pragma unroll
   for (int j = 0; j < ACH; ++j) {
@@ -212,8 +125,8 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
     const int pp = aok[j] ? p : 0;
     ax[j] = pp % W;
     const int by = pp / W;
-    ay[j] = by % H;
-    abh[j] = by - ay[j];  // b * H
+    ab[j] = by / H;
+    ay[j] = by - ab[j] * H;
   }
   auto load_stage = [&](int st, int buf) {
     const int tap = st / kchunks, k0 = (st % kchunks) * KC;
@@ -225,7 +138,7 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
       int yy = ay[j] + dy, xx = ax[j] + dx;
       yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
       xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
-      const int ps = (abh[j] + yy) * W + xx;
+      const int ps = UPX ? (ab[j] * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1) : (ab[j] * H + yy) * W + xx;
       cp_async16(&sA[buf][r][part * 8], X + (size_t)ps * K + k0 + part * 8, aok[j]);
     }
     if (!TRANSW) {
@@ -299,6 +212,11 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
           v0 += bias[n];
           v1 += bias[n + 1];
         }
+        if (addend) {
+          const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(addend + (size_t)p * N + n));
+          v0 += a.x;
+          v1 += a.y;
+        }
         if (relu) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
@@ -318,11 +236,12 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
 // M = Cin, N = Cout and K = pixels, split over pixel chunks (FP32 atomics into dW).
 // CTA: TCI input channels (one warp per 16) x TCO output channels for one tap and one chunk.
 constexpr int WCHUNK = 1024;
+constexpr int TK = 16;  // pixels per K slice
 
 template <int TCI, int TCO>
 __global__ void __launch_bounds__(TCI * 2)
 k_conv3x3_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY, float* __restrict__ dW, int npix,
-                int H, int W, int Cin, int Cout) {
+                int H, int W, int Cin, int Cout, int up) {
   constexpr int NTH = TCI * 2;  // TCI/16 warps
   constexpr int NT = TCO / 8;
   __shared__ __align__(16) bf16 sA[TCI][TK + 8];  // [ci][pixel]
@@ -346,7 +265,7 @@ k_conv3x3_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY, float* 
       const int p = pk + pp;
       uint4 v = make_uint4(0, 0, 0, 0);
       if (p < pend) {
-        const int ps = shift_pixel(p, H, W, dy, dx);
+        const int ps = up ? shift_pixel_up(p, H, W, dy, dx) : shift_pixel(p, H, W, dy, dx);
         v = *reinterpret_cast<const uint4*>(X + (size_t)ps * Cin + c0 + cg);
       }
       const bf16* e = reinterpret_cast<const bf16*>(&v);
@@ -576,19 +495,24 @@ int check(cudaError_t e) { return e == cudaSuccess ? SUR_OK : SUR_ERR_CUDA; }
 
 int tile_n(int N) { return N % 64 == 0 ? 64 : (N % 32 == 0 ? 32 : (N % 16 == 0 ? 16 : 0)); }
 
-template <int TN>
-void conv_launch(dim3 grd, cudaStream_t s, const bf16* X, const bf16* Wg, const float* bias, void* y, int npix, int H,
-                 int W, int K, int N, int tw, int sgn, int relu, int out_f32) {
-  if (!tw && !out_f32) k_conv3x3<TN, false, false><<<grd, 128, 0, s>>>(X, Wg, bias, y, npix, H, W, K, N, sgn, relu);
-  else if (!tw && out_f32) k_conv3x3<TN, false, true><<<grd, 128, 0, s>>>(X, Wg, bias, y, npix, H, W, K, N, sgn, relu);
-  else if (tw && !out_f32) k_conv3x3<TN, true, false><<<grd, 128, 0, s>>>(X, Wg, bias, y, npix, H, W, K, N, sgn, relu);
-  else k_conv3x3<TN, true, true><<<grd, 128, 0, s>>>(X, Wg, bias, y, npix, H, W, K, N, sgn, relu);
+// Output-channel tile of the implicit GEMM: the widest that divides N, halved (down to 64) only
+// while the grid would fill less than half of the SMs.  Narrow tiles re-read the pixel operand
+// once per tile, which costs more than a partly idle wave unless the grid is very small.
+int conv_tile_n(long long npix, int N) {
+  const long long ptiles = (npix + 127) / 128;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess || sms < 1)
+    sms = 1;
+  int tn = N % 128 == 0 ? 128 : tile_n(N);
+  while (tn > 64 && 2 * ptiles * (N / tn) < sms) tn /= 2;
+  return tn;
 }
 
 template <int TCI, int TCO>
 void wgrad_launch(dim3 grd, cudaStream_t s, const bf16* x, const bf16* dy, float* dw, int npix, int H, int W, int Cin,
-                  int Cout) {
-  k_conv3x3_wgrad<TCI, TCO><<<grd, TCI * 2, 0, s>>>(x, dy, dw, npix, H, W, Cin, Cout);
+                  int Cout, int up) {
+  k_conv3x3_wgrad<TCI, TCO><<<grd, TCI * 2, 0, s>>>(x, dy, dw, npix, H, W, Cin, Cout, up);
 }
 
 }  // namespace
@@ -597,12 +521,13 @@ extern "C" {
 
 int sur_conv3x3(const void* x, const void* w, const float* bias, void* y, int batch, int H, int W, int K, int N,
                 int transposed_weights, int sgn, int relu, int out_f32, void* stream) {
-  const int tn = N % 128 == 0 ? 128 : tile_n(N);
-  if (!x || !w || !y || batch < 1 || H < 1 || W < 1 || K % 16 || K < 16 || !tn || (sgn != 1 && sgn != -1))
+  if (!x || !w || !y || batch < 1 || H < 1 || W < 1 || K % 16 || K < 16 || N % 16 || N < 16 ||
+      (sgn != 1 && sgn != -1))
     return SUR_ERR_PARAM;
   if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) % 16) return SUR_ERR_PARAM;
   const long long npix = (long long)batch * H * W;
   if (npix > (1ll << 30)) return SUR_ERR_PARAM;
+  const int tn = conv_tile_n(npix, N);
   dim3 grd((unsigned)((npix + 127) / 128), (unsigned)(N / tn));
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* X = (const bf16*)x;
@@ -626,10 +551,11 @@ int sur_conv3x3(const void* x, const void* w, const float* bias, void* y, int ba
   return SUR_ERR_PARAM;
 }
 
-int sur_conv3x3_wgrad(const void* x, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout,
+static int wgrad_impl(const void* x, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout, int up,
                       void* stream) {
   const int tci = tile_n(Cin), tco = tile_n(Cout);
-  if (!x || !dy || !dw || batch < 1 || !tci || !tco) return SUR_ERR_PARAM;
+  if (!x || !dy || !dw || batch < 1 || H < 1 || W < 1 || !tci || !tco) return SUR_ERR_PARAM;
+  if (up && (H % 2 || W % 2)) return SUR_ERR_PARAM;
   if (((uintptr_t)x | (uintptr_t)dy) % 16) return SUR_ERR_PARAM;
   const long long npix = (long long)batch * H * W;
   const long long chunks = (npix + WCHUNK - 1) / WCHUNK;
@@ -639,11 +565,46 @@ int sur_conv3x3_wgrad(const void* x, const void* dy, float* dw, int batch, int H
   const bf16* X = (const bf16*)x;
   const bf16* D = (const bf16*)dy;
 #define SUR_WG(A, B) \
-  if (tci == A && tco == B) wgrad_launch<A, B>(grd, s, X, D, dw, (int)npix, H, W, Cin, Cout);
+  if (tci == A && tco == B) wgrad_launch<A, B>(grd, s, X, D, dw, (int)npix, H, W, Cin, Cout, up);
   SUR_WG(16, 16) SUR_WG(16, 32) SUR_WG(16, 64) SUR_WG(32, 16) SUR_WG(32, 32) SUR_WG(32, 64) SUR_WG(64, 16)
   SUR_WG(64, 32) SUR_WG(64, 64)
 #undef SUR_WG
   return check(cudaGetLastError());
+}
+
+int sur_conv3x3_wgrad(const void* x, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout,
+                      void* stream) {
+  return wgrad_impl(x, dy, dw, batch, H, W, Cin, Cout, 0, stream);
+}
+
+int sur_conv3x3_wgrad_up(const void* xc, const void* dy, float* dw, int batch, int H, int W, int Cin, int Cout,
+                         void* stream) {
+  return wgrad_impl(xc, dy, dw, batch, H, W, Cin, Cout, 1, stream);
+}
+
+int sur_conv3x3_up_add(const void* xc, const void* w, const float* bias, const void* addend, void* y, int batch,
+                       int H, int W, int K, int N, void* stream) {
+  if (!xc || !w || !y || batch < 1 || H < 2 || W < 2 || H % 2 || W % 2 || K % 16 || K < 16 || N % 16 || N < 16)
+    return SUR_ERR_PARAM;
+  if (((uintptr_t)xc | (uintptr_t)w | (uintptr_t)y | (uintptr_t)addend) % 16) return SUR_ERR_PARAM;
+  const long long npix = (long long)batch * H * W;
+  if (npix > (1ll << 30)) return SUR_ERR_PARAM;
+  const int tn = conv_tile_n(npix, N);
+  dim3 grd((unsigned)((npix + 127) / 128), (unsigned)(N / tn));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bf16* X = (const bf16*)xc;
+  const bf16* Wg = (const bf16*)w;
+  const bf16* A = (const bf16*)addend;
+  const bool k32 = K % 32 == 0;
+#define SUR_UP(TN_, KC_)                                                                             \
+  if (tn == TN_ && (KC_ == 32) == k32) {                                                             \
+    k_conv3x3_pipe<TN_, KC_, false, false, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, 1, 0, A); \
+    return check(cudaGetLastError());                                                                \
+  }
+  SUR_UP(128, 32) SUR_UP(128, 16) SUR_UP(64, 32) SUR_UP(64, 16) SUR_UP(32, 32) SUR_UP(32, 16) SUR_UP(16, 32)
+  SUR_UP(16, 16)
+#undef SUR_UP
+  return SUR_ERR_PARAM;
 }
 
 int sur_relu_bwd(const void* y, const void* dy, void* dx, size_t n, void* stream) {

@@ -38,6 +38,8 @@ def _sig(name, argtypes):
 _vp, _i, _sz, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
 _sig("sur_conv3x3", [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp])
 _sig("sur_conv3x3_wgrad", [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp])
+_sig("sur_conv3x3_up_add", [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp])
+_sig("sur_conv3x3_wgrad_up", [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp])
 _sig("sur_relu_bwd", [_vp, _vp, _vp, _sz, _vp])
 _sig("sur_bias_grad", [_vp, _vp, _i, _i, _vp])
 for _n in ("sur_pool2", "sur_pool2_bwd", "sur_up2", "sur_up2_bwd"):
@@ -73,6 +75,15 @@ def sur_conv3x3(x, w, bias, y, batch, H, W, K, N, transposed_weights, sgn, relu,
 
 def sur_conv3x3_wgrad(x, dy, dw, batch, H, W, Cin, Cout, stream):
     _ok(_lib.sur_conv3x3_wgrad(_p(x), _p(dy), _p(dw), batch, H, W, Cin, Cout, stream), "sur_conv3x3_wgrad")
+
+
+def sur_conv3x3_up_add(xc, w, bias, addend, y, batch, H, W, K, N, stream):
+    _ok(_lib.sur_conv3x3_up_add(_p(xc), _p(w), _p(bias), _p(addend), _p(y), batch, H, W, K, N, stream),
+        "sur_conv3x3_up_add")
+
+
+def sur_conv3x3_wgrad_up(xc, dy, dw, batch, H, W, Cin, Cout, stream):
+    _ok(_lib.sur_conv3x3_wgrad_up(_p(xc), _p(dy), _p(dw), batch, H, W, Cin, Cout, stream), "sur_conv3x3_wgrad_up")
 
 
 def sur_relu_bwd(y, dy, dx, stream):
@@ -223,16 +234,39 @@ class UNet:
             skips.append(h)
         for l in range(L - 2, -1, -1):
             hh, ww = self._sizes[l]
-            up = self._buf(f"up{l}", (B, hh, ww, self.ch[l + 1]), bf)
-            sur_up2(h, up, B, hh // 2, ww // 2, self.ch[l + 1], self.s)
-            t = self._conv(up, f"u{l}", B, hh, ww, False)
+            # s = conv(up2(h)) + skip in one kernel (upsampling read through the coarse index)
             sk = self._buf(f"s{l}", (B, hh, ww, self.ch[l]), bf)
-            sur_add(t, skips[l], sk, self.s)
+            sur_conv3x3_up_add(h, self.wb[f"u{l}"], self.b[f"u{l}"], skips[l], sk, B, hh, ww, self.ch[l + 1],
+                               self.ch[l], self.s)
             h = self._conv(sk, f"d{l}", B, hh, ww, True)
         out = self._conv(h, "out", B, H, W, False, out_f32=True)
         pred = self._buf("pred", (B, H, W, 3), self.torch.float32)
         sur_flux_update(out, base, pred, B, H, W, self.cin, self.s)
         return pred
+
+    def launches_per_forward(self):
+        """Kernel launches of one forward pass: two convolutions per level, a pooling between
+        levels, one fused decoder convolution and one convolution per decoder level, the output
+        convolution and the flux update."""
+        L = len(self.ch)
+        return 2 * L + (L - 1) + 2 * (L - 1) + 2
+
+    def capture_forward(self, x, base):
+        """Capture one forward pass over the tensors x, base in a CUDA graph; returns (graph,
+        pred).  Replaying the graph re-reads x and base in place and rewrites pred."""
+        torch = self.torch
+        self.forward(x, base)  # every buffer exists before the capture
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        old = self.s
+        self.s = side.cuda_stream
+        try:
+            with torch.cuda.graph(g, stream=side):
+                pred = self.forward(x, base)
+        finally:
+            self.s = old
+        return g, pred
 
     def backward(self, dpred):
         """Accumulate the gradients of every weight and bias for dL/dpred (FP32, (B, H, W, 3))."""
@@ -245,9 +279,9 @@ class UNet:
         dout = self._buf("dout", (B, H, W, self.cin), bf)
         sur_flux_update_bwd(dpred, dout, B, H, W, self.cin, self.s)
 
-        def conv_back(name, inp, dy, hh, ww, want_dx=True):
+        def conv_back(name, inp, dy, hh, ww, want_dx=True, up=False):
             _, ci, co = next(l for l in self.layers if l[0] == name)
-            sur_conv3x3_wgrad(inp, dy, self.gw[name], B, hh, ww, ci, co, self.s)
+            (sur_conv3x3_wgrad_up if up else sur_conv3x3_wgrad)(inp, dy, self.gw[name], B, hh, ww, ci, co, self.s)
             sur_bias_grad(dy, self.gb[name], B * hh * ww, co, self.s)
             if not want_dx:
                 return None
@@ -264,7 +298,8 @@ class UNet:
             sur_relu_bwd(bufs[f"d{l}"], dh, g, self.s)
             ds = conv_back(f"d{l}", bufs[f"s{l}"], g, hh, ww)
             dskip[l] = ds
-            dup = conv_back(f"u{l}", bufs[f"up{l}"], ds, hh, ww)
+            src = bufs[f"d{l + 1}"] if l + 1 < L - 1 else bufs[f"e{L - 1}b"]  # coarse input of u{l}
+            dup = conv_back(f"u{l}", src, ds, hh, ww, up=True)
             dc = self._buf(f"gup{l}", (B, hh // 2, ww // 2, self.ch[l + 1]), bf)
             sur_up2_bwd(dup, dc, B, hh // 2, ww // 2, self.ch[l + 1], self.s)
             dh = dc
@@ -427,15 +462,48 @@ def evaluate(net, traj, judge, batch=4):
     return rows
 
 
-def time_forward(net, x, base, reps=5):
-    """Milliseconds per forward pass of the batch x (CUDA events on the network's stream)."""
+def time_forward(net, x, base, reps=5, graph=False):
+    """Milliseconds per forward pass of the batch x (CUDA events on the stream that runs it:
+    the network's stream, or with graph=True the current stream replaying a captured forward)."""
     import torch
+    if graph:
+        g, _ = net.capture_forward(x, base)
+        stream = torch.cuda.current_stream()
+        run = g.replay
+    else:
+        stream = net.stream
+        run = lambda: net.forward(x, base)  # noqa: E731
     for _ in range(2):
-        net.forward(x, base)
+        run()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(net.stream)
+    e0.record(stream)
     for _ in range(reps):
-        net.forward(x, base)
-    e1.record(net.stream)
+        run()
+    e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def _main(argv=None):
+    """Time the forward pass of the default network on a random batch (eager and graph-replayed)."""
+    import argparse
+
+    import torch
+    ap = argparse.ArgumentParser(description=_main.__doc__)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--n", type=int, default=256, help="image side")
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args(argv)
+    net = UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn((a.batch, a.n, a.n, 16), device="cuda", generator=g).to(torch.bfloat16)
+    base = x[..., :3].float().contiguous()
+    eager = time_forward(net, x, base, reps=a.reps)
+    graph = time_forward(net, x, base, reps=a.reps, graph=True)
+    print(f"batch {a.batch} image {a.n}x{a.n}: {eager:.4f} ms/forward eager, {graph:.4f} ms/forward graph "
+          f"({net.launches_per_forward()} launches per forward)")
+
+
+if __name__ == "__main__":
+    _main()

@@ -23,6 +23,21 @@ def test_exports_every_declared_symbol(lbm):
         assert hasattr(lib, n), n
 
 
+def test_surrogate_header_exported_and_wrapped(lbm):
+    """Every function include/surrogate.h declares is exported and has a same-name wrapper."""
+    import os
+    import re
+    from paper_1803_11345_gb300 import surrogate
+    hdr = os.path.join(os.path.dirname(lbm.HEADER), "surrogate.h")
+    text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(sur_\w+)\s*\(", text)))
+    assert {"sur_conv3x3", "sur_conv3x3_up_add", "sur_conv3x3_wgrad_up", "sur_adam"} <= set(names)
+    lib = ctypes.CDLL(lbm._build.LIB)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert hasattr(surrogate, n), f"binding lacks {n}"
+
+
 def test_header_declares_what_the_binding_wraps(lbm):
     for n in lbm.declared_functions():
         assert hasattr(lbm, n), f"binding lacks {n}"

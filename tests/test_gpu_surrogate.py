@@ -35,7 +35,7 @@ def _rel(a, b):
 def test_conv_forward_backward_match_oracle(S, K, N):
     import torch
     rng = np.random.default_rng(K * 100 + N)
-    B, H, W = 2, 8, 12  # 192 pixels: not a multiple of the 64-pixel tile
+    B, H, W = 2, 8, 12  # 192 pixels: not a multiple of the 128-pixel tile
     s = torch.cuda.current_stream().cuda_stream
     x, xn = _bf(rng, (B, H, W, K))
     w, wn = _bf(rng, (9, K, N), 0.2)
@@ -54,6 +54,33 @@ def test_conv_forward_backward_match_oracle(S, K, N):
     ybf = torch.empty((B, H, W, N), dtype=torch.bfloat16, device="cuda")
     S.sur_conv3x3(x, w, bias, ybf, B, H, W, K, N, 0, 1, 1, 0, s)
     assert _rel(ybf.float().cpu().numpy(), want) < 4e-3
+
+
+@pytest.mark.parametrize("K,N", [(16, 16), (64, 32), (32, 128), (256, 128)])
+def test_fused_decoder_conv_matches_oracle(S, K, N):
+    """conv3x3(up2(xc)) + bias + skip in one kernel, and its weight gradient read through the
+    coarse image, against the oracle's separate up2 / conv3x3 / add."""
+    import torch
+    rng = np.random.default_rng(K * 7 + N)
+    B, H, W = 2, 10, 14  # 280 fine pixels: three 128-pixel tiles, the last one ragged
+    s = torch.cuda.current_stream().cuda_stream
+    xc, xcn = _bf(rng, (B, H // 2, W // 2, K))
+    w, wn = _bf(rng, (9, K, N), 0.2)
+    bias = torch.tensor(rng.standard_normal(N), dtype=torch.float32).cuda()
+    skip, skipn = _bf(rng, (B, H, W, N))
+    y = torch.empty((B, H, W, N), dtype=torch.bfloat16, device="cuda")
+    S.sur_conv3x3_up_add(xc, w, bias, skip, y, B, H, W, K, N, s)
+    want = U.conv3x3(U.up2(xcn), wn, bias.cpu().numpy().astype(np.float64)) + skipn
+    assert _rel(y.float().cpu().numpy(), want) < 4e-3
+    y2 = torch.empty_like(y)
+    S.sur_conv3x3_up_add(xc, w, None, None, y2, B, H, W, K, N, s)
+    assert _rel(y2.float().cpu().numpy(), U.conv3x3(U.up2(xcn), wn)) < 4e-3
+    dy, dyn = _bf(rng, (B, H, W, N))
+    dw = torch.zeros((9, K, N), dtype=torch.float32, device="cuda")
+    S.sur_conv3x3_wgrad_up(xc, dy, dw, B, H, W, K, N, s)
+    assert _rel(dw.cpu().numpy(), U.conv3x3_bwd_weight(U.up2(xcn), dyn)) < 1e-5
+    with pytest.raises(S.SurError):  # odd fine sizes have no coarse image
+        S.sur_conv3x3_up_add(xc, w, None, None, y2, B, H - 1, W, K, N, s)
 
 
 def test_elementwise_kernels_match_oracle(S):
@@ -168,3 +195,29 @@ def test_training_reduces_loss(S):
         net.adam_step(lr=2e-3)
     last = net.loss_and_grads(x, base, target).item()
     assert last < 0.2 * first, (first, last)
+
+
+def test_graph_replayed_forward_equals_eager(S):
+    """The CUDA-graph capture of the forward pass reproduces the eager pass bit for bit, and
+    re-reads its input tensors in place on every replay."""
+    import torch
+    ch, cin = (16, 32, 64), 16
+    net = S.UNet(ch=ch, cin=cin, seed=5)
+    rng = np.random.default_rng(11)
+    net.w["out"] = torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda()
+    S.sur_cast_bf16(net.w["out"], net.wb["out"], net.s)
+    B, H, W = 3, 32, 48
+    x, _ = _bf(rng, (B, H, W, cin), 0.5)
+    base = x[..., :3].float().contiguous()
+    g, pred = net.capture_forward(x, base)
+    x2, _ = _bf(rng, (B, H, W, cin), 0.5)
+    for inp in (x, x2):
+        x.copy_(inp)
+        base.copy_(inp[..., :3].float())
+        g.replay()
+        torch.cuda.synchronize()
+        got = pred.clone()
+        want = net.forward(x, base).clone()
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
+    assert net.launches_per_forward() == 2 * 3 + 2 + 4 + 2

@@ -38,12 +38,15 @@ class _Params(ctypes.Structure):
         ("visc_interp", ctypes.c_int), ("k8_form", ctypes.c_int),
         ("collision", ctypes.c_int), ("walls", ctypes.c_int),
         ("u_top", ctypes.c_double), ("u_bottom", ctypes.c_double),
+        ("wet_bottom", ctypes.c_double), ("wet_top", ctypes.c_double),
+        ("Fx", ctypes.c_double), ("Fy", ctypes.c_double), ("force_mode", ctypes.c_int),
     ]
 
 
 _DEFAULTS = dict(tau_l=1.0, tau_g=1.0, M=0.1, Gamma=1.0, gamma=0.04, a=0.04, omega3=1.0,
                  omega6=1.0, omega7=1.0, omega8=1.0, visc_interp=0, k8_form=0, collision=0,
-                 walls=0, u_top=0.0, u_bottom=0.0)
+                 walls=0, u_top=0.0, u_bottom=0.0, wet_bottom=0.0, wet_top=0.0, Fx=0.0, Fy=0.0,
+                 force_mode=0)
 
 
 def build(force: bool = False) -> str:
@@ -82,7 +85,12 @@ def _load():
     lib.orc_omega_phi.restype = d
     lib.orc_collide_f.argtypes = [pp, dp, d, d, d, d, dp]
     lib.orc_collide_g.argtypes = [pp, dp, d, d, d, d, d, dp]
-    lib.orc_stencils.argtypes = [i, i, i, dp, dp, dp, dp]
+    lib.orc_stencils.argtypes = [i, i, i, d, d, dp, dp, dp, dp]
+    lib.orc_wall_gradient.argtypes = [d, d, d]
+    lib.orc_wall_gradient.restype = d
+    lib.orc_force.argtypes = [pp, d, dp]
+    lib.orc_guo_source.argtypes = [d, d, d, d, dp]
+    lib.orc_velocity.argtypes = [pp, dp, d, dp]
     lib.orc_create.argtypes = [pp, dp, dp, dp, dp]
     lib.orc_create.restype = p
     lib.orc_step.argtypes = [p, i]
@@ -182,13 +190,40 @@ def collide_g(params: _Params, g, ux, uy, gx, gy, lap):
     return out
 
 
-def stencils(phi, walls: bool = False):
-    """(d/dx, d/dy, Laplacian) of a (ny, nx) array with the isotropic stencils."""
+def stencils(phi, walls: bool = False, wet_bottom: float = 0.0, wet_top: float = 0.0):
+    """(d/dx, d/dy, Laplacian) of a (ny, nx) array with the isotropic stencils; with walls the
+    ghost rows are the adjacent rows plus the wall gradients wet_bottom / wet_top."""
     phi = _f64(phi)
     ny, nx = phi.shape
     gx, gy, lap = (np.zeros_like(phi) for _ in range(3))
-    _load().orc_stencils(nx, ny, int(walls), _ptr(phi), _ptr(gx), _ptr(gy), _ptr(lap))
+    _load().orc_stencils(nx, ny, int(walls), float(wet_bottom), float(wet_top), _ptr(phi), _ptr(gx), _ptr(gy),
+                         _ptr(lap))
     return gx, gy, lap
+
+
+def wall_gradient(theta, a, gamma):
+    """Wall gradient of phi along the outward normal for contact angle theta (radians), Eq. 18."""
+    return _load().orc_wall_gradient(float(theta), float(a), float(gamma))
+
+
+def force(params: _Params, phi):
+    out = np.zeros(2)
+    _load().orc_force(ctypes.byref(params), float(phi), _ptr(out))
+    return out
+
+
+def guo_source(ux, uy, Fx, Fy):
+    out = np.zeros(9)
+    _load().orc_guo_source(ux, uy, Fx, Fy, _ptr(out))
+    return out
+
+
+def velocity(params: _Params, f, phi):
+    """(sum f c + F/2) / rho of one node's populations f."""
+    f = _f64(f)
+    out = np.zeros(2)
+    _load().orc_velocity(ctypes.byref(params), _ptr(f), float(phi), _ptr(out))
+    return out
 
 
 def node_update(params: _Params, f, g, x: int, y: int):

@@ -24,7 +24,14 @@
 //     here so that the all-equal case can be compared with BGK.
 //   * moving walls: halfway bounce-back, walls at y = -1/2 and y = ny - 1/2; the wall term uses
 //     the boundary node's own density (f) or order parameter (g) at the colliding time level.
-//   * phi at walls for the stencils: mirror ghost phi(x,-1) = phi(x,0) (neutral wetting).
+//   * phi at walls for the stencils: ghost rows phi(x,-1) = phi(x,0) + wet_bottom and
+//     phi(x,ny) = phi(x,ny-1) + wet_top, where wet_* is the wall gradient of Eq. 18 taken along
+//     the outward normal (positive: the phase phi = +1 wets the wall).  0 = mirror (neutral).
+//   * body force (needed by the contact-angle test, which names a force but no forcing scheme):
+//     Guo's source term S_i = w_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F, the velocity
+//     u = (sum f c + F/2) / rho, and in central-moment space k* = k + omega (k_eq - k) +
+//     (1 - omega/2) T^T S for every moment (omega = 0 for k_0..k_2, so k*_1 = k_1 + F_x = F_x/2).
+//     F is uniform (force_mode 0) or acts on phase l only, F (1 + phi)/2 (force_mode 1).
 //   * state kept between steps = post-collision populations f*, g*.  Initialisation sets
 //     f = f_eq, g = g_eq from the initial fields and applies one collision at t = 0.
 #include <cmath>
@@ -82,6 +89,9 @@ typedef struct {
   int collision;         // 0: hybrid central moments for f (paper), 1: BGK for f (Eq. 6)
   int walls;             // 0: periodic, 1: walls at y=-1/2 and y=ny-1/2
   double u_top, u_bottom;  // x-velocity of the top / bottom wall
+  double wet_bottom, wet_top;  // wall gradient of phi along the outward normal (Eq. 18)
+  double Fx, Fy;         // body force per unit volume
+  int force_mode;        // 0: uniform F, 1: F (1 + phi)/2 (phase l only)
 } orc_params;
 
 // ---------------------------------------------------------------------------------------
@@ -188,35 +198,84 @@ double orc_omega_rho(const orc_params* P, double phi) {
 // omega_phi from M = (1/omega_phi - 1/2) Gamma c_s^2 (paragraph after Eq. 14).
 double orc_omega_phi(const orc_params* P) { return 1.0 / (P->M / (P->Gamma * CS2) + 0.5); }
 
-// Post-collision f at one node.  Central moments: Eq. 15 for the basis, k = T^T f,
-// k_eq = T^T f_eq, Eq. 17 for k_3..k_8, k* = [rho, 0, 0, k3*..k8*], f* = (T^T)^-1 k*.
-// BGK (collision = 1): Eq. 6.
-void orc_collide_f(const orc_params* P, const double* f, double phi, double gx, double gy,
-                   double lap, double* fout) {
-  double rho = 0, jx = 0, jy = 0;
+// Wall gradient of phi for a prescribed contact angle theta (radians), Eq. 18:
+// d_perp phi_w = sign(pi/2 - theta) sqrt((2a/gamma) cos(t/3) (1 - cos(t/3))), t = acos(sin^2 theta).
+// The square root covers the whole product as printed; the sign (positive below 90 degrees, where
+// the phase phi = +1 wets the wall) follows the paragraph after Eq. 18 on hydrophilic walls.
+double orc_wall_gradient(double theta, double a, double gamma) {
+  const double PI = 3.14159265358979323846;
+  double st = std::sin(theta);
+  double t = std::acos(st * st);
+  double c = std::cos(t / 3.0);
+  double mag = std::sqrt(2.0 * a / gamma * c * (1.0 - c));
+  return theta < 0.5 * PI ? mag : (theta > 0.5 * PI ? -mag : 0.0);
+}
+
+// Body force at a node of order parameter phi (see the header for the two modes).
+void orc_force(const orc_params* P, double phi, double* F) {
+  double s = P->force_mode == 1 ? 0.5 * (1.0 + phi) : 1.0;
+  F[0] = P->Fx * s;
+  F[1] = P->Fy * s;
+}
+
+// Guo, Zheng & Shi (2002) forcing term for velocity u and force F:
+// S_i = w_i [ (c_i - u) / c_s^2 + (c_i . u) c_i / c_s^4 ] . F.
+void orc_guo_source(double ux, double uy, double Fx, double Fy, double* S) {
+  for (int i = 0; i < 9; ++i) {
+    double cu = CX[i] * ux + CY[i] * uy;
+    double ax = (CX[i] - ux) * INV_CS2 + cu * CX[i] * INV_CS2 * INV_CS2;
+    double ay = (CY[i] - uy) * INV_CS2 + cu * CY[i] * INV_CS2 * INV_CS2;
+    S[i] = W[i] * (ax * Fx + ay * Fy);
+  }
+}
+
+// Velocity of a node: (sum f c + F/2) / rho with F = orc_force(phi).
+void orc_velocity(const orc_params* P, const double* f, double phi, double* u) {
+  double rho = 0, jx = 0, jy = 0, F[2];
   for (int i = 0; i < 9; ++i) {
     rho += f[i];
     jx += f[i] * CX[i];
     jy += f[i] * CY[i];
   }
-  double ux = jx / rho, uy = jy / rho;
+  orc_force(P, phi, F);
+  u[0] = (jx + 0.5 * F[0]) / rho;
+  u[1] = (jy + 0.5 * F[1]) / rho;
+}
+
+// Post-collision f at one node.  Central moments: Eq. 15 for the basis, k = T^T f,
+// k_eq = T^T f_eq, Eq. 17 for k_3..k_8, k* = [rho, F_x/2, F_y/2, k3*..k8*] (no force: the
+// paper's [rho, 0, 0, ...]), f* = (T^T)^-1 k*.  BGK (collision = 1): Eq. 6.  The force adds
+// (1 - omega_j/2) (T^T S)_j to each relaxed moment, or (1 - omega/2) S_i to each BGK population.
+void orc_collide_f(const orc_params* P, const double* f, double phi, double gx, double gy,
+                   double lap, double* fout) {
+  double rho = 0;
+  for (int i = 0; i < 9; ++i) rho += f[i];
+  double u[2], F[2];
+  orc_velocity(P, f, phi, u);
+  orc_force(P, phi, F);
+  const bool forced = F[0] != 0.0 || F[1] != 0.0;
+  double ux = u[0], uy = u[1];
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (forced) orc_guo_source(ux, uy, F[0], F[1], S);
   double p0 = rho * CS2 + P->a * (-0.5 * phi * phi + 0.75 * phi * phi * phi * phi);  // Eq. 13
   double pt = p0 - P->gamma * phi * lap;                                              // Eq. 14
   double om = orc_omega_rho(P, phi);
   double feq[9];
   orc_feq(rho, ux, uy, pt, gx, gy, P->gamma, feq);
   if (P->collision == 1) {
-    for (int i = 0; i < 9; ++i) fout[i] = f[i] + om * (feq[i] - f[i]);
+    for (int i = 0; i < 9; ++i) fout[i] = f[i] + om * (feq[i] - f[i]) + (1.0 - 0.5 * om) * S[i];
     return;
   }
-  double TT[81], k[9], keq[9], ks[9];
+  double TT[81], k[9], keq[9], ks[9], kS[9];
   orc_basis(ux, uy, TT);
   for (int j = 0; j < 9; ++j) {
     k[j] = 0.0;
     keq[j] = 0.0;
+    kS[j] = 0.0;
     for (int i = 0; i < 9; ++i) {
       k[j] += TT[j * 9 + i] * f[i];
       keq[j] += TT[j * 9 + i] * feq[i];
+      kS[j] += TT[j * 9 + i] * S[i];
     }
   }
   if (P->k8_form == 1) {
@@ -225,10 +284,12 @@ void orc_collide_f(const orc_params* P, const double* f, double phi, double gx, 
     keq[8] = kp[8];
   }
   const double omega[9] = {0, 0, 0, P->omega3, om, om, P->omega6, P->omega7, P->omega8};
+  // Conserved moments: k_0 = rho; k_1 = sum f (c_x - u_x) = -F_x/2 before the collision and
+  // gains (T^T S)_1 = F_x, so k*_1 = F_x/2 (same for y); both are 0 without a force.
   ks[0] = rho;
-  ks[1] = 0.0;
-  ks[2] = 0.0;
-  for (int j = 3; j < 9; ++j) ks[j] = k[j] + omega[j] * (keq[j] - k[j]);
+  ks[1] = 0.5 * F[0];
+  ks[2] = 0.5 * F[1];
+  for (int j = 3; j < 9; ++j) ks[j] = k[j] + omega[j] * (keq[j] - k[j]) + (1.0 - 0.5 * omega[j]) * kS[j];
   orc_solve(9, TT, ks, fout);
   // One step of iterative refinement: the elimination leaves a rounding residual with a
   // consistent sign in the momentum rows, which would make the oracle drift although k_1 and
@@ -259,9 +320,10 @@ void orc_collide_g(const orc_params* P, const double* g, double ux, double uy, d
 }
 
 // Stencils of Eq. 12 over a whole lattice (row-major y*nx + x).  x is periodic; y is periodic
-// or, with walls, mirrored: phi(x,-1) = phi(x,0), phi(x,ny) = phi(x,ny-1).
-void orc_stencils(int nx, int ny, int walls, const double* phi, double* gx, double* gy,
-                  double* lap) {
+// or, with walls, read from ghost rows phi(x,-1) = phi(x,0) + wet_bottom and
+// phi(x,ny) = phi(x,ny-1) + wet_top (Eq. 18 gradients; 0 = mirror).
+void orc_stencils(int nx, int ny, int walls, double wet_bottom, double wet_top, const double* phi,
+                  double* gx, double* gy, double* lap) {
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
@@ -269,13 +331,20 @@ void orc_stencils(int nx, int ny, int walls, const double* phi, double* gx, doub
       for (int i = 0; i < 9; ++i) {
         int xx = ((x + CX[i]) % nx + nx) % nx;
         int yy = y + CY[i];
+        double ghost = 0.0;
         if (walls) {
-          if (yy < 0) yy = 0;
-          if (yy >= ny) yy = ny - 1;
+          if (yy < 0) {
+            yy = 0;
+            ghost = wet_bottom;
+          }
+          if (yy >= ny) {
+            yy = ny - 1;
+            ghost = wet_top;
+          }
         } else {
           yy = (yy % ny + ny) % ny;
         }
-        double v = phi[(long)yy * nx + xx];
+        double v = phi[(long)yy * nx + xx] + ghost;
         sx += SDX[i] * v;
         sy += SDY[i] * v;
         sl += SLAP[i] * v;
@@ -307,7 +376,8 @@ static void collide_all(orc_state* S, const std::vector<double>& f, const std::v
     for (int i = 0; i < 9; ++i) s += g[i * N + n];
     phi[n] = s;  // phi = sum_i g_i
   }
-  orc_stencils(P->nx, P->ny, P->walls, phi.data(), gx.data(), gy.data(), lap.data());
+  orc_stencils(P->nx, P->ny, P->walls, P->wet_bottom, P->wet_top, phi.data(), gx.data(), gy.data(),
+               lap.data());
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < N; ++n) {
     double fn[9], gn[9], fo[9], go[9];
@@ -315,14 +385,10 @@ static void collide_all(orc_state* S, const std::vector<double>& f, const std::v
       fn[i] = f[i * N + n];
       gn[i] = g[i * N + n];
     }
-    double rho = 0, jx = 0, jy = 0;
-    for (int i = 0; i < 9; ++i) {
-      rho += fn[i];
-      jx += fn[i] * CX[i];
-      jy += fn[i] * CY[i];
-    }
+    double u[2];
+    orc_velocity(P, fn, phi[n], u);
     orc_collide_f(P, fn, phi[n], gx[n], gy[n], lap[n], fo);
-    orc_collide_g(P, gn, jx / rho, jy / rho, gx[n], gy[n], lap[n], go);
+    orc_collide_g(P, gn, u[0], u[1], gx[n], gy[n], lap[n], go);
     for (int i = 0; i < 9; ++i) {
       fs[i * N + n] = fo[i];
       gs[i * N + n] = go[i];
@@ -369,7 +435,7 @@ void* orc_create(const orc_params* P, const double* phi0, const double* ux0, con
   S->f = new std::vector<double>(9 * N);
   S->g = new std::vector<double>(9 * N);
   std::vector<double> f(9 * N), g(9 * N), gx(N), gy(N), lap(N);
-  orc_stencils(P->nx, P->ny, P->walls, phi0, gx.data(), gy.data(), lap.data());
+  orc_stencils(P->nx, P->ny, P->walls, P->wet_bottom, P->wet_top, phi0, gx.data(), gy.data(), lap.data());
   for (long n = 0; n < N; ++n) {
     double rho = rho0 ? rho0[n] : 1.0, ux = ux0 ? ux0[n] : 0.0, uy = uy0 ? uy0[n] : 0.0;
     double phi = phi0[n];
@@ -399,8 +465,10 @@ void orc_step(void* h, int nsteps) {
   }
 }
 
-// Macroscopic fields of the current (post-collision) state: rho = sum f, v = sum f c / rho,
-// phi = sum g (paragraph after Eq. 14).  Any output pointer may be NULL.
+// Macroscopic fields of the current (post-collision) state: rho = sum f, phi = sum g (paragraph
+// after Eq. 14) and the velocity of the last collision, v = (sum f* c - F/2) / rho (the
+// collision added F to sum f c, which held rho v - F/2 before it; F = 0: v = sum f c / rho).
+// Any output pointer may be NULL.
 void orc_fields(void* h, double* rho, double* ux, double* uy, double* phi) {
   orc_state* S = (orc_state*)h;
   const long N = S->N;
@@ -414,9 +482,11 @@ void orc_fields(void* h, double* rho, double* ux, double* uy, double* phi) {
       jy += f[i * N + n] * CY[i];
       p += g[i * N + n];
     }
+    double F[2];
+    orc_force(&S->P, p, F);
     if (rho) rho[n] = r;
-    if (ux) ux[n] = jx / r;
-    if (uy) uy[n] = jy / r;
+    if (ux) ux[n] = (jx - 0.5 * F[0]) / r;
+    if (uy) uy[n] = (jy - 0.5 * F[1]) / r;
     if (phi) phi[n] = p;
   }
 }
@@ -488,13 +558,19 @@ void orc_node_update(const orc_params* P, const double* f, const double* g, int 
     for (int dx = -1; dx <= 1; ++dx) {
       int xx = ((x + dx) % nx + nx) % nx;
       int yy = y + dy;
+      double s = 0;
       if (P->walls) {
-        if (yy < 0) yy = 0;
-        if (yy >= ny) yy = ny - 1;
+        if (yy < 0) {
+          yy = 0;
+          s = P->wet_bottom;
+        }
+        if (yy >= ny) {
+          yy = ny - 1;
+          s = P->wet_top;
+        }
       } else {
         yy = (yy % ny + ny) % ny;
       }
-      double s = 0;
       for (int i = 0; i < 9; ++i) s += arriving(P, g, N, xx, yy, i);
       phi3[dy + 1][dx + 1] = s;
     }
@@ -510,14 +586,10 @@ void orc_node_update(const orc_params* P, const double* f, const double* g, int 
     fn[i] = arriving(P, f, N, x, y, i);
     gn[i] = arriving(P, g, N, x, y, i);
   }
-  double rho = 0, jx = 0, jy = 0;
-  for (int i = 0; i < 9; ++i) {
-    rho += fn[i];
-    jx += fn[i] * CX[i];
-    jy += fn[i] * CY[i];
-  }
+  double u[2];
+  orc_velocity(P, fn, phi3[1][1], u);
   orc_collide_f(P, fn, phi3[1][1], gxv, gyv, lap, fout);
-  orc_collide_g(P, gn, jx / rho, jy / rho, gxv, gyv, lap, gout);
+  orc_collide_g(P, gn, u[0], u[1], gxv, gyv, lap, gout);
 }
 
 void orc_free(void* h) {

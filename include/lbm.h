@@ -58,9 +58,12 @@ typedef enum {
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
 
 /* Boundaries.  PERIODIC: both directions.  WALLS_Y: periodic in x, halfway bounce-back walls
- * at y = -1/2 (moving with x-velocity u_bottom) and y = ny - 1/2 (u_top); phi is mirrored at
- * the walls for the stencils (d phi / dy = 0, neutral wetting).  The paper's tests use no-slip
- * and moving walls without stating the discrete form (contact-angle and shear paragraphs). */
+ * at y = -1/2 (moving with x-velocity u_bottom) and y = ny - 1/2 (u_top).  For the stencils phi
+ * continues into one ghost row beyond each wall: phi(x, -1) = phi(x, 0) + wet_bottom and
+ * phi(x, ny) = phi(x, ny - 1) + wet_top, where wet_* is the wall gradient of phi along the
+ * outward normal of Eq. 18 (0: mirror, neutral wetting, 90 degrees; > 0: the phase phi = +1
+ * wets the wall).  The paper's tests use no-slip and moving walls without stating the discrete
+ * form (contact-angle and shear paragraphs). */
 typedef enum { LBM_PERIODIC = 0, LBM_WALLS_Y = 1 } lbm_bc;
 
 /* How the f relaxation frequency varies with phi.  OMEGA_LINEAR is the paper's
@@ -76,6 +79,15 @@ typedef enum { LBM_K8_PROJECTED = 0, LBM_K8_PRINTED = 1 } lbm_k8_form;
 /* Collision of f.  CM: the paper's central-moment collision (Eq. 17; omega_4 = omega_5 =
  * omega_rho, omega_3 free, omega_6..8 = 1).  BGK: the double-BGK baseline of Eq. 6. */
 typedef enum { LBM_COLLIDE_CM = 0, LBM_COLLIDE_BGK = 1 } lbm_collision;
+
+/* Body force per unit volume (the contact-angle test applies one; the paper prints no forcing
+ * scheme).  UNIFORM: F = (force_x, force_y) everywhere.  PHASE_L: F (1 + phi)/2, acting on the
+ * phase phi = +1 only (with matched densities a uniform force would only build a pressure
+ * gradient).  The force enters as Guo's source term S_i = w_i [(c_i - u)/c_s^2 +
+ * (c_i . u) c_i / c_s^4] . F projected to central moments: k*_j = k_j + omega_j (k_j^eq - k_j)
+ * + (1 - omega_j/2) (T^T S)_j, with u = (sum f c + F/2)/rho; the velocity reported by
+ * lbm_fields is that u. */
+typedef enum { LBM_FORCE_UNIFORM = 0, LBM_FORCE_PHASE_L = 1 } lbm_force_mode;
 
 /* The problem statement, in the paper's symbols (paragraph after Eq. 14 and the set-ups of
  * the bubble, contact-angle and shear tests). */
@@ -93,6 +105,10 @@ typedef struct lbm_params {
   double u_top, u_bottom; /* wall x-velocities for LBM_WALLS_Y                                */
   int prec;               /* lbm_precision                                                    */
   int collision;          /* lbm_collision                                                    */
+  double wet_bottom, wet_top; /* wall gradients of phi (Eq. 18) for LBM_WALLS_Y; 0 = neutral;   */
+                          /* must be 0 with LBM_PERIODIC                                       */
+  double force_x, force_y;  /* body force per unit volume (0 = none)                           */
+  int force_mode;         /* lbm_force_mode                                                   */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice; /* opaque handle */
@@ -101,6 +117,11 @@ typedef struct lbm_lattice lbm_lattice; /* opaque handle */
  * (nu = 0.1), omega3 = 1, projected k8, omega-linear viscosity, periodic, FP32, CM collision.
  * nx = ny = 0 (the caller must set them). */
 LBM_API void lbm_default_params(lbm_params* p);
+
+/* Wall gradient of phi along the outward normal for a contact angle theta (radians) measured in
+ * the phase phi = +1, Eq. 18: sign(pi/2 - theta) sqrt((2a/gamma) cos(t/3)(1 - cos(t/3))) with
+ * t = acos(sin^2 theta).  Host function; NaN for gamma <= 0 or a < 0. */
+LBM_API double lbm_wall_gradient(double theta, double a, double gamma);
 
 /* Device bytes one lattice needs (both population copies plus a small status block) when the
  * caller supplies the memory to lbm_init.  Returns LBM_ERR_PARAM for invalid parameters. */

@@ -332,7 +332,7 @@ int lbm_batch_fields(lbm_batch* b, int member, double* rho, double* ux, double* 
   const HostGeometry& g = b->geo[member];
   const long long N = (long long)g.nx * g.ny;
   double* stage = (double*)spare_of(b, member);
-  cudaError_t e = launch_fields(b->prec, g, state_of(b, member), stage, b->stream);
+  cudaError_t e = launch_fields(b->prec, g, b->phys[member], state_of(b, member), stage, b->stream);
   double* outs[4] = {rho, ux, uy, phi};
   for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     if (outs[k]) e = cudaMemcpyAsync(outs[k], stage + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream);

@@ -78,13 +78,18 @@ const char* lbmch::validate_params(const lbm_params* p, HostGeometry* g, HostPhy
   if (p->visc != LBM_OMEGA_LINEAR && p->visc != LBM_TAU_LINEAR) return "visc must be an lbm_visc_interp";
   if (p->k8_form != LBM_K8_PROJECTED && p->k8_form != LBM_K8_PRINTED) return "k8_form must be an lbm_k8_form";
   if (p->collision != LBM_COLLIDE_CM && p->collision != LBM_COLLIDE_BGK) return "collision must be an lbm_collision";
-  const double vals[] = {p->tau_l, p->tau_g, p->M, p->Gamma, p->gamma, p->a, p->omega3, p->u_top, p->u_bottom};
+  if (p->force_mode != LBM_FORCE_UNIFORM && p->force_mode != LBM_FORCE_PHASE_L)
+    return "force_mode must be an lbm_force_mode";
+  const double vals[] = {p->tau_l,  p->tau_g,      p->M,       p->Gamma,   p->gamma,   p->a,      p->omega3,
+                         p->u_top, p->u_bottom, p->wet_bottom, p->wet_top, p->force_x, p->force_y};
   for (double v : vals)
     if (!std::isfinite(v)) return "parameters must be finite";
   if (!(p->tau_l > 0.5) || !(p->tau_g > 0.5)) return "tau_l and tau_g must exceed 1/2 (positive viscosity)";
   if (!(p->M > 0) || !(p->Gamma > 0)) return "M and Gamma must be positive";
   if (p->gamma < 0 || p->a < 0) return "gamma and a must be >= 0";
   if (!(p->omega3 > 0 && p->omega3 < 2)) return "omega3 must lie in (0, 2)";
+  if (p->bc != LBM_WALLS_Y && (p->wet_bottom != 0 || p->wet_top != 0))
+    return "wet_bottom and wet_top need walls (bc = LBM_WALLS_Y)";
   const long long pitch = ((long long)p->nx + 31) / 32 * 32;
   if (pitch * (long long)p->ny > INT_MAX) return "lattice too large: pitch * ny must fit in int32";
   g->nx = p->nx;
@@ -104,6 +109,11 @@ const char* lbmch::validate_params(const lbm_params* p, HostGeometry* g, HostPhy
   ph->Gamma = p->Gamma;
   ph->u_top = p->u_top;
   ph->u_bottom = p->u_bottom;
+  ph->wet_bottom = g->walls ? p->wet_bottom : 0.0;
+  ph->wet_top = g->walls ? p->wet_top : 0.0;
+  ph->force_x = p->force_x;
+  ph->force_y = p->force_y;
+  ph->force_mode = p->force_mode;
   ph->visc = p->visc;
   ph->k8_printed = p->k8_form == LBM_K8_PRINTED;
   ph->bgk = p->collision == LBM_COLLIDE_BGK;
@@ -132,6 +142,15 @@ size_t total_bytes(int prec, const HostGeometry& g, size_t* pop_bytes) {
 void lbmch::set_thread_error(const char* msg) { std::snprintf(g_init_err, sizeof(g_init_err), "%s", msg); }
 
 extern "C" {
+
+double lbm_wall_gradient(double theta, double a, double gamma) {
+  if (!(gamma > 0) || !(a >= 0)) return std::nan("");
+  const double pi = 3.14159265358979323846;
+  const double s = std::sin(theta);
+  const double c = std::cos(std::acos(s * s) / 3.0);
+  const double mag = std::sqrt(2.0 * a / gamma * c * (1.0 - c));
+  return theta < 0.5 * pi ? mag : (theta > 0.5 * pi ? -mag : 0.0);
+}
 
 void lbm_default_params(lbm_params* p) {
   if (!p) return;
@@ -301,7 +320,7 @@ int lbm_fields(lbm_lattice* h, double* rho, double* ux, double* uy, double* phi)
   if (!h) return LBM_ERR_PARAM;
   const long long N = (long long)h->geo.nx * h->geo.ny;
   double* stage = (double*)other_buf(h);
-  cudaError_t e = launch_fields(h->p.prec, h->geo, state_buf(h), stage, h->stream);
+  cudaError_t e = launch_fields(h->p.prec, h->geo, h->phys, state_buf(h), stage, h->stream);
   double* outs[4] = {rho, ux, uy, phi};
   for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     if (outs[k]) e = cudaMemcpyAsync(outs[k], stage + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm_internal.h"
+
 namespace lbmch {
 
 // D2Q9 velocities in the paper's order: c_x = [0,1,0,-1,0,1,-1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1]
@@ -165,11 +167,49 @@ template <class C> struct Phys {
   C omega_l, omega_g, tau_l, tau_g;  // f relaxation of phase l (phi=+1) and g (phi=-1)
   C omega3, omega_phi;
   C gamma, a, Gamma;
-  C u_top, u_bottom;  // wall x-velocities
-  int visc;           // 0 omega-linear (paper), 1 tau-linear
-  int k8_printed;     // 0 projected k8, 1 printed k8
-  int bgk;            // 0 central moments (paper), 1 BGK baseline
+  C u_top, u_bottom;      // wall x-velocities
+  C wet_bottom, wet_top;  // wall gradients of phi along the outward normal (Eq. 18); ghost rows
+  C force_x, force_y;     // body force per unit volume
+  int visc;               // 0 omega-linear (paper), 1 tau-linear
+  int k8_printed;         // 0 projected k8, 1 printed k8
+  int bgk;                // 0 central moments (paper), 1 BGK baseline
+  int force_mode;         // 0 uniform, 1 on phase l only: F (1 + phi)/2
+  int forced;             // force_x or force_y non-zero
 };
+
+// Physics in the kernel's arithmetic type from the validated host parameters.
+template <class C> inline Phys<C> make_phys(const HostPhys& h) {
+  Phys<C> p;
+  p.omega_l = (C)h.omega_l;
+  p.omega_g = (C)h.omega_g;
+  p.tau_l = (C)h.tau_l;
+  p.tau_g = (C)h.tau_g;
+  p.omega3 = (C)h.omega3;
+  p.omega_phi = (C)h.omega_phi;
+  p.gamma = (C)h.gamma;
+  p.a = (C)h.a;
+  p.Gamma = (C)h.Gamma;
+  p.u_top = (C)h.u_top;
+  p.u_bottom = (C)h.u_bottom;
+  p.wet_bottom = (C)h.wet_bottom;
+  p.wet_top = (C)h.wet_top;
+  p.force_x = (C)h.force_x;
+  p.force_y = (C)h.force_y;
+  p.visc = h.visc;
+  p.k8_printed = h.k8_printed;
+  p.bgk = h.bgk;
+  p.force_mode = h.force_mode;
+  p.forced = h.force_x != 0.0 || h.force_y != 0.0;
+  return p;
+}
+
+// Body force at a node of order parameter phi.
+template <class C>
+__device__ __forceinline__ void body_force(const Phys<C>& ph, C phi, C& Fx, C& Fy) {
+  const C w = ph.force_mode ? C(0.5) * (phi + C(1)) : C(1);
+  Fx = ph.force_x * w;
+  Fy = ph.force_y * w;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Streaming, Eqs. 4-5, in pull form: the population of direction i at node (x, y) and time t is
@@ -290,7 +330,11 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
   const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
   const C inv_rho = C(1) / rho;
-  const C ux = jx * inv_rho, uy = jy * inv_rho;
+  // Body force (Guo's scheme): the velocity carries half the force, u = (j + F/2)/rho.
+  C Fx = C(0), Fy = C(0);
+  if (ph.forced) body_force(ph, phi, Fx, Fy);
+  const C ux = ph.forced ? (jx + C(0.5) * Fx) * inv_rho : jx * inv_rho;
+  const C uy = ph.forced ? (jy + C(0.5) * Fy) * inv_rho : jy * inv_rho;
   const C ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
   // Chemical potential (free-energy paragraph), bulk pressure p0 (Eq. 13) and p~ (Eq. 14).
   const C phi2 = phi * phi;
@@ -309,7 +353,14 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
     const C m20 = (f[1] + f[3]) + corners;
     const C m02 = (f[2] + f[4]) + corners;
     const C m11 = (f[5] - f[6]) + (f[7] - f[8]);
-    const C k20 = m20 - rho * ux2, k02 = m02 - rho * uy2, k11 = m11 - rho * uxy;
+    C k20 = m20 - rho * ux2, k02 = m02 - rho * uy2, k11 = m11 - rho * uxy;
+    if (ph.forced) {
+      // with the half-force velocity the first central moments are -F/2 before the collision:
+      // kappa_20 = m_20 - 2 ux kappa_10 - rho ux^2 and so on
+      k20 += ux * Fx;
+      k02 += uy * Fy;
+      k11 += C(0.5) * (ux * Fy + uy * Fx);
+    }
     const C k3 = k20 + k02, k4 = k20 - k02, k5 = k11;
     // Equilibrium central moments (the k_eq list and Eq. 16).
     const C k3e = C(2) * pt;
@@ -324,19 +375,39 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
     const C k3s = k3 + ph.omega3 * (k3e - k3);
     const C k4s = k4 + om * (k4e - k4);
     const C k5s = k5 + om * (k5e - k5);
-    // f* = (T^T)^-1 k*, k* = [rho, 0, 0, k3*, k4*, k5*, k6e, k7e, k8e]: central -> raw moments by
-    // the binomial shift c = cbar + u, then the D2Q9 raw-moment inversion.
+    // Force: central moments of Guo's source, (T^T S)_j; zero for j = 0, 3, 4, 5, F for j = 1, 2,
+    // and for j = 6..8 (omega = 1, so half of each is added):
+    C k6s = k6e, k7s = k7e, k8s = k8e;
+    if (ph.forced) {
+      k6s += C(0.5) * (Fy * cs2 - C(2) * Fx * uxy - Fy * ux2);
+      k7s += C(0.5) * (Fx * cs2 - Fx * uy2 - C(2) * Fy * uxy);
+      k8s += C(2) * uxy * (Fx * uy + Fy * ux);
+    }
+    // f* = (T^T)^-1 k*, k* = [rho, F_x/2, F_y/2, k3*, k4*, k5*, k6*, k7*, k8*] (the paper's
+    // [rho, 0, 0, ...] without a force): central -> raw moments by the binomial shift
+    // c = cbar + u, then the D2Q9 raw-moment inversion.
     const C a20 = C(0.5) * (k3s + k4s), a02 = C(0.5) * (k3s - k4s), a11 = k5s;
-    const C r20 = a20 + rho * ux2;
-    const C r02 = a02 + rho * uy2;
-    const C r11 = a11 + rho * uxy;
-    const C r21 = k6e + C(2) * ux * a11 + uy * a20 + rho * ux2 * uy;
-    const C r12 = k7e + C(2) * uy * a11 + ux * a02 + rho * ux * uy2;
-    const C r22 = k8e + C(2) * (uy * k6e + ux * k7e) + uy2 * a20 + ux2 * a02 + C(4) * uxy * a11 +
-                  rho * ux2 * uy2;
+    C r20 = a20 + rho * ux2;
+    C r02 = a02 + rho * uy2;
+    C r11 = a11 + rho * uxy;
+    C r21 = k6s + C(2) * ux * a11 + uy * a20 + rho * ux2 * uy;
+    C r12 = k7s + C(2) * uy * a11 + ux * a02 + rho * ux * uy2;
+    C r22 = k8s + C(2) * (uy * k6s + ux * k7s) + uy2 * a20 + ux2 * a02 + C(4) * uxy * a11 + rho * ux2 * uy2;
+    C r10 = jx, r01 = jy;
+    if (ph.forced) {
+      const C q1 = C(0.5) * Fx, q2 = C(0.5) * Fy;  // k*_1, k*_2
+      r10 = jx + Fx;                               // rho ux + k*_1
+      r01 = jy + Fy;
+      r20 += C(2) * ux * q1;
+      r02 += C(2) * uy * q2;
+      r11 += ux * q2 + uy * q1;
+      r21 += ux2 * q2 + C(2) * uxy * q1;
+      r12 += uy2 * q1 + C(2) * uxy * q2;
+      r22 += C(2) * uxy * (uy * q1 + ux * q2);
+    }
     f[0] = rho - r20 - r02 + r22;
     const C hx = C(0.5) * (r20 - r22), hy = C(0.5) * (r02 - r22);
-    const C qx = C(0.5) * (jx - r12), qy = C(0.5) * (jy - r21);
+    const C qx = C(0.5) * (r10 - r12), qy = C(0.5) * (r01 - r21);
     f[1] = hx + qx;
     f[3] = hx - qx;
     f[2] = hy + qy;
@@ -371,9 +442,15 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
                     (wxx * gxx + wyy * gyy + wxy * gxy);
       sum += feq;
       f[i] = f[i] + om * (feq - f[i]);
+      if (ph.forced) {
+        // Guo's source S_i = w_i [3 (c_i - u) . F + 9 (c_i . u)(c_i . F)], weighted 1 - omega/2
+        const C cF = C(lat_cx(i)) * Fx + C(lat_cy(i)) * Fy;
+        f[i] += (C(1) - C(0.5) * om) * w * (C(3) * (cF - (ux * Fx + uy * Fy)) + C(9) * cu * cF);
+      }
     }
     const C feq0 = rho - sum;
     f[0] = f[0] + om * (feq0 - f[0]);
+    if (ph.forced) f[0] += (C(1) - C(0.5) * om) * (C(4) / C(9)) * (-C(3) * (ux * Fx + uy * Fy));
   }
 
   // g: BGK towards g_eq (Eqs. 7, 9, 10).

@@ -16,7 +16,8 @@ struct HostGeometry {
 
 struct HostPhys {
   double omega_l, omega_g, tau_l, tau_g, omega3, omega_phi, gamma, a, Gamma, u_top, u_bottom;
-  int visc, k8_printed, bgk;
+  double wet_bottom, wet_top, force_x, force_y;
+  int visc, k8_printed, bgk, force_mode;
 };
 
 // Tile of the fused step: BX columns x BY rows of threads, `rows` lattice rows per CTA.
@@ -70,7 +71,7 @@ cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, cons
                         char* dst, cudaStream_t s);
 cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
                         const char* src, char* dst, int* flag, cudaStream_t s);
-cudaError_t launch_fields(int prec, const HostGeometry& g, const char* src, double* out,
+cudaError_t launch_fields(int prec, const HostGeometry& g, const HostPhys& p, const char* src, double* out,
                           cudaStream_t s);
 // Deterministic FP64 totals [sum phi, sum rho, sum jx, sum jy] into out4 (device), using
 // `partials` (device, >= reduce_partials_bytes()) as scratch.

@@ -22,24 +22,7 @@ namespace lbmch {
 
 namespace {
 
-template <class C> Phys<C> to_phys(const HostPhys& h) {
-  Phys<C> p;
-  p.omega_l = (C)h.omega_l;
-  p.omega_g = (C)h.omega_g;
-  p.tau_l = (C)h.tau_l;
-  p.tau_g = (C)h.tau_g;
-  p.omega3 = (C)h.omega3;
-  p.omega_phi = (C)h.omega_phi;
-  p.gamma = (C)h.gamma;
-  p.a = (C)h.a;
-  p.Gamma = (C)h.Gamma;
-  p.u_top = (C)h.u_top;
-  p.u_bottom = (C)h.u_bottom;
-  p.visc = h.visc;
-  p.k8_printed = h.k8_printed;
-  p.bgk = h.bgk;
-  return p;
-}
+template <class C> Phys<C> to_phys(const HostPhys& h) { return make_phys<C>(h); }
 
 Geometry to_geo(const HostGeometry& h) {
   Geometry g;
@@ -77,12 +60,17 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
   const int hx = (tx == 0) ? ((x0 == 0) ? geo.nx - 1 : x0 - 1) : ((x0 + xv == geo.nx) ? 0 : x0 + xv);
   const int hcol = (tx == 0) ? 0 : xv + 1;
 
-  // Virtual row r in [y0 - 1, y1] -> physical row (periodic wrap, or the wall mirror
-  // phi(x, -1) = phi(x, 0), phi(x, ny) = phi(x, ny - 1)).
+  // Virtual row r in [y0 - 1, y1] -> physical row (periodic wrap, or with walls the adjacent
+  // row, whose phi plus the wall gradient is the ghost value: phi(x, -1) = phi(x, 0) +
+  // wet_bottom, phi(x, ny) = phi(x, ny - 1) + wet_top; both gradients are 0 when periodic).
   auto phys_row = [&](int r) -> int {
     if (r < 0) return geo.walls ? 0 : r + geo.ny;
     if (r >= geo.ny) return geo.walls ? geo.ny - 1 : r - geo.ny;
     return r;
+  };
+  auto ghost = [&](int r) -> C {
+    if (!geo.walls) return C(0);
+    return r < 0 ? ph.wet_bottom : (r >= geo.ny ? ph.wet_top : C(0));
   };
   auto slot = [&](int r) -> int { return (r - (y0 - 1)) % RING; };
   auto sum9 = [](const C v[9]) -> C {
@@ -118,22 +106,22 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
     if (r <= y1) {
       if (colv) {
         gAd = pull_g(x, r, gA);
-        sphi[slot(r)][tx + 1] = phi_of(gA, gAd);
+        sphi[slot(r)][tx + 1] = phi_of(gA, gAd) + ghost(r);
       }
       if (halo) {
         hBd = pull_g(hx, r, hB);
-        sphi[slot(r)][hcol] = phi_of(hB, hBd);
+        sphi[slot(r)][hcol] = phi_of(hB, hBd) + ghost(r);
       }
     }
     if (ty == 0) {
       R gt[9];
       if (colv) {
         const bool d = pull_g(x, y0 - 1, gt);
-        sphi[slot(y0 - 1)][tx + 1] = phi_of(gt, d);
+        sphi[slot(y0 - 1)][tx + 1] = phi_of(gt, d) + ghost(y0 - 1);
       }
       if (halo) {
         const bool d = pull_g(hx, y0 - 1, gt);
-        sphi[slot(y0 - 1)][hcol] = phi_of(gt, d);
+        sphi[slot(y0 - 1)][hcol] = phi_of(gt, d) + ghost(y0 - 1);
       }
     }
     const int rb = y0 + BY + ty;
@@ -156,8 +144,8 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
     if (rc <= y1 && colv) gCd = pull_g(x, rc, gC);
     if (rb < y1 && colv) fBd = pull_f(rb, fB);
     if (rb <= y1) {
-      if (colv) sphi[slot(rb)][tx + 1] = phi_of(gB, gBd);
-      if (halo) sphi[slot(rb)][hcol] = phi_of(hB, hBd);
+      if (colv) sphi[slot(rb)][tx + 1] = phi_of(gB, gBd) + ghost(rb);
+      if (halo) sphi[slot(rb)][hcol] = phi_of(hB, hBd) + ghost(rb);
     }
     if (rc <= y1 && halo) hBd = pull_g(hx, rc, hB);
     __syncthreads();
@@ -252,9 +240,14 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
       int xx = x + dx;
       xx = xx < 0 ? xx + geo.nx : (xx >= geo.nx ? xx - geo.nx : xx);
       int yy = y + dy;
-      if (geo.walls) yy = yy < 0 ? 0 : (yy >= geo.ny ? geo.ny - 1 : yy);
-      else yy = yy < 0 ? yy + geo.ny : (yy >= geo.ny ? yy - geo.ny : yy);
-      s[dy + 1][dx + 1] = (C)phi0[(long long)yy * geo.nx + xx];
+      C ghost = C(0);  // wall gradient added to the ghost rows (Eq. 18)
+      if (geo.walls) {
+        ghost = yy < 0 ? ph.wet_bottom : (yy >= geo.ny ? ph.wet_top : C(0));
+        yy = yy < 0 ? 0 : (yy >= geo.ny ? geo.ny - 1 : yy);
+      } else {
+        yy = yy < 0 ? yy + geo.ny : (yy >= geo.ny ? yy - geo.ny : yy);
+      }
+      s[dy + 1][dx + 1] = (C)phi0[(long long)yy * geo.nx + xx] + ghost;
     }
   C gx, gy, lap;
   stencils<C>(s, gx, gy, lap);
@@ -295,10 +288,13 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
 }
 
 // -------------------------------------------------------------------------------------------
-// Macroscopic fields of the stored state: out = [rho | ux | uy | phi], dense FP64.
+// Macroscopic fields of the stored state: out = [rho | ux | uy | phi], dense FP64.  The stored
+// populations are post-collision, so sum f c = rho u + F/2 with u the velocity of that collision;
+// u = (sum f c - F/2)/rho is reported (F = force_x, force_y, weighted by (1 + phi)/2 in mode 1).
 
 template <int PREC>
-__global__ void k_fields(const char* __restrict__ src, const Geometry geo, double* __restrict__ out) {
+__global__ void k_fields(const char* __restrict__ src, const Geometry geo, const double fx, const double fy,
+                         const int fmode, double* __restrict__ out) {
   using P = Pop<PREC>;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -315,9 +311,10 @@ __global__ void k_fields(const char* __restrict__ src, const Geometry geo, doubl
   }
   const long long N = (long long)geo.nx * geo.ny;
   const long long n = (long long)y * geo.nx + x;
+  const double wf = fmode ? 0.5 * (1.0 + phi) : 1.0;
   out[n] = rho;
-  out[N + n] = jx / rho;
-  out[2 * N + n] = jy / rho;
+  out[N + n] = (jx - 0.5 * fx * wf) / rho;
+  out[2 * N + n] = (jy - 0.5 * fy * wf) / rho;
   out[3 * N + n] = phi;
 }
 
@@ -609,14 +606,15 @@ int batch_blocks_per_sm(int prec, const StepTile& t) {
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_fields(int prec, const HostGeometry& g, const char* src, double* out, cudaStream_t s) {
+cudaError_t launch_fields(int prec, const HostGeometry& g, const HostPhys& p, const char* src, double* out,
+                          cudaStream_t s) {
   dim3 blk(32, 8);
   dim3 grd = node_grid(g, blk);
   switch (prec) {
-    case 0: k_fields<0><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
-    case 1: k_fields<1><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
-    case 2: k_fields<2><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
-    case 3: k_fields<3><<<grd, blk, 0, s>>>(src, to_geo(g), out); break;
+    case 0: k_fields<0><<<grd, blk, 0, s>>>(src, to_geo(g), p.force_x, p.force_y, p.force_mode, out); break;
+    case 1: k_fields<1><<<grd, blk, 0, s>>>(src, to_geo(g), p.force_x, p.force_y, p.force_mode, out); break;
+    case 2: k_fields<2><<<grd, blk, 0, s>>>(src, to_geo(g), p.force_x, p.force_y, p.force_mode, out); break;
+    case 3: k_fields<3><<<grd, blk, 0, s>>>(src, to_geo(g), p.force_x, p.force_y, p.force_mode, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -160,6 +160,12 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     if (v >= geo.ny) return geo.walls ? geo.ny - 1 : v - geo.ny;
     return v;
   };
+  // Ghost rows beyond a wall hold the adjacent row's phi plus the wall gradient (Eq. 18); both
+  // gradients are 0 on periodic lattices.
+  auto ghost = [&](int v) -> C {
+    if (!geo.walls) return C(0);
+    return v < 0 ? ph.wet_bottom : (v >= geo.ny ? ph.wet_top : C(0));
+  };
 
   // Staging of row v of set g (true) or f (false) by one warp: lane 0 arms the slot's barrier
   // with the byte count, then one lane per (plane, segment) issues its copy.
@@ -342,17 +348,18 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       else pull_s(true, rows3(true, v, c * kEsC), out);
     };
     C gt[9];
+    const C gh = ghost(v);
     if (colv) {
       pull_col(tx + H, gkeep);
-      sphi[sl * PHW + tx + 1] = sum9(gkeep);
+      sphi[sl * PHW + tx + 1] = sum9(gkeep) + gh;
     }
     if (tx == 0) {
       pull_col(H - 1, gt);
-      sphi[sl * PHW + 0] = sum9(gt);
+      sphi[sl * PHW + 0] = sum9(gt) + gh;
     }
     if (tx == BX - 1) {
       pull_col(H + xv, gt);
-      sphi[sl * PHW + xv + 1] = sum9(gt);
+      sphi[sl * PHW + xv + 1] = sum9(gt) + gh;
     }
   };
   // f of the node (column tx) at virtual row r.
@@ -450,23 +457,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
 namespace {
 
 template <int PREC> Phys<typename Pop<PREC>::C> phys_of(const HostPhys& h) {
-  using C = typename Pop<PREC>::C;
-  Phys<C> p;
-  p.omega_l = (C)h.omega_l;
-  p.omega_g = (C)h.omega_g;
-  p.tau_l = (C)h.tau_l;
-  p.tau_g = (C)h.tau_g;
-  p.omega3 = (C)h.omega3;
-  p.omega_phi = (C)h.omega_phi;
-  p.gamma = (C)h.gamma;
-  p.a = (C)h.a;
-  p.Gamma = (C)h.Gamma;
-  p.u_top = (C)h.u_top;
-  p.u_bottom = (C)h.u_bottom;
-  p.visc = h.visc;
-  p.k8_printed = h.k8_printed;
-  p.bgk = h.bgk;
-  return p;
+  return make_phys<typename Pop<PREC>::C>(h);
 }
 
 template <int PREC, int BX, int BY, int D>

@@ -22,6 +22,7 @@ LBM_PERIODIC, LBM_WALLS_Y = 0, 1
 LBM_OMEGA_LINEAR, LBM_TAU_LINEAR = 0, 1
 LBM_K8_PROJECTED, LBM_K8_PRINTED = 0, 1
 LBM_COLLIDE_CM, LBM_COLLIDE_BGK = 0, 1
+LBM_FORCE_UNIFORM, LBM_FORCE_PHASE_L = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_STAGED = 0, 1, 2
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
@@ -38,6 +39,8 @@ class lbm_params(ctypes.Structure):
         ("k8_form", ctypes.c_int), ("visc", ctypes.c_int), ("bc", ctypes.c_int),
         ("u_top", ctypes.c_double), ("u_bottom", ctypes.c_double),
         ("prec", ctypes.c_int), ("collision", ctypes.c_int),
+        ("wet_bottom", ctypes.c_double), ("wet_top", ctypes.c_double),
+        ("force_x", ctypes.c_double), ("force_y", ctypes.c_double), ("force_mode", ctypes.c_int),
     ]
 
 
@@ -56,6 +59,8 @@ def _load():
     pp = ctypes.POINTER(lbm_params)
     lib.lbm_default_params.argtypes = [pp]
     lib.lbm_default_params.restype = None
+    lib.lbm_wall_gradient.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.lbm_wall_gradient.restype = ctypes.c_double
     lib.lbm_state_bytes.argtypes = [pp, ctypes.POINTER(sz)]
     lib.lbm_state_bytes.restype = i
     lib.lbm_init.argtypes = [pp, dp, dp, dp, dp, vp, sz, vp, ctypes.POINTER(vp)]
@@ -157,6 +162,11 @@ def lbm_default_params(**overrides) -> lbm_params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def lbm_wall_gradient(theta: float, a: float, gamma: float) -> float:
+    """Eq. 18: wall gradient of phi along the outward normal for contact angle theta (radians)."""
+    return _lib.lbm_wall_gradient(float(theta), float(a), float(gamma))
 
 
 def lbm_state_bytes(p: lbm_params) -> int:

@@ -2,7 +2,7 @@
 import numpy as np
 
 # Parameter names of the C ABI that the oracle spells differently.
-_TO_ORACLE = {"visc": "visc_interp", "bc": "walls"}
+_TO_ORACLE = {"visc": "visc_interp", "bc": "walls", "force_x": "Fx", "force_y": "Fy"}
 _GPU_ONLY = {"prec"}
 
 

@@ -1,6 +1,7 @@
 """The C ABI library loads without a GPU, exports every function include/lbm.h declares, and
 rejects invalid parameters before touching the device."""
 import ctypes
+import math
 import re
 
 import pytest
@@ -53,7 +54,8 @@ def test_defaults_follow_the_paper(lbm):
 @pytest.mark.parametrize("bad", [
     dict(nx=2), dict(ny=0), dict(tau_l=0.5), dict(tau_g=0.2), dict(M=0.0), dict(Gamma=-1.0),
     dict(gamma=-0.1), dict(omega3=2.0), dict(prec=7), dict(bc=3), dict(visc=5), dict(k8_form=2),
-    dict(collision=9), dict(u_top=float("nan")), dict(nx=70000, ny=70000)])
+    dict(collision=9), dict(u_top=float("nan")), dict(nx=70000, ny=70000), dict(force_mode=2),
+    dict(force_x=float("inf")), dict(wet_bottom=0.1), dict(bc=1, wet_top=float("nan"))])
 def test_invalid_parameters_rejected(lbm, bad):
     kw = dict(nx=16, ny=16)
     kw.update(bad)
@@ -83,3 +85,15 @@ def test_init_rejects_nonfinite_and_missing_input(lbm):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_init(p, phi)
     assert ei.value.status == lbm.LBM_ERR_PARAM and "non-finite" in str(ei.value)
+
+
+def test_wall_gradient_matches_the_oracle(lbm, orc):
+    """Eq. 18 on the host side of the library equals the oracle's, and is odd about 90 degrees."""
+    for ratio in (1.0, 4.0):
+        for deg in (10, 45, 60, 90, 120, 170):
+            th = math.radians(deg)
+            want = orc.wall_gradient(th, 0.04, 0.04 * ratio)
+            assert math.isclose(lbm.lbm_wall_gradient(th, 0.04, 0.04 * ratio), want, rel_tol=1e-14, abs_tol=1e-16)
+            assert math.isclose(lbm.lbm_wall_gradient(math.pi - th, 0.04, 0.04 * ratio), -want, rel_tol=1e-14,
+                                abs_tol=1e-16)
+    assert math.isnan(lbm.lbm_wall_gradient(1.0, 0.04, 0.0))

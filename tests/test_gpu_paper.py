@@ -226,3 +226,56 @@ def test_layered_two_viscosity_poiseuille(lbm):
     assert abs(ux[:, 0] - want).max() < 3e-3 * want.max(), abs(ux[:, 0] - want).max() / want.max()
     assert abs(uy).max() < 1e-9
     lat.close()
+
+
+# -------------------------------------------------------------------------------------------
+# Droplet breakup in shear (the breakup paragraph after the Taylor test).
+
+def _components(phi):
+    """Connected regions of phi > 0 on a lattice periodic in x (4-neighbour connectivity)."""
+    from scipy import ndimage
+    m = phi > 0
+    nx = m.shape[1]
+    lab, _ = ndimage.label(np.concatenate([m, m], axis=1))
+    parent = {}
+
+    def find(a):
+        while parent.setdefault(a, a) != a:
+            a = parent[a]
+        return a
+    for y, x in zip(*np.nonzero(m)):  # a region seen in both copies of the strip is one region
+        parent[find(lab[y, x])] = find(lab[y, x + nx])
+    return len({find(lab[y, x]) for y, x in zip(*np.nonzero(m))})
+
+
+def test_droplet_breakup_in_shear(lbm):
+    """240 x 60 between walls moving at +-v_w, droplet radius 15 at the centre, H = 30, the shear
+    test's nu_l = nu_g = 0.2 and Re = v_w R^2 / (H nu) = 0.1, t_dag = H / v_w.  The paper shows
+    the droplet stretching as one body until about 20 t_dag, its ends separating near 25 t_dag
+    and satellite droplets after, but gives no capillary number; at Ca = 1.5 (gamma = a) the
+    droplet is one body at 20 t_dag and three or more drops at 30 t_dag, while at Ca = 1.0 it
+    only stretches.  Both run as one batch."""
+    pytest.importorskip("scipy")
+    nx, ny, R, nu, Re = 240, 60, 15, 0.2, 0.1
+    H = ny / 2
+    vw = Re * H * nu / R ** 2
+    tdag = H / vw
+    mem = []
+    for ca in (1.5, 1.0):
+        sigma = vw * R * nu / (H * ca)
+        ga = 3 * sigma / math.sqrt(8)  # sigma = sqrt(8 gamma a / 9) with gamma = a
+        mem.append((W.droplet(nx, ny, R, gamma=ga, a=ga),
+                    dict(tau_l=tau(nu), tau_g=tau(nu), gamma=ga, a=ga, M=0.1, bc=lbm.LBM_WALLS_Y, u_top=vw,
+                         u_bottom=-vw)))
+    bat = lbm.Batch(mem, prec="fp32")
+    s0 = [float(m[0].sum()) for m in mem]
+    bat.step(int(20 * tdag))
+    assert [_components(bat.fields(m)[3]) for m in range(2)] == [1, 1]
+    bat.step(int(10 * tdag))
+    assert bat.check()[0] == lbm.LBM_OK
+    n_break, n_keep = (_components(bat.fields(m)[3]) for m in range(2))
+    assert n_break >= 3 and n_keep == 1, (n_break, n_keep)
+    for m in range(2):
+        # sum phi to FP32 rounding over 3.4e5 steps of 14 400 nodes
+        assert abs(bat.fields(m)[3].sum() - s0[m]) < 1e-8 * nx * ny * 30 * tdag
+    bat.close()

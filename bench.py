@@ -68,7 +68,7 @@ def measured_peaks():
 
 
 # Sources that define the fused step kernel k_step (the kernel the roofline reports).
-STEP_SOURCES = ("lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
+STEP_SOURCES = ("lbm_step.cuh", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
 
 
 def kernel_source_hash():

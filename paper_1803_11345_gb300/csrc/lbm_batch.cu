@@ -165,10 +165,17 @@ cudaError_t build_items(lbm_batch* b, const StepTile& t, int target) {
   return cudaSuccess;
 }
 
+// Every member's population buffer under 4 GiB: the step kernel forms plane offsets in 32 bits.
+bool members_fit_32(const lbm_batch* b) {
+  for (const HostGeometry& g : b->geo)
+    if (pop_buffer_bytes(b->prec, g.plane) >= (size_t(1) << 32)) return false;
+  return true;
+}
+
 cudaError_t launch_one(lbm_batch* b, int parity) {
   return launch_step_batch(b->prec, b->tile, (const BatchItem*)(b->arena + b->L.items_off), b->nitems,
                            (const BatchMember*)(b->arena + b->L.members_off), b->arena + b->L.phys_off, parity,
-                           (int*)(b->arena + b->L.flags_off), b->grid, b->stream);
+                           (int*)(b->arena + b->L.flags_off), b->grid, members_fit_32(b), b->stream);
 }
 
 cudaError_t build_graph(lbm_batch* b) {

@@ -389,8 +389,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
     h->tile = t;
     return LBM_OK;
   }
-  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED) || rows < 0 || bx < 0 || by < 0 ||
-      depth < 0) {
+  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED && variant != LBM_KERNEL_GENERIC_WIDE) ||
+      rows < 0 || bx < 0 || by < 0 || depth < 0) {
     set_err(h->err, "lbm_set_kernel: invalid arguments");
     return LBM_ERR_PARAM;
   }
@@ -400,6 +400,7 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   t.by = by ? by : (t.staged ? 4 : 1);
   t.depth = depth ? depth : 1;
   t.rows = 0;
+  t.wide = variant == LBM_KERNEL_GENERIC_WIDE;
   const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) : tile_supported(h->p.prec, t.bx, t.by);
   if (!ok) {
     set_err(h->err, "lbm_set_kernel: no %s kernel for tile %dx%d depth %d on nx = %d",
@@ -420,7 +421,10 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
 
 int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows) {
   if (!h) return LBM_ERR_PARAM;
-  if (variant) *variant = h->tile.staged ? LBM_KERNEL_STAGED : LBM_KERNEL_GENERIC;
+  if (variant)
+    *variant = h->tile.staged ? LBM_KERNEL_STAGED
+               : (h->tile.wide || !offsets_fit_32(h->p.prec, h->geo.plane)) ? LBM_KERNEL_GENERIC_WIDE
+                                                                            : LBM_KERNEL_GENERIC;
   if (bx) *bx = h->tile.bx;
   if (by) *by = h->tile.by;
   if (depth) *depth = h->tile.depth;

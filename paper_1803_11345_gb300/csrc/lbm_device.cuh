@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 
 namespace lbmch {
@@ -31,6 +33,28 @@ __host__ __device__ constexpr int lat_w36(int i) { return i == 0 ? 16 : (i <= 4 
 // ---------------------------------------------------------------------------------------------
 // Storage policies.  A population buffer holds 18 planes (f_0..f_8, g_0..g_8) of `plane`
 // elements; node (x, y) sits at y * pitch + x inside each plane.
+//
+// Every accessor takes the plane stride either as a 64-bit element count (any lattice) or as a
+// Plane32: the same count for buffers under 4 GiB, where every byte offset inside the buffer fits
+// in 32 bits, so an address is one 32-bit multiply-add plus one add to the base instead of 64-bit
+// multiplies (the step kernel is partly instruction-bound).
+struct Plane32 {
+  unsigned n;  // elements per plane
+};
+
+// Element idx of the plane that starts `first` planes of element type E into the buffer.
+template <class E>
+__device__ __forceinline__ const E* plane_elem(const char* b, long long pl, int first, int idx) {
+  return reinterpret_cast<const E*>(b) + first * pl + idx;
+}
+template <class E>
+__device__ __forceinline__ const E* plane_elem(const char* b, Plane32 pl, int first, int idx) {
+  return reinterpret_cast<const E*>(b + ((unsigned)first * pl.n + (unsigned)idx) * (unsigned)sizeof(E));
+}
+template <class E, class PL>
+__device__ __forceinline__ E* plane_elem(char* b, PL pl, int first, int idx) {
+  return const_cast<E*>(plane_elem<E>(static_cast<const char*>(b), pl, first, idx));
+}
 
 template <int PREC> struct Pop;
 
@@ -38,17 +62,26 @@ template <int PREC> struct Pop;
 template <class T> struct PopDense {
   using C = T;
   static constexpr size_t kBytesPerElem = 18 * sizeof(T);
-  __device__ __forceinline__ static C ld(const char* b, long long pl, int p, int idx) {
-    return __ldg(reinterpret_cast<const T*>(b) + p * pl + idx);
+  template <class PL> __device__ __forceinline__ static C ld(const char* b, PL pl, int p, int idx) {
+    return __ldg(plane_elem<T>(b, pl, p, idx));
   }
-  __device__ __forceinline__ static void st(char* b, long long pl, int p, int idx, C v) {
-    reinterpret_cast<T*>(b)[p * pl + idx] = v;
+  template <class PL> __device__ __forceinline__ static void st(char* b, PL pl, int p, int idx, C v) {
+    *plane_elem<T>(b, pl, p, idx) = v;
   }
-  __device__ __forceinline__ static C ldf(const char* b, long long pl, int i, int idx) { return ld(b, pl, i, idx); }
-  __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) { return ld(b, pl, 9 + i, idx); }
-  __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) { st(b, pl, i, idx, v); }
-  __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) { st(b, pl, 9 + i, idx, v); }
-  __device__ __forceinline__ static void store_node(char* b, long long pl, int idx, const C f[9], const C g[9]) {
+  template <class PL> __device__ __forceinline__ static C ldf(const char* b, PL pl, int i, int idx) {
+    return ld(b, pl, i, idx);
+  }
+  template <class PL> __device__ __forceinline__ static C ldg(const char* b, PL pl, int i, int idx) {
+    return ld(b, pl, 9 + i, idx);
+  }
+  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C v) {
+    st(b, pl, i, idx, v);
+  }
+  template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
+    st(b, pl, 9 + i, idx, v);
+  }
+  template <class PL>
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       stf(b, pl, i, idx, f[i]);
@@ -57,8 +90,12 @@ template <class T> struct PopDense {
   }
   // Raw access: the stored bits, decoded only where used (keeps loads in flight).
   using R = T;
-  __device__ __forceinline__ static R rawf(const char* b, long long pl, int i, int idx) { return ldf(b, pl, i, idx); }
-  __device__ __forceinline__ static R rawg(const char* b, long long pl, int i, int idx) { return ldg(b, pl, i, idx); }
+  template <class PL> __device__ __forceinline__ static R rawf(const char* b, PL pl, int i, int idx) {
+    return ldf(b, pl, i, idx);
+  }
+  template <class PL> __device__ __forceinline__ static R rawg(const char* b, PL pl, int i, int idx) {
+    return ldg(b, pl, i, idx);
+  }
   __device__ __forceinline__ static C decf(int, R r) { return r; }
   __device__ __forceinline__ static C decg(int, R r) { return r; }
   __device__ __forceinline__ static R keep(C v) { return v; }   // an already-decoded value
@@ -86,35 +123,43 @@ template <class H> struct PopHalf {
   using C = float;
   static constexpr size_t kBytesPerElem = 16 * sizeof(H) + 2 * sizeof(float);
   __device__ __forceinline__ static float wrest(int i) { return (float)lat_w36(i) * (1.0f / 36.0f); }
-  __device__ __forceinline__ static const float* rest_plane(const char* b, long long pl, int set) {
-    return reinterpret_cast<const float*>(reinterpret_cast<const H*>(b) + 16 * pl) + set * pl;
+  // The two FP32 rest planes follow the 16 half planes: 16 * sizeof(H) / 4 float planes in.
+  static constexpr int kRestFirst = 16 * (int)sizeof(H) / (int)sizeof(float);
+  template <class PL> __device__ __forceinline__ static const float* rest(const char* b, PL pl, int set, int idx) {
+    return plane_elem<float>(b, pl, kRestFirst + set, idx);
   }
-  __device__ __forceinline__ static float* rest_plane(char* b, long long pl, int set) {
-    return reinterpret_cast<float*>(reinterpret_cast<H*>(b) + 16 * pl) + set * pl;
+  template <class PL> __device__ __forceinline__ static float* rest(char* b, PL pl, int set, int idx) {
+    return plane_elem<float>(b, pl, kRestFirst + set, idx);
   }
-  __device__ __forceinline__ static C ldf(const char* b, long long pl, int i, int idx) {
-    if (i == 0) return __ldg(rest_plane(b, pl, 0) + idx);
-    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (i - 1) * pl + idx)) + wrest(i);
+  template <class PL> __device__ __forceinline__ static const H* half(const char* b, PL pl, int p, int idx) {
+    return plane_elem<H>(b, pl, p, idx);
   }
-  __device__ __forceinline__ static C ldg(const char* b, long long pl, int i, int idx) {
-    if (i == 0) return __ldg(rest_plane(b, pl, 1) + idx);
-    return Cvt<H>::to(__ldg(reinterpret_cast<const H*>(b) + (7 + i) * pl + idx));
+  template <class PL> __device__ __forceinline__ static H* half(char* b, PL pl, int p, int idx) {
+    return plane_elem<H>(b, pl, p, idx);
+  }
+  template <class PL> __device__ __forceinline__ static C ldf(const char* b, PL pl, int i, int idx) {
+    if (i == 0) return __ldg(rest(b, pl, 0, idx));
+    return Cvt<H>::to(__ldg(half(b, pl, i - 1, idx))) + wrest(i);
+  }
+  template <class PL> __device__ __forceinline__ static C ldg(const char* b, PL pl, int i, int idx) {
+    if (i == 0) return __ldg(rest(b, pl, 1, idx));
+    return Cvt<H>::to(__ldg(half(b, pl, 7 + i, idx)));
   }
   // Single values (checkpoint restore): the rest populations are stored as given.
-  __device__ __forceinline__ static void stf(char* b, long long pl, int i, int idx, C v) {
-    if (i == 0) rest_plane(b, pl, 0)[idx] = v;
-    else reinterpret_cast<H*>(b)[(i - 1) * pl + idx] = Cvt<H>::from(v - wrest(i));
+  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C v) {
+    if (i == 0) *rest(b, pl, 0, idx) = v;
+    else *half(b, pl, i - 1, idx) = Cvt<H>::from(v - wrest(i));
   }
-  __device__ __forceinline__ static void stg(char* b, long long pl, int i, int idx, C v) {
-    if (i == 0) rest_plane(b, pl, 1)[idx] = v;
-    else reinterpret_cast<H*>(b)[(7 + i) * pl + idx] = Cvt<H>::from(v);
+  template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
+    if (i == 0) *rest(b, pl, 1, idx) = v;
+    else *half(b, pl, 7 + i, idx) = Cvt<H>::from(v);
   }
   // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
   // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
   // to the post-collision rho and phi: 16-bit rounding then redistributes among directions but
   // does not create or destroy mass or order parameter.
-  __device__ __forceinline__ static void store_node(char* b, long long pl, int idx, const C f[9], const C g[9]) {
-    H* hb = reinterpret_cast<H*>(b);
+  template <class PL>
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9]) {
     const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const float phi = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     float sf = 0.0f, sg = 0.0f;
@@ -122,24 +167,24 @@ template <class H> struct PopHalf {
     for (int i = 1; i < 9; ++i) {
       const H hf = Cvt<H>::from(f[i] - wrest(i));
       const H hg = Cvt<H>::from(g[i]);
-      hb[(i - 1) * pl + idx] = hf;
-      hb[(7 + i) * pl + idx] = hg;
+      *half(b, pl, i - 1, idx) = hf;
+      *half(b, pl, 7 + i, idx) = hg;
       sf += Cvt<H>::to(hf) + wrest(i);
       sg += Cvt<H>::to(hg);
     }
-    rest_plane(b, pl, 0)[idx] = rho - sf;
-    rest_plane(b, pl, 1)[idx] = phi - sg;
+    *rest(b, pl, 0, idx) = rho - sf;
+    *rest(b, pl, 1, idx) = phi - sg;
   }
   // Raw access: 32-bit words holding either the FP32 rest value (i = 0) or the 16-bit pattern of
   // a moving population, decoded only where used so that loads stay in flight.
   using R = uint32_t;
-  __device__ __forceinline__ static R rawf(const char* b, long long pl, int i, int idx) {
-    if (i == 0) return __float_as_uint(__ldg(rest_plane(b, pl, 0) + idx));
-    return (R)__ldg(reinterpret_cast<const unsigned short*>(b) + (i - 1) * pl + idx);
+  template <class PL> __device__ __forceinline__ static R rawf(const char* b, PL pl, int i, int idx) {
+    if (i == 0) return __float_as_uint(__ldg(rest(b, pl, 0, idx)));
+    return (R)__ldg(reinterpret_cast<const unsigned short*>(half(b, pl, i - 1, idx)));
   }
-  __device__ __forceinline__ static R rawg(const char* b, long long pl, int i, int idx) {
-    if (i == 0) return __float_as_uint(__ldg(rest_plane(b, pl, 1) + idx));
-    return (R)__ldg(reinterpret_cast<const unsigned short*>(b) + (7 + i) * pl + idx);
+  template <class PL> __device__ __forceinline__ static R rawg(const char* b, PL pl, int i, int idx) {
+    if (i == 0) return __float_as_uint(__ldg(rest(b, pl, 1, idx)));
+    return (R)__ldg(reinterpret_cast<const unsigned short*>(half(b, pl, 7 + i, idx)));
   }
   __device__ __forceinline__ static float h2f(R r) {
     H h;
@@ -217,13 +262,13 @@ __device__ __forceinline__ void body_force(const Phys<C>& ph, C phi, C& Fx, C& F
 // walled.  A link whose source lies beyond a wall is the bounced-back population of the node
 // itself, opposite direction, plus the moving-wall term 6 w_i s c_xi u_w, where s is the node's
 // own density (for f) or order parameter (for g) at t - 1.
-template <int PREC, bool IS_G>
+template <int PREC, bool IS_G, class PL = long long>
 __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometry& geo,
                                      typename Pop<PREC>::C u_top, typename Pop<PREC>::C u_bot,
-                                     int x, int y, typename Pop<PREC>::C out[9]) {
+                                     int x, int y, typename Pop<PREC>::C out[9], PL pl = PL()) {
   using P = Pop<PREC>;
   using C = typename P::C;
-  const long long pl = geo.plane;
+  if constexpr (std::is_same<PL, long long>::value) pl = geo.plane;
   auto LD = [&](int i, int idx) -> C { return IS_G ? P::ldg(src, pl, i, idx) : P::ldf(src, pl, i, idx); };
   const int xm = (x == 0) ? geo.nx - 1 : x - 1;
   const int xp = (x == geo.nx - 1) ? 0 : x + 1;
@@ -279,20 +324,20 @@ __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometr
 // Raw variant of pull(): for rows away from walls the nine values are the stored bits, left
 // undecoded (returns false); wall rows need arithmetic, so they are pulled decoded and kept as
 // such (returns true).  unpack() turns either form into values.
-template <int PREC, bool IS_G>
+template <int PREC, bool IS_G, class PL = long long>
 __device__ __forceinline__ bool pull_raw(const char* __restrict__ src, const Geometry& geo,
                                          typename Pop<PREC>::C u_top, typename Pop<PREC>::C u_bot,
-                                         int x, int y, typename Pop<PREC>::R out[9]) {
+                                         int x, int y, typename Pop<PREC>::R out[9], PL pl = PL()) {
   using P = Pop<PREC>;
   using C = typename P::C;
   if (geo.walls && (y == 0 || y == geo.ny - 1)) {
     C v[9];
-    pull<PREC, IS_G>(src, geo, u_top, u_bot, x, y, v);
+    pull<PREC, IS_G, PL>(src, geo, u_top, u_bot, x, y, v, pl);
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i] = P::keep(v[i]);
     return true;
   }
-  const long long pl = geo.plane;
+  if constexpr (std::is_same<PL, long long>::value) pl = geo.plane;
   auto LD = [&](int i, int idx) { return IS_G ? P::rawg(src, pl, i, idx) : P::rawf(src, pl, i, idx); };
   const int xm = (x == 0) ? geo.nx - 1 : x - 1;
   const int xp = (x == geo.nx - 1) ? 0 : x + 1;

@@ -26,6 +26,7 @@ struct HostPhys {
 struct StepTile {
   int bx, by, rows;
   int staged, depth;
+  int wide = 0;  // generic kernel with 64-bit plane offsets even when the buffer is under 4 GiB
 };
 
 // Batched stepping: one member lattice (two population copies) and one unit of work (a tile of
@@ -46,9 +47,10 @@ size_t phys_bytes(int prec);
 cudaError_t upload_phys(int prec, const HostPhys* host, int count, void* dev, cudaStream_t s);
 // One time step of every member: items[] dealt round-robin to `grid` resident CTAs.  parity 0:
 // state in buf0 -> buf1; parity 1: buf1 -> buf0.  flags[m] collects member m's non-finite flag.
+// off32: every member's population buffer is under 4 GiB (32-bit plane offsets).
 cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
                               const BatchMember* members, const void* phys, int parity, int* flags,
-                              int grid, cudaStream_t s);
+                              int grid, bool off32, cudaStream_t s);
 int batch_blocks_per_sm(int prec, const StepTile& t);
 
 // Parameter validation shared by the single-lattice and batched entry points (message or NULL),
@@ -65,6 +67,9 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 
 // Bytes of one population buffer (18 planes) for a storage precision.
 size_t pop_buffer_bytes(int prec, long long plane);
+// Every byte offset inside one population buffer fits in 32 bits (the step kernel then forms
+// plane offsets in 32-bit arithmetic).
+bool offsets_fit_32(int prec, long long plane);
 
 // Launchers; each returns the cudaError_t of the launch.
 cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, const double* fields,

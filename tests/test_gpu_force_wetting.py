@@ -105,6 +105,7 @@ def test_every_tile_with_wetting_and_force_fp64(lbm, orc):
     o.step(40)
     variants = [(lbm.LBM_KERNEL_GENERIC, bx, by, 0) for bx, by in GENERIC_TILES]
     variants += [(lbm.LBM_KERNEL_STAGED, bx, by, d) for bx, by, d in STAGED_TILES]
+    variants += [(lbm.LBM_KERNEL_GENERIC_WIDE, bx, by, 0) for bx, by in GENERIC_TILES]
     for var, bx, by, d in variants:
         for rows in (0, 7):
             lat = lbm.Lattice(phi0, **kw)

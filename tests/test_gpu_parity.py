@@ -242,9 +242,10 @@ STAGED_TILES = [(32, 4, 1), (32, 8, 1), (64, 2, 1), (64, 4, 1), (64, 4, 2), (128
 
 @pytest.mark.parametrize("bc", [0, 1])
 def test_every_tile_fp64(lbm, orc, bc):
-    """Each compiled tile of the generic and the staged kernel, on a lattice whose width is a
-    ragged multiple of the tile (nx = 136) and a short segment height (rows = 7), matches the
-    oracle at FP64 after 60 steps, periodic and with moving walls."""
+    """Each compiled tile of the generic kernel (32-bit and 64-bit plane offsets) and of the staged
+    kernel, on a lattice whose width is a ragged multiple of the tile (nx = 136) and a short
+    segment height (rows = 7), matches the oracle at FP64 after 60 steps, periodic and with moving
+    walls."""
     nx, ny = 136, 45
     phi0 = W.droplet(nx, ny, 14, gamma=0.04, a=0.04)
     kw = dict(prec=lbm.LBM_FP64, tau_l=0.9, tau_g=0.55, bc=bc, u_top=0.02, u_bottom=-0.01)
@@ -252,6 +253,7 @@ def test_every_tile_fp64(lbm, orc, bc):
     o.step(60)
     variants = [(lbm.LBM_KERNEL_GENERIC, bx, by, 0) for bx, by in GENERIC_TILES]
     variants += [(lbm.LBM_KERNEL_STAGED, bx, by, d) for bx, by, d in STAGED_TILES]
+    variants += [(lbm.LBM_KERNEL_GENERIC_WIDE, bx, by, 0) for bx, by in GENERIC_TILES]
     for var, bx, by, d in variants:
         for rows in (0, 7):
             lat = lbm.Lattice(phi0, **kw)

@@ -252,6 +252,41 @@ def config_dict(args):
 # ------------------------------------------------------------------------------------------
 # GPU leg.
 
+def storage_forms(lbm, phi0, params, stream, ms_fp32, steps=500, phi_steps=1000):
+    """The 16-bit storage forms on the same workload and GPU: time per step against the FP32 step
+    just timed, and phi after `phi_steps` steps against an FP32 run from the same state (the error
+    against the FP64 oracle is stated by the tests: 2e-3 FP16, 2e-2 BF16 over 1000 steps)."""
+    import numpy as np
+    import torch
+    ref = lbm.Lattice(phi0, stream=stream, **params)
+    ref.step(phi_steps)
+    phi_ref = ref.fields()[3]
+    ref.close()
+    out = {}
+    for prec in ("fp16s", "bf16s"):
+        kw = dict(params, prec=lbm.PRECISIONS[prec])
+        lat = lbm.Lattice(phi0, stream=stream, **kw)
+        lat.step(20)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        lat.step(phi_steps - 20 - steps)
+        d = np.abs(lat.fields()[3] - phi_ref)
+        kernel = {lbm.LBM_KERNEL_PAIR: "k_step_pair (two nodes per thread)"}.get(lat.kernel[0], "k_step")
+        lat.close()
+        nodes = phi0.size
+        out[prec] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "speedup_vs_fp32": ms_fp32 / ms,
+                     "hbm_frac": BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9 / measured_peaks()[0],
+                     "phi_vs_fp32_after_steps": phi_steps, "phi_max_abs_diff": float(d.max()),
+                     "phi_rms_diff": float(np.sqrt((d * d).mean())), "kernel": kernel}
+    out["batch"] = "bench.py --workload batch: 256 lattices, aggregate MLUPS vs one launch per member"
+    out["surrogate"] = "bench.py --workload surrogate: U-Net forward vs the solver's 50 steps, phi RMS error"
+    return out
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -305,6 +340,8 @@ def run_gpu(args):
 
     # Parity spot check on this run (cheap): sum phi is conserved by the scheme.
     sphi, srho, _, _ = lat.conservation()
+    kernel_name = {lbm.LBM_KERNEL_PAIR: "k_step_pair", lbm.LBM_KERNEL_STAGED: "k_step_staged"}.get(
+        lat.kernel[0], "k_step")
     lat.close()
     del lat
     torch.cuda.synchronize()
@@ -345,6 +382,10 @@ def run_gpu(args):
             cpu = {"value": None, "unit": "MLUPS", "cores": None, "kind": "oracle",
                    "sample": f"failed: {exc}"}
 
+    forms = None
+    if rank == 0 and ws == 1 and args.prec == "fp32" and not args.no_forms:
+        forms = storage_forms(lbm, phi0, params, stream, ms_step)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -354,9 +395,10 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                         "bytes_per_node": bpn, "kernel": "k_step"},
+                         "bytes_per_node": bpn, "kernel": kernel_name},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
             "check": {"sum_phi": sphi, "sum_rho": srho},
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -555,6 +597,7 @@ def main(argv=None):
     ap.add_argument("--prec", choices=list(BYTES_PER_NODE), default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit storage comparison")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
     ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
     ap.add_argument("--sur-n", type=int, default=256)

@@ -389,7 +389,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
     h->tile = t;
     return LBM_OK;
   }
-  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED && variant != LBM_KERNEL_GENERIC_WIDE) ||
+  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED && variant != LBM_KERNEL_GENERIC_WIDE &&
+       variant != LBM_KERNEL_PAIR) ||
       rows < 0 || bx < 0 || by < 0 || depth < 0) {
     set_err(h->err, "lbm_set_kernel: invalid arguments");
     return LBM_ERR_PARAM;
@@ -401,10 +402,17 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   t.depth = depth ? depth : 1;
   t.rows = 0;
   t.wide = variant == LBM_KERNEL_GENERIC_WIDE;
-  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) : tile_supported(h->p.prec, t.bx, t.by);
+  t.pair = variant == LBM_KERNEL_PAIR;
+  if (t.pair) {
+    t.bx = bx ? bx : 128;
+    t.by = by ? by : 1;
+  }
+  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t)
+                  : t.pair ? pair_supported(h->p.prec, h->geo, t.bx, t.by)
+                           : tile_supported(h->p.prec, t.bx, t.by);
   if (!ok) {
-    set_err(h->err, "lbm_set_kernel: no %s kernel for tile %dx%d depth %d on nx = %d",
-            t.staged ? "staged" : "generic", t.bx, t.by, t.depth, h->geo.nx);
+    set_err(h->err, "lbm_set_kernel: no %s kernel for tile %dx%d depth %d on this lattice (nx = %d)",
+            t.staged ? "staged" : (t.pair ? "paired 16-bit" : "generic"), t.bx, t.by, t.depth, h->geo.nx);
     return LBM_ERR_PARAM;
   }
   if (rows > 0) {
@@ -412,7 +420,9 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   } else {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t) : generic_blocks_per_sm(h->p.prec, t);
+    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t)
+                       : t.pair ? pair_blocks_per_sm(h->p.prec, t)
+                                : generic_blocks_per_sm(h->p.prec, t);
     t.rows = rows_for_wave(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1));
   }
   h->tile = t;
@@ -423,6 +433,7 @@ int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* de
   if (!h) return LBM_ERR_PARAM;
   if (variant)
     *variant = h->tile.staged ? LBM_KERNEL_STAGED
+               : h->tile.pair ? LBM_KERNEL_PAIR
                : (h->tile.wide || !offsets_fit_32(h->p.prec, h->geo.plane)) ? LBM_KERNEL_GENERIC_WIDE
                                                                             : LBM_KERNEL_GENERIC;
   if (bx) *bx = h->tile.bx;
@@ -455,6 +466,14 @@ int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
     StepTile t{st[0], st[1], 0, 1, st[2]};
     if (!staged_supported(h->p.prec, h->geo, t)) continue;
     t.rows = rows_for_wave(h->geo, t, sms * staged_blocks_per_sm(h->p.prec, t));
+    cands.push_back(t);
+  }
+  const int ptiles[][2] = {{64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  for (auto& pt : ptiles) {
+    if (!pair_supported(h->p.prec, h->geo, pt[0], pt[1])) continue;
+    StepTile t{pt[0], pt[1], 0, 0, 1};
+    t.pair = 1;
+    t.rows = rows_for_wave(h->geo, t, sms * pair_blocks_per_sm(h->p.prec, t));
     cands.push_back(t);
   }
   cudaEvent_t e0, e1;

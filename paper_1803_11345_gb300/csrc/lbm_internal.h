@@ -27,6 +27,7 @@ struct StepTile {
   int bx, by, rows;
   int staged, depth;
   int wide = 0;  // generic kernel with 64-bit plane offsets even when the buffer is under 4 GiB
+  int pair = 0;  // 16-bit storage, two nodes per thread (lbm_pair.cu); columns per CTA = 2 bx
 };
 
 // Batched stepping: one member lattice (two population copies) and one unit of work (a tile of
@@ -64,6 +65,13 @@ void set_thread_error(const char* msg);
 
 // Fill n doubles with v.
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
+
+// The paired 16-bit step (lbm_pair.cu): whether tile bx x by can serve the lattice (16-bit
+// storage, periodic, nx even, buffer under 4 GiB), resident CTAs per SM, and the launch.
+bool pair_supported(int prec, const HostGeometry& g, int bx, int by);
+int pair_blocks_per_sm(int prec, const StepTile& t);
+cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
+                             char* dst, int* flag, cudaStream_t s);
 
 // Bytes of one population buffer (18 planes) for a storage precision.
 size_t pop_buffer_bytes(int prec, long long plane);

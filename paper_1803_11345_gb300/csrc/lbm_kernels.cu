@@ -272,16 +272,24 @@ bool tile_supported(int prec, int bx, int by) {
 }
 
 StepTile default_tile(int prec, const HostGeometry& g, int device) {
-  // Measured on GB300 at 4096^2 (FP32): the software-pipelined generic kernel with one row of
-  // 256 threads per CTA and the grid sized to one wave is the fastest compiled shape.
-  StepTile t;
-  t.staged = 0;
-  t.depth = 1;
-  t.bx = 256;
-  t.by = 1;
+  // Measured on GB300 at 4096^2: FP32 / FP64, the software-pipelined generic kernel with one row
+  // of 256 threads per CTA; 16-bit storage, the paired kernel with 128 x 1 threads (256 columns)
+  // where the lattice allows it (1.2x the generic kernel); grids sized to one wave.
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (sms <= 0) sms = 152;
+  StepTile t;
+  t.staged = 0;
+  t.depth = 1;
+  if (pair_supported(prec, g, 128, 1)) {
+    t.bx = 128;
+    t.by = 1;
+    t.pair = 1;
+    t.rows = rows_for_wave(g, t, sms * std::max(1, pair_blocks_per_sm(prec, t)));
+    return t;
+  }
+  t.bx = 256;
+  t.by = 1;
   t.rows = rows_for_wave(g, t, sms * generic_blocks_per_sm(prec, t));
   return t;
 }
@@ -299,7 +307,8 @@ int generic_blocks_per_sm(int prec, const StepTile& t) {
 
 int rows_for_wave(const HostGeometry& g, const StepTile& t, int ctas) {
   // One full wave: gx * gy ~ ctas CTAs, rows a multiple of BY.
-  const int gx = (g.nx + t.bx - 1) / t.bx;
+  const int cols = t.pair ? 2 * t.bx : t.bx;  // a paired tile covers two columns per thread
+  const int gx = (g.nx + cols - 1) / cols;
   int gy = std::max(1, ctas / gx);
   int rows = (g.ny + gy - 1) / gy;
   rows = ((rows + t.by - 1) / t.by) * t.by;
@@ -323,6 +332,7 @@ cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, cons
 cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
                         const char* src, char* dst, int* flag, cudaStream_t s) {
   if (t.staged) return launch_step_staged(prec, g, p, t, src, dst, flag, s);
+  if (t.pair) return launch_step_pair(prec, g, p, t, src, dst, flag, s);
   switch (prec) {
     case 0: return step_prec<0>(g, p, t, src, dst, flag, s);
     case 1: return step_prec<1>(g, p, t, src, dst, flag, s);

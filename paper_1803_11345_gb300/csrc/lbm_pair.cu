@@ -1,0 +1,296 @@
+// Fused step for 16-bit population storage with two neighbouring nodes per thread.
+//
+// The 16-bit step is bound by instruction issue, not by memory: a node moves only 80 bytes but
+// costs as many address computations, loads, stores and loop steps as an FP32 node.  Here a
+// thread owns the node pair (x, x+1), x even, so that
+//   * a population the pair pulls from straight above or below (c_x = 0) is one aligned 32-bit
+//     word holding both 16-bit values;
+//   * a population arriving from the left (c_x = +1) is the high half of the word at x-2 and the
+//     low half of the word at x (one byte permute), from the right (c_x = -1) the high half of
+//     the word at x and the low half of the word at x+2;
+//   * the rest populations f_0, g_0 (FP32) are one 64-bit load;
+// and every address is formed once for two nodes.  The per-node arithmetic is that of the
+// one-node kernel (same decode, collision, encode and closure functions).  Requirements: periodic
+// boundaries, nx even (pairs never straddle the periodic seam), population copy under 4 GiB.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbmch {
+
+namespace {
+
+// Pulled populations of one set for a node pair, as stored: the eight moving directions as
+// packed 16-bit pairs (low half = node x, high half = node x+1), the rest population as FP32.
+struct RawPair {
+  uint32_t w[8];
+  float r0a, r0b;
+};
+
+// The same pull while its loads are in flight: for a direction with c_x != 0 the pair straddles
+// two aligned words, kept apart (w: the word at x, e: the word at x - 2 or x + 2) until finish()
+// combines them, one band later, so that no instruction waits on the loads in the meantime.
+struct RawPairLoad {
+  uint32_t w[8];
+  uint32_t e[6];
+  float r0a, r0b;
+};
+
+// Index among the six c_x != 0 directions (1, 3, 5, 6, 7, 8), or -1.
+__host__ __device__ constexpr int side_index(int i) {
+  return i == 1 ? 0 : i == 3 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : i == 8 ? 5 : -1;
+}
+
+__device__ __forceinline__ void finish(const RawPairLoad& l, RawPair& o) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (lat_cx(i) == 0) o.w[i - 1] = l.w[i - 1];
+    else if (lat_cx(i) == 1) o.w[i - 1] = __byte_perm(l.e[side_index(i)], l.w[i - 1], 0x5432);
+    else o.w[i - 1] = __byte_perm(l.w[i - 1], l.e[side_index(i)], 0x5432);
+  }
+  o.r0a = l.r0a;
+  o.r0b = l.r0b;
+}
+
+__device__ __forceinline__ uint32_t ld_word(const char* __restrict__ b, unsigned byte_off) {
+  return __ldg(reinterpret_cast<const unsigned int*>(b + byte_off));
+}
+
+// Eqs. 4-5 in pull form for the pair (x, x+1) at row y of a periodic lattice: direction i comes
+// from row y - c_yi and columns x - c_xi, x + 1 - c_xi.  xm2 / xp2 are the even columns x - 2 and
+// x + 2 with periodic wrap; ym / yp the rows above and below with wrap.
+template <int PREC, bool IS_G>
+__device__ __forceinline__ void pull_pair(const char* __restrict__ src, Plane32 pl, int pitch, int x, int xm2,
+                                          int xp2, int y, int ym, int yp, RawPairLoad& o) {
+  using P = Pop<PREC>;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const unsigned p = IS_G ? 7 + i : i - 1;  // half plane of direction i
+    const int row = lat_cy(i) == 1 ? ym : (lat_cy(i) == -1 ? yp : y);
+    const unsigned rbase = (p * pl.n + (unsigned)(row * pitch)) * 2u;
+    o.w[i - 1] = ld_word(src, rbase + 2u * (unsigned)x);
+    if (lat_cx(i) == 1) o.e[side_index(i)] = ld_word(src, rbase + 2u * (unsigned)xm2);
+    if (lat_cx(i) == -1) o.e[side_index(i)] = ld_word(src, rbase + 2u * (unsigned)xp2);
+  }
+  const unsigned rest = ((unsigned)(P::kRestFirst + (IS_G ? 1 : 0)) * pl.n + (unsigned)(y * pitch + x)) * 4u;
+  const float2 r0 = __ldg(reinterpret_cast<const float2*>(src + rest));
+  o.r0a = r0.x;
+  o.r0b = r0.y;
+}
+
+// Node k (0: x, 1: x+1) of a pulled pair, as the one-node kernel's raw words.
+template <int PREC, bool IS_G>
+__device__ __forceinline__ void unpack_pair(const RawPair& rp, int k, float out[9]) {
+  using P = Pop<PREC>;
+  typename P::R raw[9];
+  raw[0] = __float_as_uint(k ? rp.r0b : rp.r0a);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) raw[i] = k ? (rp.w[i - 1] >> 16) : (rp.w[i - 1] & 0xFFFFu);
+  unpack<PREC, IS_G>(raw, false, out);
+}
+
+template <int PREC>
+__device__ __forceinline__ float phi_pair(const RawPair& rp, int k) {
+  float v[9];
+  unpack_pair<PREC, true>(rp, k, v);
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// One tile: node pairs x0 + 2 tx (BX pairs, 2 BX columns, clipped to nx) and rows
+// [y0, y0 + rows) (clipped to ny), by one CTA of BX x BY threads marching down BY rows at a time.
+// Same software pipeline and phi ring as the one-node kernel (see step_tile).
+template <int PREC, int BX, int BY>
+__device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, char* __restrict__ dst,
+                                               const Geometry& geo, const Phys<float>& ph, const int x0,
+                                               const int y0, const int rows, int* __restrict__ flag,
+                                               float (*sphi)[2 * BX + 2], const Plane32 pl) {
+  using P = Pop<PREC>;
+  using R = typename P::R;
+  constexpr int RING = 3 * BY + 1;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nx = geo.nx, ny = geo.ny, pitch = geo.pitch;
+  const int y1 = min(y0 + rows, ny);
+  const int xv = min(2 * BX, nx - x0);  // valid columns of this strip (even)
+  const int x = x0 + 2 * tx;
+  const bool colv = 2 * tx < xv;
+  const int xm2 = (x == 0) ? nx - 2 : x - 2;
+  const int xp2 = (x + 2 >= nx) ? 0 : x + 2;
+  // Threads tx == 0 and tx == BX-1 also pull the single halo node left / right of the strip.
+  const bool halo = tx == 0 || tx == BX - 1;
+  const int hx = (tx == 0) ? ((x0 == 0) ? nx - 1 : x0 - 1) : ((x0 + xv == nx) ? 0 : x0 + xv);
+  const int hcol = (tx == 0) ? 0 : xv + 1;
+
+  auto wrap = [&](int r) -> int { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  auto slot = [&](int r) -> int { return (int)((unsigned)(r - (y0 - 1)) % (unsigned)RING); };
+  auto pull_g2 = [&](int r, RawPairLoad& o) {
+    const int y = wrap(r);
+    pull_pair<PREC, true>(src, pl, pitch, x, xm2, xp2, y, y == 0 ? ny - 1 : y - 1, y == ny - 1 ? 0 : y + 1, o);
+  };
+  auto pull_f2 = [&](int r, RawPairLoad& o) {
+    pull_pair<PREC, false>(src, pl, pitch, x, xm2, xp2, r, r == 0 ? ny - 1 : r - 1, r == ny - 1 ? 0 : r + 1, o);
+  };
+  auto pull_h = [&](int r, R out[9]) {
+    pull_raw<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, hx, wrap(r), out, pl);
+  };
+  auto phi_h = [&](const R raw[9]) -> float {
+    float v[9];
+    unpack<PREC, true>(raw, false, v);
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+  };
+  auto put_phi = [&](int r, const RawPair& g) {
+    float* row = sphi[slot(r)];
+    row[2 * tx + 1] = phi_pair<PREC>(g, 0);
+    row[2 * tx + 2] = phi_pair<PREC>(g, 1);
+  };
+
+  RawPair gA, gB, fA;
+  RawPairLoad gC, fB;  // in flight
+  R hB[9];
+  {
+    const int r = y0 + ty;
+    if (r <= y1) {
+      if (colv) {
+        pull_g2(r, gC);
+        finish(gC, gA);
+        put_phi(r, gA);
+      }
+      if (halo) {
+        pull_h(r, hB);
+        sphi[slot(r)][hcol] = phi_h(hB);
+      }
+    }
+    if (ty == 0) {
+      if (colv) {
+        RawPair gt;
+        pull_g2(y0 - 1, gC);
+        finish(gC, gt);
+        put_phi(y0 - 1, gt);
+      }
+      if (halo) {
+        R ht[9];
+        pull_h(y0 - 1, ht);
+        sphi[slot(y0 - 1)][hcol] = phi_h(ht);
+      }
+    }
+    const int rb = y0 + BY + ty;
+    if (rb <= y1) {
+      if (colv) {
+        pull_g2(rb, gC);
+        finish(gC, gB);
+      }
+      if (halo) pull_h(rb, hB);
+    }
+    if (colv && r < y1) {
+      pull_f2(r, fB);
+      finish(fB, fA);
+    }
+  }
+
+  for (int Y = y0; Y < y1; Y += BY) {
+    const int r = Y + ty;            // collided now
+    const int rb = Y + BY + ty;      // phi formed now
+    const int rc = Y + 2 * BY + ty;  // g issued now
+    const bool act = colv && r < y1;
+    if (rc <= y1 && colv) pull_g2(rc, gC);
+    if (rb < y1 && colv) pull_f2(rb, fB);
+    if (rb <= y1) {
+      if (colv) put_phi(rb, gB);
+      if (halo) sphi[slot(rb)][hcol] = phi_h(hB);
+    }
+    if (rc <= y1 && halo) pull_h(rc, hB);
+    __syncthreads();
+    if (act) {
+      const int sm = slot(r - 1), s0 = slot(r), sp = slot(r + 1);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float s[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          s[0][d] = sphi[sm][2 * tx + k + d];
+          s[1][d] = sphi[s0][2 * tx + k + d];
+          s[2][d] = sphi[sp][2 * tx + k + d];
+        }
+        float dxp, dyp, lap;
+        stencils<float>(s, dxp, dyp, lap);
+        const float phi = s[1][1];
+        float f[9], g[9];
+        unpack_pair<PREC, false>(fA, k, f);
+        unpack_pair<PREC, true>(gA, k, g);
+        const float rho = collide<float>(ph, f, g, phi, dxp, dyp, lap);
+        if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
+        P::store_node(dst, pl, r * pitch + x + k, f, g);
+      }
+    }
+    gA = gB;
+    finish(gC, gB);  // the loads issued at the top of this band have had the band to arrive
+    finish(fB, fA);
+  }
+}
+
+template <int PREC, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo, const Phys<float> ph,
+            const int rows, int* __restrict__ flag) {
+  __shared__ float sphi[3 * BY + 1][2 * BX + 2];
+  step_pair_tile<PREC, BX, BY>(src, dst, geo, ph, blockIdx.x * 2 * BX, blockIdx.y * rows, rows, flag, sphi,
+                               Plane32{(unsigned)geo.plane});
+}
+
+#define LBM_PAIR_TILES(X) X(64, 2) X(64, 4) X(128, 1) X(128, 2)
+
+template <int PREC, int BX, int BY>
+cudaError_t pair_bxby(const HostGeometry& g, const HostPhys& p, int rows, const char* src, char* dst, int* flag,
+                      cudaStream_t s) {
+  dim3 grd((g.nx + 2 * BX - 1) / (2 * BX), (g.ny + rows - 1) / rows);
+  Geometry geo;
+  geo.nx = g.nx;
+  geo.ny = g.ny;
+  geo.pitch = g.pitch;
+  geo.plane = g.plane;
+  geo.walls = g.walls;
+  k_step_pair<PREC, BX, BY><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, make_phys<float>(p), rows, flag);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t pair_prec(const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src, char* dst,
+                      int* flag, cudaStream_t s) {
+#define LBM_CASE(X, Y) \
+  if (t.bx == X && t.by == Y) return pair_bxby<PREC, X, Y>(g, p, t.rows, src, dst, flag, s);
+  LBM_PAIR_TILES(LBM_CASE)
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+int pair_occ(int bx, int by) {
+  int nb = 0;
+#define LBM_CASE(X, Y) \
+  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair<PREC, X, Y>, X * Y, 0);
+  LBM_PAIR_TILES(LBM_CASE)
+#undef LBM_CASE
+  return nb;
+}
+
+}  // namespace
+
+bool pair_supported(int prec, const HostGeometry& g, int bx, int by) {
+  if ((prec != 2 && prec != 3) || g.walls || g.nx % 2 || !offsets_fit_32(prec, g.plane)) return false;
+#define LBM_CASE(X, Y) \
+  if (bx == X && by == Y) return true;
+  LBM_PAIR_TILES(LBM_CASE)
+#undef LBM_CASE
+  return false;
+}
+
+int pair_blocks_per_sm(int prec, const StepTile& t) {
+  return prec == 2 ? pair_occ<2>(t.bx, t.by) : (prec == 3 ? pair_occ<3>(t.bx, t.by) : 0);
+}
+
+cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
+                             char* dst, int* flag, cudaStream_t s) {
+  if (prec == 2) return pair_prec<2>(g, p, t, src, dst, flag, s);
+  if (prec == 3) return pair_prec<3>(g, p, t, src, dst, flag, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbmch

@@ -287,3 +287,56 @@ def test_staged_kernel_rejects_unaligned_width(lbm):
     with pytest.raises(lbm.LbmError):
         lat.set_kernel(lbm.LBM_KERNEL_STAGED)
     assert lat.kernel[0] == lbm.LBM_KERNEL_GENERIC
+
+
+PAIR_TILES = [(64, 2), (64, 4), (128, 1), (128, 2)]
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_paired_16bit_kernel_follows_one_node_kernel(lbm, orc, prec):
+    """The paired 16-bit kernel (two nodes per thread) performs the one-node kernel's per-node
+    arithmetic (same decode, collision, encode and closure), so on a ragged periodic lattice
+    (nx = 326: even, not a multiple of any strip width; ny = 90; viscosity ratio 10) every paired
+    tile follows the one-node kernel within one 16-bit rounding of a population after 200 steps
+    (measured: bit-identical; a separately compiled kernel may contract a multiply-add
+    differently), and both stay within the 16-bit bound of the FP64 oracle."""
+    phi0 = W.spinodal(326, 90, seed=4)
+    kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53, visc=lbm.LBM_TAU_LINEAR)
+    ref = lbm.Lattice(phi0, **kw)
+    ref.set_kernel(lbm.LBM_KERNEL_GENERIC, 256, 1)
+    ref.step(200)
+    fr, gr = ref.populations()
+    o = orc.Oracle(phi0, **oracle_kwargs(kw))
+    o.step(200)
+    po = o.fields()[3]
+    for bx, by in PAIR_TILES:
+        for rows in (0, 7):
+            lat = lbm.Lattice(phi0, **kw)
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR, bx, by, 0, rows)
+            assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR
+            lat.step(200)
+            f, g = lat.populations()
+            assert abs_err(f, fr) <= 1e-3 and abs_err(g, gr) <= 1e-3, (bx, by, rows, abs_err(f, fr), abs_err(g, gr))
+            bound = 2e-3 if prec == "fp16s" else 2e-2
+            assert abs_err(lat.fields()[3], po) <= bound
+            lat.close()
+
+
+def test_paired_kernel_choice_and_limits(lbm):
+    """AUTO picks the paired kernel for 16-bit storage on periodic lattices with even nx, and the
+    one-node kernel otherwise; asking for it where it cannot serve is an error."""
+    even = W.spinodal(64, 40, seed=1)
+    odd = W.spinodal(65, 40, seed=1)
+    assert lbm.Lattice(even, prec=lbm.LBM_FP16S).kernel[0] == lbm.LBM_KERNEL_PAIR
+    assert lbm.Lattice(even, prec=lbm.LBM_BF16S).kernel[0] == lbm.LBM_KERNEL_PAIR
+    assert lbm.Lattice(odd, prec=lbm.LBM_FP16S).kernel[0] == lbm.LBM_KERNEL_GENERIC
+    assert lbm.Lattice(even, prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y).kernel[0] == lbm.LBM_KERNEL_GENERIC
+    assert lbm.Lattice(even, prec=lbm.LBM_FP32).kernel[0] == lbm.LBM_KERNEL_GENERIC
+    for phi, kw in ((odd, dict(prec=lbm.LBM_FP16S)), (even, dict(prec=lbm.LBM_FP32)),
+                    (even, dict(prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y))):
+        lat = lbm.Lattice(phi, **kw)
+        with pytest.raises(lbm.LbmError):
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)
+        with pytest.raises(lbm.LbmError):
+            lbm.Lattice(even, prec=lbm.LBM_FP16S).set_kernel(lbm.LBM_KERNEL_PAIR, 96, 1)
+        lat.close()

@@ -67,8 +67,8 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Sources that define the fused step kernel k_step (the kernel the roofline reports).
-STEP_SOURCES = ("lbm_step.cuh", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
+# Sources that define the fused step kernels k_step / k_step_pair (the kernel the roofline reports).
+STEP_SOURCES = ("lbm_step.cuh", "lbm_pair.cu", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
 
 
 def kernel_source_hash():

@@ -60,12 +60,8 @@ __device__ __forceinline__ int shift_pixel_up(int p, int H, int W, int dy, int d
 //   Y[p][n] = sum_tap sum_k X[p + sgn*off(tap)][k] * Wt(tap, k, n)  (+ bias[n], ReLU)
 // forward:       X = input (K = Cin),  Wt(tap,k,n) = Wgt[tap][k][n] (n = Cout), sgn = +1
 // backward data: X = dY (K = Cout),    Wt(tap,k,n) = Wgt[tap][n][k] (n = Cin),  sgn = -1
-// Requires K % 16 == 0 and N % TN == 0 (channel counts are padded by the host).
-//
-// Tile: 128 pixels x TN channels per CTA of 8 warps
-// (4 along pixels x 2 along channels, 32 x TN/2 each), KC channels of one tap per stage, stages
-// double-buffered in shared memory by cp.async (zero-filled outside the image), fragments read
-// with ldmatrix from rows padded by 16 bytes (conflict-free).
+// Requires K % 16 == 0 and N % 16 == 0.  The kernel (k_conv3x3_halo, below) stages a spatial
+// block with its halo once per 16 input channels and runs all nine taps from shared memory.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
@@ -81,93 +77,113 @@ __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
 }
-__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2_t(uint32_t r[2], const void* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
 }
 
-// UPX: X is the coarse (H/2 x W/2) image and the convolution reads its 2x nearest upsampling
-// (fine pixel (y, x) -> coarse (y/2, x/2)) without materialising it.  addend (may be NULL, BF16
-// npix x N) is added to the result before the ReLU.
-template <int TN, int KC, bool TRANSW, bool OUT_F32, bool UPX = false>
-__global__ void __launch_bounds__(256)
-k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* __restrict__ bias,
-               void* __restrict__ Y, int npix, int H, int W, int K, int N, int sgn, int relu,
-               const bf16* __restrict__ addend = nullptr) {
-  constexpr int TPX = 128, AST = KC + 8;
-  constexpr int WN = TN >= 16 ? TN / 2 : 8;  // channels per warp
-  constexpr int NT = WN / 8;                 // n8 tiles per warp
-  constexpr int BR = TRANSW ? TN : KC;       // B stored [k][n] (forward) or [n][k] (transposed)
+// Halo-tile form of the same convolution.  A CTA owns a TH x TW block of output pixels of one
+// image (TH * TW <= 256) and TN <= 64 output channels.  Each stage brings 16 input channels of
+// the block plus its one-pixel periodic halo, (TH + 2) x (TW + 2) pixels, and the weights of all
+// nine taps for them into shared memory; the nine taps then read shifted windows of the same
+// halo tile (each lane of ldmatrix gives its own row address, so a shift is an address offset).
+// Compared with staging one tap at a time, every input value crosses from L2 once per stage
+// instead of nine times and a stage carries nine times the tensor work to hide the next stage's
+// loads behind.  8 warps, each 32 pixels x TN channels; stages double-buffered by cp.async.
+struct HaloGeom {
+  int TW, TH;      // output block: TW columns x TH rows
+  int tiles_x;     // blocks per image row band
+  int tiles_img;   // blocks per image
+  int HP;          // halo pixels (TH + 2) * (TW + 2)
+};
+
+template <int TN, bool TRANSW, bool OUT_F32, bool UPX>
+__global__ void __launch_bounds__(256, 2)
+k_conv3x3_halo(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const float* __restrict__ bias,
+               void* __restrict__ Y, const HaloGeom hg, int H, int W, int K, int N, int sgn, int relu,
+               const bf16* __restrict__ addend) {
+  constexpr int KC = 16, AST = KC + 8;           // channels per stage; padded halo rows (48 B)
+  constexpr int NT = TN / 8;                     // n8 tiles per warp
+  constexpr int BR = TRANSW ? TN : KC;           // per tap: B[k][n] (forward) or B[n][k] (transposed)
   constexpr int BC = (TRANSW ? KC : TN) + 8;
-  __shared__ __align__(16) bf16 sA[2][TPX][AST];
-  __shared__ __align__(16) bf16 sB[2][BR][BC];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp & 3, wn = warp >> 2;
-  const int g = lane >> 2, t = lane & 3;
-  const int p0 = blockIdx.x * TPX;
-  const int n0 = blockIdx.y * TN;
-  const int kchunks = K / KC;
-  const int nstage = 9 * kchunks;
+  constexpr int ACH = 4;                         // halo chunks (16 B) per thread per stage: 2 HP <= 1024
+  extern __shared__ __align__(16) unsigned char conv_smem[];
+  const int HP = hg.HP, TW = hg.TW, TH = hg.TH, HW = TW + 2;
+  bf16* sAbase = reinterpret_cast<bf16*>(conv_smem);                      // [2][HP][AST]
+  bf16* sBbase = sAbase + 2 * (size_t)HP * AST;                           // [2][9][BR][BC]
+  auto sA = [&](int buf, int h) -> bf16* { return sAbase + ((size_t)buf * HP + h) * AST; };
+  auto sB = [&](int buf, int tap, int r) -> bf16* { return sBbase + (((size_t)buf * 9 + tap) * BR + r) * BC; };
 
-  // The pixels whose A chunks this thread copies are fixed: decompose them once.
-  constexpr int ACH = TPX * KC / 8 / 256;  // A chunks per thread per stage
-  int ay[ACH], ax[ACH], ab[ACH];
-  bool aok[ACH];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int img = blockIdx.x / hg.tiles_img, tin = blockIdx.x % hg.tiles_img;
+  const int ty0 = (tin / hg.tiles_x) * TH, tx0 = (tin % hg.tiles_x) * TW;
+  const int n0 = blockIdx.y * TN;
+  const int nst = K / KC;
+
+  // Global source pixel of each halo chunk this thread copies (the same every stage).
+  int aps[ACH];
 #pragma unroll
   for (int j = 0; j < ACH; ++j) {
     const int c = tid + j * 256;
-    const int p = p0 + c / (KC / 8);
-    aok[j] = p < npix;
-    const int pp = aok[j] ? p : 0;
-    ax[j] = pp % W;
-    const int by = pp / W;
-    ab[j] = by / H;
-    ay[j] = by - ab[j] * H;
+    const int h = c >> 1;
+    aps[j] = -1;
+    if (h < HP) {
+      const int hy = h / HW, hx = h - hy * HW;
+      int yy = ty0 - 1 + hy, xx = tx0 - 1 + hx;
+      yy = ((yy % H) + H) % H;
+      xx = ((xx % W) + W) % W;
+      aps[j] = UPX ? (img * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1) : (img * H + yy) * W + xx;
+    }
   }
   auto load_stage = [&](int st, int buf) {
-    const int tap = st / kchunks, k0 = (st % kchunks) * KC;
-    const int dy = sgn * (tap / 3 - 1), dx = sgn * (tap % 3 - 1);
+    const int k0 = st * KC;
 #pragma unroll
     for (int j = 0; j < ACH; ++j) {
       const int c = tid + j * 256;
-      const int r = c / (KC / 8), part = c % (KC / 8);
-      int yy = ay[j] + dy, xx = ax[j] + dx;
-      yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
-      xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
-      const int ps = UPX ? (ab[j] * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1) : (ab[j] * H + yy) * W + xx;
-      cp_async16(&sA[buf][r][part * 8], X + (size_t)ps * K + k0 + part * 8, aok[j]);
+      if (aps[j] >= 0) cp_async16(sA(buf, c >> 1) + (c & 1) * 8, X + (size_t)aps[j] * K + k0 + (c & 1) * 8, true);
     }
     if (!TRANSW) {
-      for (int c = tid; c < KC * TN / 8; c += 256) {
-        const int kk = c / (TN / 8), c8 = (c % (TN / 8)) * 8;
-        cp_async16(&sB[buf][kk][c8], Wg + ((size_t)tap * K + k0 + kk) * N + n0 + c8, true);
+      for (int c = tid; c < 9 * KC * TN / 8; c += 256) {
+        const int tap = c / (KC * TN / 8), r = c % (KC * TN / 8);
+        const int kk = r / (TN / 8), c8 = (r % (TN / 8)) * 8;
+        cp_async16(sB(buf, tap, kk) + c8, Wg + ((size_t)tap * K + k0 + kk) * N + n0 + c8, true);
       }
     } else {
-      for (int c = tid; c < TN * KC / 8; c += 256) {
-        const int nn = c / (KC / 8), part = c % (KC / 8);
-        cp_async16(&sB[buf][nn][part * 8], Wg + ((size_t)tap * N + n0 + nn) * K + k0 + part * 8, true);
+      for (int c = tid; c < 9 * TN * KC / 8; c += 256) {
+        const int tap = c / (TN * KC / 8), r = c % (TN * KC / 8);
+        const int nn = r / (KC / 8), part = (r % (KC / 8)) * 8;
+        cp_async16(sB(buf, tap, nn) + part, Wg + ((size_t)tap * N + n0 + nn) * K + k0 + part, true);
       }
     }
   };
 
+  // The halo row of this lane's ldmatrix row for each m16 tile (tap (0, 0)); rows of pixels past
+  // the block point at a valid row and are never stored.
+  int hrow[2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int q = warp * 32 + mt * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+    const int i = q / TW, jx = q - i * TW;
+    hrow[mt] = (q < TH * TW) ? (i + 1) * HW + jx + 1 : HW + 1;
+  }
+
   float acc[2][NT][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int j = 0; j < NT; ++j)
+    for (int b = 0; b < NT; ++b)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
 
-  const bool warp_active = wn * WN < TN;  // TN = 16 uses only the first channel half
   load_stage(0, 0);
   cp_async_commit();
-  for (int st = 0; st < nstage; ++st) {
+  for (int st = 0; st < nst; ++st) {
     const int buf = st & 1;
-    if (st + 1 < nstage) {
+    if (st + 1 < nst) {
       load_stage(st + 1, buf ^ 1);
       cp_async_commit();
       cp_async_wait<1>();
@@ -175,61 +191,63 @@ k_conv3x3_pipe(const bf16* __restrict__ X, const bf16* __restrict__ Wg, const fl
       cp_async_wait<0>();
     }
     __syncthreads();
-    if (warp_active) {
 #pragma unroll
-      for (int kk = 0; kk < KC / 16; ++kk) {
-        uint32_t a[2][4];
+    for (int tap = 0; tap < 9; ++tap) {
+      const int shift = sgn * ((tap / 3 - 1) * HW + (tap % 3 - 1));
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) ldsm_x4(a[mt], sA(buf, hrow[mt] + shift) + 8 * (lane >> 4));
+#pragma unroll
+      for (int np = 0; np < NT / 2; ++np) {
+        uint32_t b[4];
+        if (!TRANSW) ldsm_x4_t(b, sB(buf, tap, (lane & 7) + 8 * ((lane >> 3) & 1)) + np * 16 + 8 * (lane >> 4));
+        else ldsm_x4(b, sB(buf, tap, np * 16 + (lane & 7) + 8 * (lane >> 4)) + 8 * ((lane >> 3) & 1));
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-          const int row = wm * 32 + mt * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
-          ldsm_x4(a[mt], &sA[buf][row][kk * 16 + 8 * (lane >> 4)]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          uint32_t b[2];
-          const int l = lane & 15;
-          if (!TRANSW) ldsm_x2_t(b, &sB[buf][kk * 16 + (l >> 3) * 8 + (l & 7)][wn * WN + nt * 8]);
-          else ldsm_x2(b, &sB[buf][wn * WN + nt * 8 + (l & 7)][kk * 16 + (l >> 3) * 8]);
-#pragma unroll
-          for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b);
+          mma16816(acc[mt][2 * np], a[mt], b);
+          mma16816(acc[mt][2 * np + 1], a[mt], b + 2);
         }
       }
     }
     __syncthreads();  // the buffer is refilled by the next stage's loads
   }
-  if (!warp_active) return;
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+    for (int hh = 0; hh < 2; ++hh) {
+      const int q = warp * 32 + mt * 16 + g + hh * 8;
+      if (q >= TH * TW) continue;
+      const int i = q / TW, jx = q - i * TW;
+      const int yy = ty0 + i, xx = tx0 + jx;
+      if (yy >= H || xx >= W) continue;
+      const size_t p = ((size_t)img * H + yy) * W + xx;
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int p = p0 + wm * 32 + mt * 16 + g + hh * 8;
-        if (p >= npix) continue;
-        const int n = n0 + wn * WN + nt * 8 + 2 * t;
+      for (int nt = 0; nt < NT; ++nt) {
+        const int n = n0 + nt * 8 + 2 * t;
         float v0 = acc[mt][nt][hh * 2], v1 = acc[mt][nt][hh * 2 + 1];
         if (bias) {
           v0 += bias[n];
           v1 += bias[n + 1];
         }
         if (addend) {
-          const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(addend + (size_t)p * N + n));
-          v0 += a.x;
-          v1 += a.y;
+          const float2 av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(addend + p * N + n));
+          v0 += av.x;
+          v1 += av.y;
         }
         if (relu) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
         }
         if (OUT_F32) {
-          float* y = static_cast<float*>(Y) + (size_t)p * N + n;
+          float* y = static_cast<float*>(Y) + p * N + n;
           y[0] = v0;
           y[1] = v1;
         } else {
-          bf16* y = static_cast<bf16*>(Y) + (size_t)p * N + n;
+          bf16* y = static_cast<bf16*>(Y) + p * N + n;
           *reinterpret_cast<__nv_bfloat162*>(y) = __floats2bfloat162_rn(v0, v1);
         }
       }
+    }
 }
 
 // Weight gradient: dW[tap][ci][co] += sum_p X[p + off(tap)][ci] * dY[p][co]; a GEMM with
@@ -495,17 +513,54 @@ int check(cudaError_t e) { return e == cudaSuccess ? SUR_OK : SUR_ERR_CUDA; }
 
 int tile_n(int N) { return N % 64 == 0 ? 64 : (N % 32 == 0 ? 32 : (N % 16 == 0 ? 16 : 0)); }
 
-// Output-channel tile of the implicit GEMM: the widest that divides N, halved (down to 64) only
-// while the grid would fill less than half of the SMs.  Narrow tiles re-read the pixel operand
-// once per tile, which costs more than a partly idle wave unless the grid is very small.
-int conv_tile_n(long long npix, int N) {
-  const long long ptiles = (npix + 127) / 128;
+// Output block of the halo-tile convolution: up to 64 columns wide and 256 pixels, with its halo
+// tile at most 512 pixels (the kernel's per-thread chunk count) and no taller than the image.
+HaloGeom halo_geom(int H, int W) {
+  HaloGeom g;
+  g.TW = W < 64 ? W : 64;
+  int th = 256 / g.TW;
+  const int cap = 512 / (g.TW + 2) - 2;
+  if (th > cap) th = cap;
+  if (th > H) th = H;
+  g.TH = th < 1 ? 1 : th;
+  g.tiles_x = (W + g.TW - 1) / g.TW;
+  g.tiles_img = g.tiles_x * ((H + g.TH - 1) / g.TH);
+  g.HP = (g.TH + 2) * (g.TW + 2);
+  return g;
+}
+
+template <int TN, bool TRANSW>
+constexpr size_t halo_smem_max() {
+  return (2 * 512 * 24 + 2 * 9 * (size_t)(TRANSW ? TN : 16) * ((TRANSW ? 16 : TN) + 8)) * sizeof(bf16);
+}
+
+template <int TN, bool TRANSW, bool OUT_F32, bool UPX>
+int halo_launch(int batch, const HaloGeom& hg, cudaStream_t s, const bf16* X, const bf16* Wg, const float* bias,
+                void* y, int H, int W, int K, int N, int sgn, int relu, const bf16* addend) {
+  auto kern = k_conv3x3_halo<TN, TRANSW, OUT_F32, UPX>;
+  static bool configured = false;  // per instantiation, once per process
+  if (!configured) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)halo_smem_max<TN, TRANSW>()) !=
+        cudaSuccess)
+      return SUR_ERR_CUDA;
+    configured = true;
+  }
+  const size_t smem =
+      (2 * (size_t)hg.HP * 24 + 2 * 9 * (size_t)(TRANSW ? TN : 16) * ((TRANSW ? 16 : TN) + 8)) * sizeof(bf16);
+  dim3 grd((unsigned)(batch * hg.tiles_img), (unsigned)(N / TN));
+  kern<<<grd, 256, smem, s>>>(X, Wg, bias, y, hg, H, W, K, N, sgn, relu, addend);
+  return check(cudaGetLastError());
+}
+
+// Channel tile of the halo-tile convolution: 64, 32 or 16 dividing N, halved while the grid
+// would not give every SM a CTA.
+int halo_tile_n(long long blocks, int N) {
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                 cudaSuccess || sms < 1)
     sms = 1;
-  int tn = N % 128 == 0 ? 128 : tile_n(N);
-  while (tn > 64 && 2 * ptiles * (N / tn) < sms) tn /= 2;
+  int tn = N % 64 == 0 ? 64 : (N % 32 == 0 ? 32 : 16);
+  while (tn > 16 && blocks * (N / tn) < sms) tn /= 2;
   return tn;
 }
 
@@ -527,27 +582,23 @@ int sur_conv3x3(const void* x, const void* w, const float* bias, void* y, int ba
   if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) % 16) return SUR_ERR_PARAM;
   const long long npix = (long long)batch * H * W;
   if (npix > (1ll << 30)) return SUR_ERR_PARAM;
-  const int tn = conv_tile_n(npix, N);
-  dim3 grd((unsigned)((npix + 127) / 128), (unsigned)(N / tn));
+  const HaloGeom hg = halo_geom(H, W);
+  const int tn = halo_tile_n((long long)batch * hg.tiles_img, N);
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* X = (const bf16*)x;
   const bf16* Wg = (const bf16*)w;
-  const bool k32 = K % 32 == 0;
-#define SUR_PIPE(TN_, KC_)                                                                                    \
-  if (tn == TN_ && (KC_ == 32) == k32) {                                                                      \
-    if (!transposed_weights && !out_f32)                                                                      \
-      k_conv3x3_pipe<TN_, KC_, false, false><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu); \
-    else if (!transposed_weights)                                                                             \
-      k_conv3x3_pipe<TN_, KC_, false, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);  \
-    else if (!out_f32)                                                                                        \
-      k_conv3x3_pipe<TN_, KC_, true, false><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);  \
-    else                                                                                                      \
-      k_conv3x3_pipe<TN_, KC_, true, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, sgn, relu);   \
-    return check(cudaGetLastError());                                                                         \
+#define SUR_HALO(TN_)                                                                                          \
+  if (tn == TN_) {                                                                                             \
+    if (!transposed_weights && !out_f32)                                                                       \
+      return halo_launch<TN_, false, false, false>(batch, hg, s, X, Wg, bias, y, H, W, K, N, sgn, relu, nullptr); \
+    if (!transposed_weights)                                                                                   \
+      return halo_launch<TN_, false, true, false>(batch, hg, s, X, Wg, bias, y, H, W, K, N, sgn, relu, nullptr);  \
+    if (!out_f32)                                                                                              \
+      return halo_launch<TN_, true, false, false>(batch, hg, s, X, Wg, bias, y, H, W, K, N, sgn, relu, nullptr);  \
+    return halo_launch<TN_, true, true, false>(batch, hg, s, X, Wg, bias, y, H, W, K, N, sgn, relu, nullptr);     \
   }
-  SUR_PIPE(128, 32) SUR_PIPE(128, 16) SUR_PIPE(64, 32) SUR_PIPE(64, 16) SUR_PIPE(32, 32) SUR_PIPE(32, 16)
-  SUR_PIPE(16, 32) SUR_PIPE(16, 16)
-#undef SUR_PIPE
+  SUR_HALO(64) SUR_HALO(32) SUR_HALO(16)
+#undef SUR_HALO
   return SUR_ERR_PARAM;
 }
 
@@ -589,21 +640,15 @@ int sur_conv3x3_up_add(const void* xc, const void* w, const float* bias, const v
   if (((uintptr_t)xc | (uintptr_t)w | (uintptr_t)y | (uintptr_t)addend) % 16) return SUR_ERR_PARAM;
   const long long npix = (long long)batch * H * W;
   if (npix > (1ll << 30)) return SUR_ERR_PARAM;
-  const int tn = conv_tile_n(npix, N);
-  dim3 grd((unsigned)((npix + 127) / 128), (unsigned)(N / tn));
+  const HaloGeom hg = halo_geom(H, W);
+  const int tn = halo_tile_n((long long)batch * hg.tiles_img, N);
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* X = (const bf16*)xc;
   const bf16* Wg = (const bf16*)w;
   const bf16* A = (const bf16*)addend;
-  const bool k32 = K % 32 == 0;
-#define SUR_UP(TN_, KC_)                                                                             \
-  if (tn == TN_ && (KC_ == 32) == k32) {                                                             \
-    k_conv3x3_pipe<TN_, KC_, false, false, true><<<grd, 256, 0, s>>>(X, Wg, bias, y, (int)npix, H, W, K, N, 1, 0, A); \
-    return check(cudaGetLastError());                                                                \
-  }
-  SUR_UP(128, 32) SUR_UP(128, 16) SUR_UP(64, 32) SUR_UP(64, 16) SUR_UP(32, 32) SUR_UP(32, 16) SUR_UP(16, 32)
-  SUR_UP(16, 16)
-#undef SUR_UP
+  if (tn == 64) return halo_launch<64, false, false, true>(batch, hg, s, X, Wg, bias, y, H, W, K, N, 1, 0, A);
+  if (tn == 32) return halo_launch<32, false, false, true>(batch, hg, s, X, Wg, bias, y, H, W, K, N, 1, 0, A);
+  if (tn == 16) return halo_launch<16, false, false, true>(batch, hg, s, X, Wg, bias, y, H, W, K, N, 1, 0, A);
   return SUR_ERR_PARAM;
 }
 

@@ -468,7 +468,7 @@ int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
     t.rows = rows_for_wave(h->geo, t, sms * staged_blocks_per_sm(h->p.prec, t));
     cands.push_back(t);
   }
-  const int ptiles[][2] = {{64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  const int ptiles[][2] = {{64, 2}, {128, 1}};
   for (auto& pt : ptiles) {
     if (!pair_supported(h->p.prec, h->geo, pt[0], pt[1])) continue;
     StepTile t{pt[0], pt[1], 0, 0, 1};

@@ -80,8 +80,10 @@ template <class T> struct PopDense {
   template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
     st(b, pl, 9 + i, idx, v);
   }
+  // rho, phi: the node's density and order parameter (used by the 16-bit closures only).
   template <class PL>
-  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9]) {
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], C /*rho*/,
+                                                    C /*phi*/) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       stf(b, pl, i, idx, f[i]);
@@ -156,12 +158,12 @@ template <class H> struct PopHalf {
   }
   // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
   // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
-  // to the post-collision rho and phi: 16-bit rounding then redistributes among directions but
-  // does not create or destroy mass or order parameter.
+  // to the node's rho and phi (the collision conserves both; the caller passes them): 16-bit
+  // rounding then redistributes among directions but does not create or destroy mass or order
+  // parameter.  With deviations d_i = f_i - w_i, f_0 = (rho - 5/9) - sum d_i (sum_{i>0} w_i = 5/9).
   template <class PL>
-  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9]) {
-    const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const float phi = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], float rho,
+                                                    float phi) {
     float sf = 0.0f, sg = 0.0f;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -169,12 +171,14 @@ template <class H> struct PopHalf {
       const H hg = Cvt<H>::from(g[i]);
       *half(b, pl, i - 1, idx) = hf;
       *half(b, pl, 7 + i, idx) = hg;
-      sf += Cvt<H>::to(hf) + wrest(i);
+      sf += Cvt<H>::to(hf);
       sg += Cvt<H>::to(hg);
     }
-    *rest(b, pl, 0, idx) = rho - sf;
+    *rest(b, pl, 0, idx) = rest_f(rho, sf);
     *rest(b, pl, 1, idx) = phi - sg;
   }
+  // The f rest closure from rho and the sum of the rounded moving deviations.
+  __device__ __forceinline__ static float rest_f(float rho, float sum_dev) { return (rho - 5.0f / 9.0f) - sum_dev; }
   // Raw access: 32-bit words holding either the FP32 rest value (i = 0) or the 16-bit pattern of
   // a moving population, decoded only where used so that loads stay in flight.
   using R = uint32_t;

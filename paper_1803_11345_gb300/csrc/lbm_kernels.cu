@@ -87,8 +87,8 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
   }
   f[0] = rho - sf;
   g[0] = phi - sg;
-  collide<C>(ph, f, g, phi, gx, gy, lap);
-  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g);
+  const C rho_c = collide<C>(ph, f, g, phi, gx, gy, lap);
+  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g, rho_c, phi);
 }
 
 // -------------------------------------------------------------------------------------------

@@ -9,6 +9,8 @@
 //     low half of the word at x (one byte permute), from the right (c_x = -1) the high half of
 //     the word at x and the low half of the word at x+2;
 //   * the rest populations f_0, g_0 (FP32) are one 64-bit load;
+//   * the results of the two nodes are stored as 32-bit words (64-bit for the rest
+//     populations), rounded two at a time;
 // and every address is formed once for two nodes.  The per-node arithmetic is that of the
 // one-node kernel (same decode, collision, encode and closure functions).  Requirements: periodic
 // boundaries, nx even (pairs never straddle the periodic seam), population copy under 4 GiB.
@@ -54,6 +56,30 @@ __device__ __forceinline__ void finish(const RawPairLoad& l, RawPair& o) {
 __device__ __forceinline__ uint32_t ld_word(const char* __restrict__ b, unsigned byte_off) {
   return __ldg(reinterpret_cast<const unsigned int*>(b + byte_off));
 }
+__device__ __forceinline__ void st_word(char* __restrict__ b, unsigned byte_off, uint32_t v) {
+  *reinterpret_cast<unsigned int*>(b + byte_off) = v;
+}
+
+// Two floats rounded to the storage type and packed (low half = first), and back.
+template <int PREC> struct Pack;
+template <> struct Pack<2> {
+  __device__ __forceinline__ static uint32_t pack(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static float2 unpack(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  }
+};
+template <> struct Pack<3> {
+  __device__ __forceinline__ static uint32_t pack(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static float2 unpack(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+  }
+};
 
 // Eqs. 4-5 in pull form for the pair (x, x+1) at row y of a periodic lattice: direction i comes
 // from row y - c_yi and columns x - c_xi, x + 1 - c_xi.  xm2 / xp2 are the even columns x - 2 and
@@ -200,6 +226,10 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
     __syncthreads();
     if (act) {
       const int sm = slot(r - 1), s0 = slot(r), sp = slot(r + 1);
+      // Node x is collided and encoded first (its moving populations packed two directions per
+      // word, held across the second collision), then node x+1; the stored words pair the nodes.
+      uint32_t qf[4], qg[4];  // node x: (d_1, d_2), (d_3, d_4), ... and (g_1, g_2), ...
+      float f0a = 0.f, g0a = 0.f;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         float s[3][3];
@@ -217,7 +247,42 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
         unpack_pair<PREC, true>(gA, k, g);
         const float rho = collide<float>(ph, f, g, phi, dxp, dyp, lap);
         if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-        P::store_node(dst, pl, r * pitch + x + k, f, g);
+        // Round the moving populations in pairs of directions (same rounding as one at a time)
+        // and form the rest closures from the rounded values.
+        uint32_t pf[4], pg[4];
+        float sf = 0.f, sg = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          pf[j] = Pack<PREC>::pack(f[2 * j + 1] - P::wrest(2 * j + 1), f[2 * j + 2] - P::wrest(2 * j + 2));
+          pg[j] = Pack<PREC>::pack(g[2 * j + 1], g[2 * j + 2]);
+          const float2 rf = Pack<PREC>::unpack(pf[j]), rg = Pack<PREC>::unpack(pg[j]);
+          sf += rf.x;
+          sf += rf.y;
+          sg += rg.x;
+          sg += rg.y;
+        }
+        const float f0 = P::rest_f(rho, sf), g0 = phi - sg;
+        if (k == 0) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            qf[j] = pf[j];
+            qg[j] = pg[j];
+          }
+          f0a = f0;
+          g0a = g0;
+        } else {
+          const unsigned e = (unsigned)(r * pitch + x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // direction 2j+1 pairs the low halves, direction 2j+2 the high halves
+            st_word(dst, ((unsigned)(2 * j) * pl.n + e) * 2u, __byte_perm(qf[j], pf[j], 0x5410));
+            st_word(dst, ((unsigned)(2 * j + 1) * pl.n + e) * 2u, __byte_perm(qf[j], pf[j], 0x7632));
+            st_word(dst, ((unsigned)(8 + 2 * j) * pl.n + e) * 2u, __byte_perm(qg[j], pg[j], 0x5410));
+            st_word(dst, ((unsigned)(9 + 2 * j) * pl.n + e) * 2u, __byte_perm(qg[j], pg[j], 0x7632));
+          }
+          *reinterpret_cast<float2*>(dst + ((unsigned)P::kRestFirst * pl.n + e) * 4u) = make_float2(f0a, f0);
+          *reinterpret_cast<float2*>(dst + ((unsigned)(P::kRestFirst + 1) * pl.n + e) * 4u) = make_float2(g0a, g0);
+        }
       }
     }
     gA = gB;
@@ -226,8 +291,9 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   }
 }
 
+// Residency target: 3 CTAs of 128 threads per SM (12 warps).
 template <int PREC, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 3)
 k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo, const Phys<float> ph,
             const int rows, int* __restrict__ flag) {
   __shared__ float sphi[3 * BY + 1][2 * BX + 2];
@@ -235,7 +301,9 @@ k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry
                                Plane32{(unsigned)geo.plane});
 }
 
-#define LBM_PAIR_TILES(X) X(64, 2) X(64, 4) X(128, 1) X(128, 2)
+// Compiled tiles: 128-thread CTAs (3 per SM); 256-thread shapes spill at the register cap of
+// 2 CTAs per SM and were 1.5x slower.
+#define LBM_PAIR_TILES(X) X(64, 2) X(128, 1)
 
 template <int PREC, int BX, int BY>
 cudaError_t pair_bxby(const HostGeometry& g, const HostPhys& p, int rows, const char* src, char* dst, int* flag,

@@ -57,14 +57,13 @@ template <int PREC> struct Stage {
   }
   // Store the post-collision populations of one node (element e of every output plane of n
   // elements) into the staging buffer, with the same encoding as Pop<PREC>::store_node.
-  __device__ __forceinline__ static void store_node(char* ob, int n, int e, const C f[9], const C g[9]) {
+  __device__ __forceinline__ static void store_node(char* ob, int n, int e, const C f[9], const C g[9], C rho,
+                                                    C phi) {
     if constexpr (!kHalf) {
 #pragma unroll
       for (int q = 0; q < 18; ++q) reinterpret_cast<C*>(ob + ooff(q, n))[e] = q < 9 ? f[q] : g[q - 9];
     } else {
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
-      const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-      const float phi = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
       float sf = 0.0f, sg = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
@@ -73,10 +72,10 @@ template <int PREC> struct Stage {
         const Hf hg = Cvt<Hf>::from(g[i]);
         reinterpret_cast<Hf*>(ob + ooff(i, n))[e] = hf;
         reinterpret_cast<Hf*>(ob + ooff(9 + i, n))[e] = hg;
-        sf += Cvt<Hf>::to(hf) + w;
+        sf += Cvt<Hf>::to(hf);
         sg += Cvt<Hf>::to(hg);
       }
-      reinterpret_cast<float*>(ob + ooff(0, n))[e] = rho - sf;
+      reinterpret_cast<float*>(ob + ooff(0, n))[e] = PopHalf<Hf>::rest_f(rho, sf);
       reinterpret_cast<float*>(ob + ooff(9, n))[e] = phi - sg;
     }
   }
@@ -430,7 +429,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       const C phi = s[1][1];
       const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
       if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-      S::store_node(obuf, NOUT, ty * BX + tx, f, gcur);
+      S::store_node(obuf, NOUT, ty * BX + tx, f, gcur, rho, phi);
       fence_proxy_async_smem();
     }
     __syncthreads();

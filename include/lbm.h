@@ -174,13 +174,15 @@ LBM_API int lbm_set_populations(lbm_lattice* h, const double* f, const double* g
  * phi (LBM_ERR_NONFINITE) or a CUDA error occurred (LBM_ERR_CUDA); clears the flag. */
 LBM_API int lbm_check(lbm_lattice* h);
 
-/* Fused-step kernel choice.  AUTO: the fastest measured on GB300 — PAIR for 16-bit storage where
- * the lattice allows it, else GENERIC, each with its default tile.  GENERIC: populations pulled straight from global memory; plane offsets are formed
+/* Fused-step kernel choice.  AUTO: the fastest measured on GB300 — PAIR for 16-bit storage on
+ * lattices of 4 M nodes or more where it can serve them, else GENERIC, each with its default tile
+ * (lbm_autotune times all of them).  GENERIC: populations pulled straight from global memory; plane offsets are formed
  * in 32-bit arithmetic while a population copy is under 4 GiB, in 64-bit beyond.  GENERIC_WIDE:
  * the same kernel with 64-bit offsets for any lattice (what GENERIC runs for copies of 4 GiB or
  * more; selectable so that this path can be checked on small lattices).  PAIR: 16-bit storage
  * only, two neighbouring nodes per thread so that 16-bit populations move as 32-bit words (bx x by
- * threads cover 2 bx columns); needs periodic boundaries, even nx and a copy under 4 GiB.  STAGED: whole rows
+ * threads cover 2 bx columns; with walls a second launch steps the two wall rows); needs even nx and
+ * a copy under 4 GiB.  STAGED: whole rows
  * staged in shared memory by bulk copies; needs nx to be a multiple of 16 bytes / stored element
  * size (2 columns FP64, 4 FP32, 8 16-bit). */
 typedef enum {

@@ -67,7 +67,7 @@ void set_thread_error(const char* msg);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 
 // The paired 16-bit step (lbm_pair.cu): whether tile bx x by can serve the lattice (16-bit
-// storage, periodic, nx even, buffer under 4 GiB), resident CTAs per SM, and the launch.
+// storage, nx even, buffer under 4 GiB), resident CTAs per SM, and the launch.
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by);
 int pair_blocks_per_sm(int prec, const StepTile& t);
 cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,

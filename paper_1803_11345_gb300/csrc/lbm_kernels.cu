@@ -272,16 +272,18 @@ bool tile_supported(int prec, int bx, int by) {
 }
 
 StepTile default_tile(int prec, const HostGeometry& g, int device) {
-  // Measured on GB300 at 4096^2: FP32 / FP64, the software-pipelined generic kernel with one row
-  // of 256 threads per CTA; 16-bit storage, the paired kernel with 128 x 1 threads (256 columns)
-  // where the lattice allows it (1.2x the generic kernel); grids sized to one wave.
+  // Measured on GB300: FP32 / FP64, the software-pipelined generic kernel with one row of 256
+  // threads per CTA; 16-bit storage on lattices of 4 M nodes or more, the paired kernel with
+  // 128 x 1 threads (256 columns) where the lattice allows it (1.3x the generic kernel at 4096^2;
+  // on small lattices each CTA gets few rows and the pipeline start-up dominates: at 1024 x 512
+  // the generic kernel is faster).  Grids sized to one wave.
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (sms <= 0) sms = 152;
   StepTile t;
   t.staged = 0;
   t.depth = 1;
-  if (pair_supported(prec, g, 128, 1)) {
+  if (pair_supported(prec, g, 128, 1) && (long long)g.nx * g.ny >= (1ll << 22)) {
     t.bx = 128;
     t.by = 1;
     t.pair = 1;

@@ -12,10 +12,13 @@
 //   * the results of the two nodes are stored as 32-bit words (64-bit for the rest
 //     populations), rounded two at a time;
 // and every address is formed once for two nodes.  The per-node arithmetic is that of the
-// one-node kernel (same decode, collision, encode and closure functions).  Requirements: periodic
-// boundaries, nx even (pairs never straddle the periodic seam), population copy under 4 GiB.
+// one-node kernel (same decode, collision, encode and closure functions).  With walls the kernel
+// collides the interior rows only (it forms phi on the wall rows with the bounce-back pull) and
+// k_step_edge, the one-node tile code, steps the two wall rows in a second launch.
+// Requirements: nx even (pairs never straddle the periodic seam), population copy under 4 GiB.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_step.cuh"
 
 namespace lbmch {
 
@@ -124,7 +127,7 @@ __device__ __forceinline__ float phi_pair(const RawPair& rp, int k) {
 // One tile: node pairs x0 + 2 tx (BX pairs, 2 BX columns, clipped to nx) and rows
 // [y0, y0 + rows) (clipped to ny), by one CTA of BX x BY threads marching down BY rows at a time.
 // Same software pipeline and phi ring as the one-node kernel (see step_tile).
-template <int PREC, int BX, int BY>
+template <int PREC, int BX, int BY, bool WALLS>
 __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, char* __restrict__ dst,
                                                const Geometry& geo, const Phys<float>& ph, const int x0,
                                                const int y0, const int rows, int* __restrict__ flag,
@@ -145,7 +148,10 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   const int hx = (tx == 0) ? ((x0 == 0) ? nx - 1 : x0 - 1) : ((x0 + xv == nx) ? 0 : x0 + xv);
   const int hcol = (tx == 0) ? 0 : xv + 1;
 
-  auto wrap = [&](int r) -> int { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  auto wrap = [&](int r) -> int {  // periodic wrap; with walls, ghost rows map to the wall rows
+    if constexpr (WALLS) return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
+    return r < 0 ? r + ny : (r >= ny ? r - ny : r);
+  };
   auto slot = [&](int r) -> int { return (int)((unsigned)(r - (y0 - 1)) % (unsigned)RING); };
   auto pull_g2 = [&](int r, RawPairLoad& o) {
     const int y = wrap(r);
@@ -154,19 +160,32 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   auto pull_f2 = [&](int r, RawPairLoad& o) {
     pull_pair<PREC, false>(src, pl, pitch, x, xm2, xp2, r, r == 0 ? ny - 1 : r - 1, r == ny - 1 ? 0 : r + 1, o);
   };
-  auto pull_h = [&](int r, R out[9]) {
-    pull_raw<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, hx, wrap(r), out, pl);
+  // A row whose pulls cross a wall (walled lattices: y = 0 and y = ny - 1).  Ghost rows beyond a
+  // wall (y = -1, ny) are read only by the wall rows' stencils, which this kernel does not use.
+  auto wall_row = [&](int r) -> bool { return WALLS && (r == 0 || r == ny - 1); };
+  auto pull_h = [&](int r, R out[9]) -> bool {
+    return pull_raw<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, hx, wrap(r), out, pl);
   };
-  auto phi_h = [&](const R raw[9]) -> float {
+  auto phi_h = [&](const R raw[9], bool dec) -> float {
     float v[9];
-    unpack<PREC, true>(raw, false, v);
+    unpack<PREC, true>(raw, dec, v);
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
   };
   auto put_phi = [&](int r, const RawPair& g) {
     float* row = sphi[slot(r)];
+    if constexpr (WALLS) if (wall_row(r)) {  // bounce-back pull, node by node
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float v[9];
+        pull<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, x + k, r, v, pl);
+        row[2 * tx + 1 + k] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+      }
+      return;
+    }
     row[2 * tx + 1] = phi_pair<PREC>(g, 0);
     row[2 * tx + 2] = phi_pair<PREC>(g, 1);
   };
+  bool hBd = false;
 
   RawPair gA, gB, fA;
   RawPairLoad gC, fB;  // in flight
@@ -180,8 +199,8 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
         put_phi(r, gA);
       }
       if (halo) {
-        pull_h(r, hB);
-        sphi[slot(r)][hcol] = phi_h(hB);
+        hBd = pull_h(r, hB);
+        sphi[slot(r)][hcol] = phi_h(hB, hBd);
       }
     }
     if (ty == 0) {
@@ -193,8 +212,8 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       }
       if (halo) {
         R ht[9];
-        pull_h(y0 - 1, ht);
-        sphi[slot(y0 - 1)][hcol] = phi_h(ht);
+        const bool d = pull_h(y0 - 1, ht);
+        sphi[slot(y0 - 1)][hcol] = phi_h(ht, d);
       }
     }
     const int rb = y0 + BY + ty;
@@ -203,7 +222,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
         pull_g2(rb, gC);
         finish(gC, gB);
       }
-      if (halo) pull_h(rb, hB);
+      if (halo) hBd = pull_h(rb, hB);
     }
     if (colv && r < y1) {
       pull_f2(r, fB);
@@ -215,14 +234,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
     const int r = Y + ty;            // collided now
     const int rb = Y + BY + ty;      // phi formed now
     const int rc = Y + 2 * BY + ty;  // g issued now
-    const bool act = colv && r < y1;
+    const bool act = colv && r < y1 && !wall_row(r);
     if (rc <= y1 && colv) pull_g2(rc, gC);
     if (rb < y1 && colv) pull_f2(rb, fB);
     if (rb <= y1) {
       if (colv) put_phi(rb, gB);
-      if (halo) sphi[slot(rb)][hcol] = phi_h(hB);
+      if (halo) sphi[slot(rb)][hcol] = phi_h(hB, hBd);
     }
-    if (rc <= y1 && halo) pull_h(rc, hB);
+    if (rc <= y1 && halo) hBd = pull_h(rc, hB);
     __syncthreads();
     if (act) {
       const int sm = slot(r - 1), s0 = slot(r), sp = slot(r + 1);
@@ -291,13 +310,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   }
 }
 
-// Residency target: 3 CTAs of 128 threads per SM (12 warps).
-template <int PREC, int BX, int BY>
+// Residency target: 3 CTAs of 128 threads per SM (12 warps).  WALLS: compiled separately so that
+// the periodic kernel carries no wall code.
+template <int PREC, int BX, int BY, bool WALLS>
 __global__ void __launch_bounds__(BX * BY, 3)
 k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo, const Phys<float> ph,
             const int rows, int* __restrict__ flag) {
   __shared__ float sphi[3 * BY + 1][2 * BX + 2];
-  step_pair_tile<PREC, BX, BY>(src, dst, geo, ph, blockIdx.x * 2 * BX, blockIdx.y * rows, rows, flag, sphi,
+  step_pair_tile<PREC, BX, BY, WALLS>(src, dst, geo, ph, blockIdx.x * 2 * BX, blockIdx.y * rows, rows, flag, sphi,
                                Plane32{(unsigned)geo.plane});
 }
 
@@ -309,13 +329,16 @@ template <int PREC, int BX, int BY>
 cudaError_t pair_bxby(const HostGeometry& g, const HostPhys& p, int rows, const char* src, char* dst, int* flag,
                       cudaStream_t s) {
   dim3 grd((g.nx + 2 * BX - 1) / (2 * BX), (g.ny + rows - 1) / rows);
-  Geometry geo;
-  geo.nx = g.nx;
-  geo.ny = g.ny;
-  geo.pitch = g.pitch;
-  geo.plane = g.plane;
-  geo.walls = g.walls;
-  k_step_pair<PREC, BX, BY><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, make_phys<float>(p), rows, flag);
+  const Geometry geo = to_geo(g);
+  const Phys<float> ph = make_phys<float>(p);
+  if (!g.walls) {
+    k_step_pair<PREC, BX, BY, false><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph, rows, flag);
+  } else {
+    k_step_pair<PREC, BX, BY, true><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph, rows, flag);
+    // the two wall rows: one-node tile code, one row each
+    constexpr int EX = 256;
+    k_step_edge<PREC, EX><<<dim3((g.nx + EX - 1) / EX, 2), EX, 0, s>>>(src, dst, geo, ph, flag);
+  }
   return cudaGetLastError();
 }
 
@@ -333,7 +356,7 @@ template <int PREC>
 int pair_occ(int bx, int by) {
   int nb = 0;
 #define LBM_CASE(X, Y) \
-  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair<PREC, X, Y>, X * Y, 0);
+  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair<PREC, X, Y, false>, X * Y, 0);
   LBM_PAIR_TILES(LBM_CASE)
 #undef LBM_CASE
   return nb;
@@ -342,7 +365,7 @@ int pair_occ(int bx, int by) {
 }  // namespace
 
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by) {
-  if ((prec != 2 && prec != 3) || g.walls || g.nx % 2 || !offsets_fit_32(prec, g.plane)) return false;
+  if ((prec != 2 && prec != 3) || g.nx % 2 || !offsets_fit_32(prec, g.plane)) return false;
 #define LBM_CASE(X, Y) \
   if (bx == X && by == Y) return true;
   LBM_PAIR_TILES(LBM_CASE)

@@ -188,6 +188,18 @@ k_step(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
     step_tile<PREC, BX, BY>(src, dst, geo, ph, blockIdx.x * BX, blockIdx.y * rows, rows, flag, sphi, geo.plane);
 }
 
+// The two wall rows (y = 0 and y = ny - 1) of a walled lattice, one row each for blockIdx.y = 0
+// and 1: the rows another kernel (the paired 16-bit step) leaves out.
+template <int PREC, int BX>
+__global__ void __launch_bounds__(BX)
+k_step_edge(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
+            const Phys<typename Pop<PREC>::C> ph, int* __restrict__ flag) {
+  using C = typename Pop<PREC>::C;
+  __shared__ C sphi[4][BX + 2];
+  step_tile<PREC, BX, 1>(src, dst, geo, ph, blockIdx.x * BX, blockIdx.y ? geo.ny - 1 : 0, 1, flag, sphi,
+                         Plane32{(unsigned)geo.plane});
+}
+
 // -------------------------------------------------------------------------------------------
 // Batched step: a persistent grid walks a list of tiles drawn from many independent lattices.
 

@@ -323,20 +323,55 @@ def test_paired_16bit_kernel_follows_one_node_kernel(lbm, orc, prec):
 
 
 def test_paired_kernel_choice_and_limits(lbm):
-    """AUTO picks the paired kernel for 16-bit storage on periodic lattices with even nx, and the
-    one-node kernel otherwise; asking for it where it cannot serve is an error."""
+    """AUTO picks the paired kernel for 16-bit storage on lattices of 4 M nodes or more with even
+    nx (periodic or walled), and the one-node kernel otherwise; asking for it where it cannot serve
+    is an error."""
+    big = np.zeros((2048, 2048))
     even = W.spinodal(64, 40, seed=1)
     odd = W.spinodal(65, 40, seed=1)
-    assert lbm.Lattice(even, prec=lbm.LBM_FP16S).kernel[0] == lbm.LBM_KERNEL_PAIR
-    assert lbm.Lattice(even, prec=lbm.LBM_BF16S).kernel[0] == lbm.LBM_KERNEL_PAIR
+    for kw in (dict(prec=lbm.LBM_FP16S), dict(prec=lbm.LBM_BF16S), dict(prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y)):
+        lat = lbm.Lattice(big, **kw)
+        assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR, kw
+        lat.close()
+    assert lbm.Lattice(even, prec=lbm.LBM_FP16S).kernel[0] == lbm.LBM_KERNEL_GENERIC
     assert lbm.Lattice(odd, prec=lbm.LBM_FP16S).kernel[0] == lbm.LBM_KERNEL_GENERIC
-    assert lbm.Lattice(even, prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y).kernel[0] == lbm.LBM_KERNEL_GENERIC
     assert lbm.Lattice(even, prec=lbm.LBM_FP32).kernel[0] == lbm.LBM_KERNEL_GENERIC
-    for phi, kw in ((odd, dict(prec=lbm.LBM_FP16S)), (even, dict(prec=lbm.LBM_FP32)),
-                    (even, dict(prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y))):
+    lbm.Lattice(even, prec=lbm.LBM_FP16S).set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)  # small: allowed on request
+    for phi, kw in ((odd, dict(prec=lbm.LBM_FP16S)), (even, dict(prec=lbm.LBM_FP32))):
         lat = lbm.Lattice(phi, **kw)
         with pytest.raises(lbm.LbmError):
             lat.set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)
-        with pytest.raises(lbm.LbmError):
-            lbm.Lattice(even, prec=lbm.LBM_FP16S).set_kernel(lbm.LBM_KERNEL_PAIR, 128, 2)
         lat.close()
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(even, prec=lbm.LBM_FP16S).set_kernel(lbm.LBM_KERNEL_PAIR, 128, 2)
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_paired_16bit_kernel_with_walls(lbm, orc, prec):
+    """Walled lattices: the paired kernel collides the interior rows (forming phi on the wall rows
+    with the bounce-back pull) and a second launch steps the two wall rows with the one-node tile
+    code.  Moving walls, different wall gradients (Eq. 18 ghost rows) and a force on the droplet
+    phase, on a ragged even-width lattice: every paired tile follows the one-node kernel within one
+    16-bit rounding after 200 steps and both stay within the 16-bit bound of the FP64 oracle."""
+    phi0 = W.droplet(198, 46, 12, gamma=0.04, a=0.04, cy=14.0)
+    kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.6, bc=lbm.LBM_WALLS_Y, u_top=0.01, u_bottom=-0.005,
+              wet_bottom=0.15, wet_top=-0.1, force_y=-2e-5, force_mode=lbm.LBM_FORCE_PHASE_L)
+    ref = lbm.Lattice(phi0, **kw)
+    ref.set_kernel(lbm.LBM_KERNEL_GENERIC, 256, 1)
+    ref.step(200)
+    fr, gr = ref.populations()
+    o = orc.Oracle(phi0, **oracle_kwargs(kw))
+    o.step(200)
+    po = o.fields()[3]
+    bound = 2e-3 if prec == "fp16s" else 2e-2
+    assert abs_err(ref.fields()[3], po) <= bound
+    for bx, by in PAIR_TILES:
+        for rows in (0, 7):
+            lat = lbm.Lattice(phi0, **kw)
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR, bx, by, 0, rows)
+            assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR
+            lat.step(200)
+            f, g = lat.populations()
+            assert abs_err(f, fr) <= 1e-3 and abs_err(g, gr) <= 1e-3, (bx, by, rows, abs_err(f, fr), abs_err(g, gr))
+            assert abs_err(lat.fields()[3], po) <= bound
+            lat.close()

@@ -178,13 +178,15 @@ def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, ms_max: float) 
 # ------------------------------------------------------------------------------------------
 # CPU oracle leg (bounded sample).
 
-def time_oracle(budget_s: float, n_side: int, max_steps: int = 10**9):
+def time_oracle(budget_s: float, n_side: int, max_steps: int = 10**9, threads: int = 0):
     """Run the FP64 oracle on an n_side^2 sample of the workload for up to budget_s seconds
-    (whole steps).  Returns (MLUPS, steps, seconds, threads)."""
+    (whole steps) on `threads` OpenMP threads (0: all host cores).  Returns (MLUPS, steps,
+    seconds, threads used)."""
     import oracle
     from paper_1803_11345_gb300 import workloads as W
     oracle.build()
-    threads = oracle.set_threads(0)
+    default = oracle.set_threads(0)
+    threads = oracle.set_threads(threads if threads > 0 else default)
     phi0 = W.spinodal(n_side, n_side, seed=SEED)
     o = oracle.Oracle(phi0, visc_interp=1, **workload_params())
     o.step(1)
@@ -196,6 +198,7 @@ def time_oracle(budget_s: float, n_side: int, max_steps: int = 10**9):
             break
     dt = time.perf_counter() - t0
     o.close()
+    oracle.set_threads(default)
     return n_side * n_side * steps / dt / 1e6, steps, dt, threads
 
 
@@ -375,9 +378,12 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
             c_mlups, c_steps, c_dt, c_thr = time_oracle(args.cpu_budget, 128)
+            s_mlups, s_steps, s_dt, _ = time_oracle(min(5.0, args.cpu_budget), 128, threads=1)
             cpu = {"value": c_mlups, "unit": "MLUPS", "cores": c_thr, "kind": "oracle",
                    "sample": f"128x128 periodic sample of the spinodal workload, {c_steps} steps "
-                             f"in {c_dt:.1f} s, FP64"}
+                             f"in {c_dt:.1f} s, FP64",
+                   "serial": {"value": s_mlups, "unit": "MLUPS", "cores": 1,
+                              "sample": f"same sample, {s_steps} steps in {s_dt:.1f} s on one thread"}}
         except Exception as exc:  # report, do not hide
             cpu = {"value": None, "unit": "MLUPS", "cores": None, "kind": "oracle",
                    "sample": f"failed: {exc}"}
@@ -393,7 +399,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": config_dict(args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "frac_vs_nominal_8tbs": achieved / 8000.0, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "bytes_per_node": bpn, "kernel": kernel_name},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,

@@ -67,14 +67,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Sources that define the fused step kernels k_step / k_step_pair (the kernel the roofline reports).
-STEP_SOURCES = ("lbm_step.cuh", "lbm_pair.cu", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
+# Sources that define the fused step kernel the roofline reports: k_step (FP32 / FP64) and, for
+# 16-bit storage, k_step_pair as well.
+STEP_SOURCES = ("lbm_step.cuh", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
+PAIR_SOURCES = STEP_SOURCES + ("lbm_pair.cu",)
 
 
-def kernel_source_hash():
+def kernel_source_hash(prec: str = "fp32"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1803_11345_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in (PAIR_SOURCES if prec in ("fp16s", "bf16s") else STEP_SOURCES):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -94,7 +96,7 @@ def ncu_traffic(prec: str, n: int):
                 for kv in line.split(":", 1)[1].split():
                     k, v = kv.split("=")
                     vals[k] = v
-    if vals.get("source_hash") != kernel_source_hash():
+    if vals.get("source_hash") != kernel_source_hash(prec):
         return None
     try:
         per_node = float(vals["dram_bytes_per_node"])

@@ -368,6 +368,17 @@ __device__ __forceinline__ void unpack(const typename Pop<PREC>::R raw[9], bool 
   for (int i = 0; i < 9; ++i) out[i] = decoded ? P::kept(raw[i]) : (IS_G ? P::decg(i, raw[i]) : P::decf(i, raw[i]));
 }
 
+// c_i . (vx, vy) for lattice direction i, without multiplying by the velocity set's 0 and +-1
+// components (for finite inputs the same value as the two products and the sum).
+template <class C>
+__device__ __forceinline__ C lat_dot(int i, C vx, C vy) {
+  const int cx = lat_cx(i), cy = lat_cy(i);
+  if (cx == 0) return cy > 0 ? vy : -vy;
+  if (cy == 0) return cx > 0 ? vx : -vx;
+  if (cx == cy) return cx > 0 ? vx + vy : -(vx + vy);
+  return cx > 0 ? vx - vy : vy - vx;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Collision of one node.  Inputs: pulled f, g; phi = sum g; the Eq. 12 stencils dx, dy, lap of
 // phi.  Outputs overwrite f and g with the post-collision values.  Returns rho.
@@ -474,7 +485,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const C w = C(lat_w36(i)) / C(36);
-      const C cu = C(lat_cx(i)) * ux + C(lat_cy(i)) * uy;
+      const C cu = lat_dot<C>(i, ux, uy);
       // Eq. 11 weights (w^yy_4 = +1/3): axis i: w^xx = 1/3 on x-links, -1/6 on y-links; diagonals -1/24.
       C wxx, wyy, wxy;
       if (i <= 4) {
@@ -485,7 +496,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
       } else {
         wxx = -C(1) / C(24);
         wyy = -C(1) / C(24);
-        wxy = C(0.25) * C(lat_cx(i) * lat_cy(i));
+        wxy = C(0.25 * lat_cx(i) * lat_cy(i));
       }
       const C feq = w * (C(3) * pt + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu)) +
                     (wxx * gxx + wyy * gyy + wxy * gxy);
@@ -493,7 +504,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
       f[i] = f[i] + om * (feq - f[i]);
       if (ph.forced) {
         // Guo's source S_i = w_i [3 (c_i - u) . F + 9 (c_i . u)(c_i . F)], weighted 1 - omega/2
-        const C cF = C(lat_cx(i)) * Fx + C(lat_cy(i)) * Fy;
+        const C cF = lat_dot<C>(i, Fx, Fy);
         f[i] += (C(1) - C(0.5) * om) * w * (C(3) * (cF - (ux * Fx + uy * Fy)) + C(9) * cu * cF);
       }
     }
@@ -510,7 +521,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const C w = C(lat_w36(i)) / C(36);
-      const C cu = C(lat_cx(i)) * ux + C(lat_cy(i)) * uy;
+      const C cu = lat_dot<C>(i, ux, uy);
       const C geq = w * (gmu + phi * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
       sum += geq;
       g[i] = g[i] + ph.omega_phi * (geq - g[i]);

@@ -69,7 +69,7 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 // The paired 16-bit step (lbm_pair.cu): whether tile bx x by can serve the lattice (16-bit
 // storage, nx even, buffer under 4 GiB), resident CTAs per SM, and the launch.
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by);
-int pair_blocks_per_sm(int prec, const StepTile& t);
+int pair_blocks_per_sm(int prec, const StepTile& t, bool walls);
 cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
                              char* dst, int* flag, cudaStream_t s);
 

@@ -287,7 +287,7 @@ StepTile default_tile(int prec, const HostGeometry& g, int device) {
     t.bx = 128;
     t.by = 1;
     t.pair = 1;
-    t.rows = rows_for_wave(g, t, sms * std::max(1, pair_blocks_per_sm(prec, t)));
+    t.rows = rows_for_wave(g, t, sms * std::max(1, pair_blocks_per_sm(prec, t, g.walls != 0)));
     return t;
   }
   t.bx = 256;

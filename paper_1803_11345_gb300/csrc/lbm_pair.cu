@@ -11,12 +11,16 @@
 //   * the rest populations f_0, g_0 (FP32) are one 64-bit load;
 //   * the results of the two nodes are stored as 32-bit words (64-bit for the rest
 //     populations), rounded two at a time;
-// and every address is formed once for two nodes.  The per-node arithmetic is that of the
-// one-node kernel (same decode, collision, encode and closure functions).  With walls the kernel
+// and every address is formed once for two nodes.  The two nodes' arithmetic runs in the packed
+// FP32 instructions (lbm_f2.cuh): a 16-bit word of one direction decodes to the register pair
+// (node x, node x+1), the collision and stencils are the one-node kernel's functions instantiated
+// on that pair, and the encoded pair is again one word.  Decode, encode and closures round as
+// the one-node kernel does; the collision may place its FMAs differently (see F2Prod).  With walls the kernel
 // collides the interior rows only (it forms phi on the wall rows with the bounce-back pull) and
 // k_step_edge, the one-node tile code, steps the two wall rows in a second launch.
 // Requirements: nx even (pairs never straddle the periodic seam), population copy under 4 GiB.
 #include "lbm_device.cuh"
+#include "lbm_f2.cuh"
 #include "lbm_internal.h"
 #include "lbm_step.cuh"
 
@@ -106,21 +110,22 @@ __device__ __forceinline__ void pull_pair(const char* __restrict__ src, Plane32 
   o.r0b = r0.y;
 }
 
-// Node k (0: x, 1: x+1) of a pulled pair, as the one-node kernel's raw words.
+// The pulled populations of the pair decoded (lane .x node x, lane .y node x+1): the stored f
+// deviations shifted back by w_i as the one-node kernel's decode does.
 template <int PREC, bool IS_G>
-__device__ __forceinline__ void unpack_pair(const RawPair& rp, int k, float out[9]) {
-  using P = Pop<PREC>;
-  typename P::R raw[9];
-  raw[0] = __float_as_uint(k ? rp.r0b : rp.r0a);
+__device__ __forceinline__ void unpack_pair(const RawPair& rp, F2 out[9]) {
+  out[0] = F2(rp.r0a, rp.r0b);
 #pragma unroll
-  for (int i = 1; i < 9; ++i) raw[i] = k ? (rp.w[i - 1] >> 16) : (rp.w[i - 1] & 0xFFFFu);
-  unpack<PREC, IS_G>(raw, false, out);
+  for (int i = 1; i < 9; ++i) {
+    const F2 v(Pack<PREC>::unpack(rp.w[i - 1]));
+    out[i] = IS_G ? v : v + F2(Pop<PREC>::wrest(i));
+  }
 }
 
 template <int PREC>
-__device__ __forceinline__ float phi_pair(const RawPair& rp, int k) {
-  float v[9];
-  unpack_pair<PREC, true>(rp, k, v);
+__device__ __forceinline__ F2 phi_pair(const RawPair& rp) {
+  F2 v[9];
+  unpack_pair<PREC, true>(rp, v);
   return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
 }
 
@@ -129,7 +134,7 @@ __device__ __forceinline__ float phi_pair(const RawPair& rp, int k) {
 // Same software pipeline and phi ring as the one-node kernel (see step_tile).
 template <int PREC, int BX, int BY, bool WALLS>
 __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, char* __restrict__ dst,
-                                               const Geometry& geo, const Phys<float>& ph, const int x0,
+                                               const Geometry& geo, const Phys<F2>& ph, const int x0,
                                                const int y0, const int rows, int* __restrict__ flag,
                                                float (*sphi)[2 * BX + 2], const Plane32 pl) {
   using P = Pop<PREC>;
@@ -137,6 +142,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   constexpr int RING = 3 * BY + 1;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int nx = geo.nx, ny = geo.ny, pitch = geo.pitch;
+  const float u_top = ph.u_top.v.x, u_bottom = ph.u_bottom.v.x;
   const int y1 = min(y0 + rows, ny);
   const int xv = min(2 * BX, nx - x0);  // valid columns of this strip (even)
   const int x = x0 + 2 * tx;
@@ -164,7 +170,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   // wall (y = -1, ny) are read only by the wall rows' stencils, which this kernel does not use.
   auto wall_row = [&](int r) -> bool { return WALLS && (r == 0 || r == ny - 1); };
   auto pull_h = [&](int r, R out[9]) -> bool {
-    return pull_raw<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, hx, wrap(r), out, pl);
+    return pull_raw<PREC, true, Plane32>(src, geo, u_top, u_bottom, hx, wrap(r), out, pl);
   };
   auto phi_h = [&](const R raw[9], bool dec) -> float {
     float v[9];
@@ -177,13 +183,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         float v[9];
-        pull<PREC, true, Plane32>(src, geo, ph.u_top, ph.u_bottom, x + k, r, v, pl);
+        pull<PREC, true, Plane32>(src, geo, u_top, u_bottom, x + k, r, v, pl);
         row[2 * tx + 1 + k] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
       }
       return;
     }
-    row[2 * tx + 1] = phi_pair<PREC>(g, 0);
-    row[2 * tx + 2] = phi_pair<PREC>(g, 1);
+    const F2 p = phi_pair<PREC>(g);
+    row[2 * tx + 1] = p.v.x;
+    row[2 * tx + 2] = p.v.y;
   };
   bool hBd = false;
 
@@ -244,65 +251,43 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
     if (rc <= y1 && halo) hBd = pull_h(rc, hB);
     __syncthreads();
     if (act) {
-      const int sm = slot(r - 1), s0 = slot(r), sp = slot(r + 1);
-      // Node x is collided and encoded first (its moving populations packed two directions per
-      // word, held across the second collision), then node x+1; the stored words pair the nodes.
-      uint32_t qf[4], qg[4];  // node x: (d_1, d_2), (d_3, d_4), ... and (g_1, g_2), ...
-      float f0a = 0.f, g0a = 0.f;
+      // phi of columns x-1 .. x+2 on rows r-1, r, r+1, two aligned float2 per row; stencil
+      // entry s[dy+1][dx+1] holds (node x, node x+1).
+      const int rs[3] = {slot(r - 1), slot(r), slot(r + 1)};
+      F2 s[3][3];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        float s[3][3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          s[0][d] = sphi[sm][2 * tx + k + d];
-          s[1][d] = sphi[s0][2 * tx + k + d];
-          s[2][d] = sphi[sp][2 * tx + k + d];
-        }
-        float dxp, dyp, lap;
-        stencils<float>(s, dxp, dyp, lap);
-        const float phi = s[1][1];
-        float f[9], g[9];
-        unpack_pair<PREC, false>(fA, k, f);
-        unpack_pair<PREC, true>(gA, k, g);
-        const float rho = collide<float>(ph, f, g, phi, dxp, dyp, lap);
-        if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-        // Round the moving populations in pairs of directions (same rounding as one at a time)
-        // and form the rest closures from the rounded values.
-        uint32_t pf[4], pg[4];
-        float sf = 0.f, sg = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          pf[j] = Pack<PREC>::pack(f[2 * j + 1] - P::wrest(2 * j + 1), f[2 * j + 2] - P::wrest(2 * j + 2));
-          pg[j] = Pack<PREC>::pack(g[2 * j + 1], g[2 * j + 2]);
-          const float2 rf = Pack<PREC>::unpack(pf[j]), rg = Pack<PREC>::unpack(pg[j]);
-          sf += rf.x;
-          sf += rf.y;
-          sg += rg.x;
-          sg += rg.y;
-        }
-        const float f0 = P::rest_f(rho, sf), g0 = phi - sg;
-        if (k == 0) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            qf[j] = pf[j];
-            qg[j] = pg[j];
-          }
-          f0a = f0;
-          g0a = g0;
-        } else {
-          const unsigned e = (unsigned)(r * pitch + x);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            // direction 2j+1 pairs the low halves, direction 2j+2 the high halves
-            st_word(dst, ((unsigned)(2 * j) * pl.n + e) * 2u, __byte_perm(qf[j], pf[j], 0x5410));
-            st_word(dst, ((unsigned)(2 * j + 1) * pl.n + e) * 2u, __byte_perm(qf[j], pf[j], 0x7632));
-            st_word(dst, ((unsigned)(8 + 2 * j) * pl.n + e) * 2u, __byte_perm(qg[j], pg[j], 0x5410));
-            st_word(dst, ((unsigned)(9 + 2 * j) * pl.n + e) * 2u, __byte_perm(qg[j], pg[j], 0x7632));
-          }
-          *reinterpret_cast<float2*>(dst + ((unsigned)P::kRestFirst * pl.n + e) * 4u) = make_float2(f0a, f0);
-          *reinterpret_cast<float2*>(dst + ((unsigned)(P::kRestFirst + 1) * pl.n + e) * 4u) = make_float2(g0a, g0);
-        }
+      for (int d = 0; d < 3; ++d) {
+        const float2 lo = *reinterpret_cast<const float2*>(&sphi[rs[d]][2 * tx]);
+        const float2 hi = *reinterpret_cast<const float2*>(&sphi[rs[d]][2 * tx + 2]);
+        s[d][0] = F2(lo);
+        s[d][1] = F2(lo.y, hi.x);
+        s[d][2] = F2(hi);
       }
+      F2 dxp, dyp, lap;
+      stencils<F2>(s, dxp, dyp, lap);
+      const F2 phi = s[1][1];
+      F2 f[9], g[9];
+      unpack_pair<PREC, false>(fA, f);
+      unpack_pair<PREC, true>(gA, g);
+      const F2 rho = collide<F2>(ph, f, g, phi, dxp, dyp, lap);
+      if (!(isfinite(rho.v.x) && isfinite(rho.v.y) && isfinite(phi.v.x) && isfinite(phi.v.y))) atomicOr(flag, 1);
+      // Encode: direction i of both nodes rounds into one word (f as the deviation from w_i);
+      // the rest closures are formed from the rounded values in direction order.
+      const unsigned e = (unsigned)(r * pitch + x);
+      F2 sf(0.0f), sg(0.0f);
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const F2 d = f[i] - F2(P::wrest(i));
+        const uint32_t wf = Pack<PREC>::pack(d.v.x, d.v.y);
+        const uint32_t wg = Pack<PREC>::pack(g[i].v.x, g[i].v.y);
+        st_word(dst, ((unsigned)(i - 1) * pl.n + e) * 2u, wf);
+        st_word(dst, ((unsigned)(7 + i) * pl.n + e) * 2u, wg);
+        sf += F2(Pack<PREC>::unpack(wf));
+        sg += F2(Pack<PREC>::unpack(wg));
+      }
+      const F2 f0 = (rho - F2(5.0f / 9.0f)) - sf, g0 = phi - sg;
+      *reinterpret_cast<float2*>(dst + ((unsigned)P::kRestFirst * pl.n + e) * 4u) = f0.v;
+      *reinterpret_cast<float2*>(dst + ((unsigned)(P::kRestFirst + 1) * pl.n + e) * 4u) = g0.v;
     }
     gA = gB;
     finish(gC, gB);  // the loads issued at the top of this band have had the band to arrive
@@ -310,13 +295,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   }
 }
 
-// Residency target: 3 CTAs of 128 threads per SM (12 warps).  WALLS: compiled separately so that
-// the periodic kernel carries no wall code.
+// Residency target: 3 CTAs of 128 threads per SM (12 warps); the walled variant, which also pulls
+// the wall rows' bounce-back populations, 2 (it spills at the 3-CTA register cap).  WALLS:
+// compiled separately so that the periodic kernel carries no wall code.
 template <int PREC, int BX, int BY, bool WALLS>
-__global__ void __launch_bounds__(BX * BY, 3)
-k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo, const Phys<float> ph,
+__global__ void __launch_bounds__(BX * BY, WALLS ? 2 : 3)
+k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo, const Phys<F2> ph,
             const int rows, int* __restrict__ flag) {
-  __shared__ float sphi[3 * BY + 1][2 * BX + 2];
+  __shared__ __align__(16) float sphi[3 * BY + 1][2 * BX + 2];
   step_pair_tile<PREC, BX, BY, WALLS>(src, dst, geo, ph, blockIdx.x * 2 * BX, blockIdx.y * rows, rows, flag, sphi,
                                Plane32{(unsigned)geo.plane});
 }
@@ -330,11 +316,12 @@ cudaError_t pair_bxby(const HostGeometry& g, const HostPhys& p, int rows, const 
                       cudaStream_t s) {
   dim3 grd((g.nx + 2 * BX - 1) / (2 * BX), (g.ny + rows - 1) / rows);
   const Geometry geo = to_geo(g);
-  const Phys<float> ph = make_phys<float>(p);
+  const Phys<F2> ph2 = make_phys<F2>(p);
   if (!g.walls) {
-    k_step_pair<PREC, BX, BY, false><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph, rows, flag);
+    k_step_pair<PREC, BX, BY, false><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph2, rows, flag);
   } else {
-    k_step_pair<PREC, BX, BY, true><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph, rows, flag);
+    k_step_pair<PREC, BX, BY, true><<<grd, dim3(BX, BY), 0, s>>>(src, dst, geo, ph2, rows, flag);
+    const Phys<float> ph = make_phys<float>(p);
     // the two wall rows: one-node tile code, one row each
     constexpr int EX = 256;
     k_step_edge<PREC, EX><<<dim3((g.nx + EX - 1) / EX, 2), EX, 0, s>>>(src, dst, geo, ph, flag);
@@ -353,10 +340,12 @@ cudaError_t pair_prec(const HostGeometry& g, const HostPhys& p, const StepTile& 
 }
 
 template <int PREC>
-int pair_occ(int bx, int by) {
+int pair_occ(int bx, int by, bool walls) {
   int nb = 0;
-#define LBM_CASE(X, Y) \
-  if (bx == X && by == Y) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair<PREC, X, Y, false>, X * Y, 0);
+#define LBM_CASE(X, Y)                                                                                         \
+  if (bx == X && by == Y)                                                                                      \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                             \
+        &nb, walls ? k_step_pair<PREC, X, Y, true> : k_step_pair<PREC, X, Y, false>, X * Y, 0);
   LBM_PAIR_TILES(LBM_CASE)
 #undef LBM_CASE
   return nb;
@@ -373,8 +362,8 @@ bool pair_supported(int prec, const HostGeometry& g, int bx, int by) {
   return false;
 }
 
-int pair_blocks_per_sm(int prec, const StepTile& t) {
-  return prec == 2 ? pair_occ<2>(t.bx, t.by) : (prec == 3 ? pair_occ<3>(t.bx, t.by) : 0);
+int pair_blocks_per_sm(int prec, const StepTile& t, bool walls) {
+  return prec == 2 ? pair_occ<2>(t.bx, t.by, walls) : (prec == 3 ? pair_occ<3>(t.bx, t.by, walls) : 0);
 }
 
 cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,

@@ -295,11 +295,11 @@ PAIR_TILES = [(64, 2), (128, 1)]
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
 def test_paired_16bit_kernel_follows_one_node_kernel(lbm, orc, prec):
     """The paired 16-bit kernel (two nodes per thread) performs the one-node kernel's per-node
-    arithmetic (same decode, collision, encode and closure), so on a ragged periodic lattice
+    arithmetic in packed FP32 instructions (same decode, encode and closure roundings; the
+    collision's multiply-adds may be fused at other places), so on a ragged periodic lattice
     (nx = 326: even, not a multiple of any strip width; ny = 90; viscosity ratio 10) every paired
     tile follows the one-node kernel within one 16-bit rounding of a population after 200 steps
-    (measured: bit-identical; a separately compiled kernel may contract a multiply-add
-    differently), and both stay within the 16-bit bound of the FP64 oracle."""
+    (measured: 4e-7 FP16, 1.3e-6 BF16), and both stay within the 16-bit bound of the FP64 oracle."""
     phi0 = W.spinodal(326, 90, seed=4)
     kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53, visc=lbm.LBM_TAU_LINEAR)
     ref = lbm.Lattice(phi0, **kw)
@@ -351,8 +351,12 @@ def test_paired_16bit_kernel_with_walls(lbm, orc, prec):
     """Walled lattices: the paired kernel collides the interior rows (forming phi on the wall rows
     with the bounce-back pull) and a second launch steps the two wall rows with the one-node tile
     code.  Moving walls, different wall gradients (Eq. 18 ghost rows) and a force on the droplet
-    phase, on a ragged even-width lattice: every paired tile follows the one-node kernel within one
-    16-bit rounding after 200 steps and both stay within the 16-bit bound of the FP64 oracle."""
+    phase, on a ragged even-width lattice: every paired tile follows the one-node kernel within a
+    few 16-bit roundings after 200 steps and both stay within the 16-bit bound of the FP64 oracle.
+    The kernels fuse the collision's multiply-adds at different places; where that moves a moving
+    population across a rounding boundary, the FP32 rest closure moves by one 16-bit ulp of it,
+    and next to a moving contact line such differences persist: for BF16 one ulp at |g_i| ~ 0.11 is
+    4.9e-4 and two have been measured (1.04e-3), so BF16 states 2e-3 and FP16 1e-3."""
     phi0 = W.droplet(198, 46, 12, gamma=0.04, a=0.04, cy=14.0)
     kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.6, bc=lbm.LBM_WALLS_Y, u_top=0.01, u_bottom=-0.005,
               wet_bottom=0.15, wet_top=-0.1, force_y=-2e-5, force_mode=lbm.LBM_FORCE_PHASE_L)
@@ -372,6 +376,7 @@ def test_paired_16bit_kernel_with_walls(lbm, orc, prec):
             assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR
             lat.step(200)
             f, g = lat.populations()
-            assert abs_err(f, fr) <= 1e-3 and abs_err(g, gr) <= 1e-3, (bx, by, rows, abs_err(f, fr), abs_err(g, gr))
+            kb = 1e-3 if prec == "fp16s" else 2e-3
+            assert abs_err(f, fr) <= kb and abs_err(g, gr) <= kb, (bx, by, rows, abs_err(f, fr), abs_err(g, gr))
             assert abs_err(lat.fields()[3], po) <= bound
             lat.close()

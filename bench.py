@@ -70,7 +70,7 @@ def measured_peaks():
 # Sources that define the fused step kernel the roofline reports: k_step (FP32 / FP64) and, for
 # 16-bit storage, k_step_pair as well.
 STEP_SOURCES = ("lbm_step.cuh", "lbm_kernels.cu", "lbm_device.cuh", "lbm_internal.h")
-PAIR_SOURCES = STEP_SOURCES + ("lbm_pair.cu",)
+PAIR_SOURCES = STEP_SOURCES + ("lbm_pair.cu", "lbm_f2.cuh")
 
 
 def kernel_source_hash(prec: str = "fp32"):

@@ -195,10 +195,14 @@ typedef enum {
 
 /* Override the kernel and its tile: bx x by threads per CTA (0, 0 = default for the variant),
  * depth = bands of prefetch of the staged kernel (0 = default), rows = lattice rows per CTA
- * (0 = sized so the grid fills the GPU in one wave).  Affects later lbm_step calls only; results
- * do not depend on the choice beyond rounding order (none for FP64/FP32 here: every variant
- * performs the same operations per node).  LBM_ERR_PARAM for a combination without a compiled
- * kernel or a lattice the variant cannot serve. */
+ * (0 = sized so the grid fills the GPU in one wave; for PAIR on a periodic lattice up to 4 waves
+ * of at least 32 rows).
+ * Affects later lbm_step calls only.  Every variant performs the same operations per node, so
+ * results depend on the choice only through rounding: separately compiled kernels may fuse
+ * different multiply-adds (1-2 ulp per step in FP64 or FP32; PAIR computes in packed FP32
+ * instructions with its own fusions, and a 16-bit rounding can then land differently).
+ * LBM_ERR_PARAM for a combination without a compiled kernel or a lattice the variant cannot
+ * serve. */
 LBM_API int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int rows);
 
 /* The kernel and tile lbm_step uses now (variant is GENERIC, GENERIC_WIDE, PAIR or STAGED); NULL

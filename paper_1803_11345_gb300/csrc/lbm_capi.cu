@@ -423,7 +423,7 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
     const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t)
                        : t.pair ? pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0)
                                 : generic_blocks_per_sm(h->p.prec, t);
-    t.rows = rows_for_wave(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1));
+    t.rows = default_rows(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1));
   }
   h->tile = t;
   return LBM_OK;
@@ -473,7 +473,7 @@ int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
     if (!pair_supported(h->p.prec, h->geo, pt[0], pt[1])) continue;
     StepTile t{pt[0], pt[1], 0, 0, 1};
     t.pair = 1;
-    t.rows = rows_for_wave(h->geo, t, sms * pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0));
+    t.rows = default_rows(h->geo, t, sms * pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0));
     cands.push_back(t);
   }
   cudaEvent_t e0, e1;

@@ -105,12 +105,15 @@ int staged_blocks_per_sm(int prec, const StepTile& t);
 cudaError_t launch_step_staged(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
                                const char* src, char* dst, int* flag, cudaStream_t s);
 
-// Default tile for a precision and lattice, sized so the grid fills the GPU in one wave.
+// Default tile for a precision and lattice, sized so the grid fills the GPU in one wave (the paired kernel: a few waves).
 StepTile default_tile(int prec, const HostGeometry& g, int device);
 // Resident CTAs per SM of the generic kernel for a tile.
 int generic_blocks_per_sm(int prec, const StepTile& t);
 // Rows per CTA so that the grid is about `ctas` CTAs (one wave).
 int rows_for_wave(const HostGeometry& g, const StepTile& t, int ctas);
+// Default rows per CTA for a tile, given the CTAs of one wave: one wave for the one-node kernels,
+// up to 4 waves of at least 32 rows for the paired kernel on periodic lattices.
+int default_rows(const HostGeometry& g, const StepTile& t, int ctas_per_wave);
 // Whether a tile shape has a compiled kernel.
 bool tile_supported(int prec, int bx, int by);
 

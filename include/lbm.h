@@ -217,7 +217,7 @@ LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by,
 LBM_API int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms);
 
 /* ---------------------------------------------------------------------------------------------
- * Batches: many independent lattices (the benchmark spec's batched parameter sweep; the paper runs one
+ * Batches: many independent lattices (a batched parameter sweep; the paper runs one
  * lattice at a time).  Every member has its own lbm_params (sizes, viscosities, gamma, a, walls...)
  * but all share one precision.  One launch of a persistent kernel per time step advances every
  * member: resident CTAs walk a work list of tiles of roughly equal node count drawn from all

@@ -50,11 +50,14 @@ typedef enum {
   LBM_ERR_STATE = -6      /* call not valid for this handle                                */
 } lbm_status;
 
-/* Storage precision of the populations.  FP64: stored and computed in FP64.  FP32: stored and
- * computed in FP32.  FP16S / BF16S: the moving populations f_i - w_i and g_i (i >= 1) stored as
- * 16-bit deviations from the rest state; the rest populations f_0 and g_0 stored in FP32 as
- * closures (Eq. 10) of the rounded moving ones, so that storage conserves rho and phi exactly;
- * all arithmetic in FP32. */
+/* Storage precision of the populations.  Every precision computes the collision on deviations
+ * d_i = f_i - w_i from the rest state (rho = 1, v = 0), with every moment carried minus its rest
+ * value, so that no order-one quantity is added to the small departures that carry the flow.
+ * FP64: f_i stored and computed in FP64.  FP32: d_i and g_i stored and computed in FP32.
+ * FP16S / BF16S: the moving populations d_i and g_i (i >= 1) stored as 16-bit values; the rest
+ * populations d_0 and g_0 stored in FP32 as closures (Eq. 10) of the rounded moving ones, so that
+ * storage conserves rho and phi exactly; all arithmetic in FP32.  Whatever the precision, the FP64
+ * views of the state (lbm_fields, lbm_get_populations, lbm_set_populations) carry f_i itself. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
 
 /* Boundaries.  PERIODIC: both directions.  WALLS_Y: periodic in x, halfway bounce-back walls
@@ -270,8 +273,9 @@ LBM_API void lbm_batch_free(lbm_batch* b);
  * totals for the same state.
  *   state   device pointer (16-byte aligned) to one population copy in the layout lbm_init
  *           builds: pitch = nx rounded up to a multiple of 32, plane = pitch * ny elements;
- *           FP64/FP32: 18 planes (f_0..f_8, g_0..g_8) of that type; FP16S/BF16S: 16 16-bit planes
- *           (f_1 - w_1 .. f_8 - w_8, then g_1..g_8) followed by two FP32 planes (f_0, g_0).  For a lattice created
+ *           FP64: 18 planes (f_0..f_8, g_0..g_8); FP32: 18 planes (f_0 - w_0 .. f_8 - w_8,
+ *           g_0..g_8); FP16S/BF16S: 16 16-bit planes (f_1 - w_1 .. f_8 - w_8, then g_1..g_8)
+ *           followed by two FP32 planes (f_0 - w_0, g_0).  For a lattice created
  *           on a caller-supplied device_buffer, each population copy takes
  *           (lbm_state_bytes(p) - 256) / 2 bytes and the state after t = lbm_time(h) steps is the
  *           copy at device_buffer + (t % 2) * that size.

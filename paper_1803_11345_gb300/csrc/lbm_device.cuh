@@ -58,10 +58,24 @@ __device__ __forceinline__ E* plane_elem(char* b, PL pl, int first, int idx) {
 
 template <int PREC> struct Pop;
 
-// FP64 / FP32: plain values, plane p at element offset p * plane.
-template <class T> struct PopDense {
+// Lattice weight w_i in the arithmetic type, and in FP64 for the FP64 views of the state.
+template <class C> __host__ __device__ constexpr C lat_w(int i) { return C(lat_w36(i)) / C(36); }
+
+// How the storage policies below present f: every accessor for f gives and takes the deviation
+// d_i = f_i - w_i from the rest state (rho = 1, v = 0), the form the collision computes in, so
+// that no quantity of order one is added to the small departures from rest that carry the flow.
+// g is presented as stored.  ldf_full / stf_full give and take f_i itself, in FP64, for the
+// FP64 views of the state (fields, checkpoints).
+
+// FP64 / FP32: plain values, plane p at element offset p * plane.  The f planes hold f_i itself
+// (FP64: checkpoints round-trip bit for bit) or its deviation d_i (FP32, DEV: the rounding unit
+// of a stored value is then that of d_i, ~1e-3 to 1e-2, instead of that of w_i).
+template <class T, bool DEV> struct PopDense {
   using C = T;
   static constexpr size_t kBytesPerElem = 18 * sizeof(T);
+  // stored f value <-> deviation
+  __device__ __forceinline__ static C fdec(int i, C v) { return DEV ? v : v - lat_w<C>(i); }
+  __device__ __forceinline__ static C fenc(int i, C d) { return DEV ? d : d + lat_w<C>(i); }
   template <class PL> __device__ __forceinline__ static C ld(const char* b, PL pl, int p, int idx) {
     return __ldg(plane_elem<T>(b, pl, p, idx));
   }
@@ -69,20 +83,27 @@ template <class T> struct PopDense {
     *plane_elem<T>(b, pl, p, idx) = v;
   }
   template <class PL> __device__ __forceinline__ static C ldf(const char* b, PL pl, int i, int idx) {
-    return ld(b, pl, i, idx);
+    return fdec(i, ld(b, pl, i, idx));
   }
   template <class PL> __device__ __forceinline__ static C ldg(const char* b, PL pl, int i, int idx) {
     return ld(b, pl, 9 + i, idx);
   }
-  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C v) {
-    st(b, pl, i, idx, v);
+  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C d) {
+    st(b, pl, i, idx, fenc(i, d));
   }
   template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
     st(b, pl, 9 + i, idx, v);
   }
-  // rho, phi: the node's density and order parameter (used by the 16-bit closures only).
+  template <class PL> __device__ __forceinline__ static double ldf_full(const char* b, PL pl, int i, int idx) {
+    return DEV ? (double)ld(b, pl, i, idx) + lat_w<double>(i) : (double)ld(b, pl, i, idx);
+  }
+  template <class PL> __device__ __forceinline__ static void stf_full(char* b, PL pl, int i, int idx, double v) {
+    st(b, pl, i, idx, DEV ? (T)(v - lat_w<double>(i)) : (T)v);
+  }
+  // f: deviations; drho, phi: the node's density deviation and order parameter (used by the
+  // 16-bit closures only).
   template <class PL>
-  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], C /*rho*/,
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], C /*drho*/,
                                                     C /*phi*/) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -93,24 +114,23 @@ template <class T> struct PopDense {
   // Raw access: the stored bits, decoded only where used (keeps loads in flight).
   using R = T;
   template <class PL> __device__ __forceinline__ static R rawf(const char* b, PL pl, int i, int idx) {
-    return ldf(b, pl, i, idx);
+    return ld(b, pl, i, idx);
   }
   template <class PL> __device__ __forceinline__ static R rawg(const char* b, PL pl, int i, int idx) {
-    return ldg(b, pl, i, idx);
+    return ld(b, pl, 9 + i, idx);
   }
-  __device__ __forceinline__ static C decf(int, R r) { return r; }
+  __device__ __forceinline__ static C decf(int i, R r) { return fdec(i, r); }
   __device__ __forceinline__ static C decg(int, R r) { return r; }
   __device__ __forceinline__ static R keep(C v) { return v; }   // an already-decoded value
   __device__ __forceinline__ static C kept(R r) { return r; }
 };
-template <> struct Pop<0> : PopDense<double> {};
-template <> struct Pop<1> : PopDense<float> {};
+template <> struct Pop<0> : PopDense<double, false> {};
+template <> struct Pop<1> : PopDense<float, true> {};
 
-// 16-bit storage: 16 planes of 16-bit floats hold the moving populations, f_i - w_i for
-// i = 1..8 (deviation from the rest state rho = 1, v = 0) at plane i-1 and g_i (rest value 0) at
-// plane 7+i; then two FP32 planes hold the rest populations f_0 and g_0, stored as closures so
-// that every node's stored populations sum to its rho and phi (see store_node).  Arithmetic is
-// FP32.
+// 16-bit storage: 16 planes of 16-bit floats hold the moving populations, d_i = f_i - w_i for
+// i = 1..8 at plane i-1 and g_i (rest value 0) at plane 7+i; then two FP32 planes hold the rest
+// populations d_0 = f_0 - 4/9 and g_0, stored as closures so that every node's stored
+// populations sum to its rho and phi (see store_node).  Arithmetic is FP32.
 template <class H> struct Cvt;
 template <> struct Cvt<__half> {
   __device__ __forceinline__ static float to(__half h) { return __half2float(h); }
@@ -124,7 +144,6 @@ template <> struct Cvt<__nv_bfloat16> {
 template <class H> struct PopHalf {
   using C = float;
   static constexpr size_t kBytesPerElem = 16 * sizeof(H) + 2 * sizeof(float);
-  __device__ __forceinline__ static float wrest(int i) { return (float)lat_w36(i) * (1.0f / 36.0f); }
   // The two FP32 rest planes follow the 16 half planes: 16 * sizeof(H) / 4 float planes in.
   static constexpr int kRestFirst = 16 * (int)sizeof(H) / (int)sizeof(float);
   template <class PL> __device__ __forceinline__ static const float* rest(const char* b, PL pl, int set, int idx) {
@@ -141,44 +160,50 @@ template <class H> struct PopHalf {
   }
   template <class PL> __device__ __forceinline__ static C ldf(const char* b, PL pl, int i, int idx) {
     if (i == 0) return __ldg(rest(b, pl, 0, idx));
-    return Cvt<H>::to(__ldg(half(b, pl, i - 1, idx))) + wrest(i);
+    return Cvt<H>::to(__ldg(half(b, pl, i - 1, idx)));
   }
   template <class PL> __device__ __forceinline__ static C ldg(const char* b, PL pl, int i, int idx) {
     if (i == 0) return __ldg(rest(b, pl, 1, idx));
     return Cvt<H>::to(__ldg(half(b, pl, 7 + i, idx)));
   }
   // Single values (checkpoint restore): the rest populations are stored as given.
-  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C v) {
-    if (i == 0) *rest(b, pl, 0, idx) = v;
-    else *half(b, pl, i - 1, idx) = Cvt<H>::from(v - wrest(i));
+  template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C d) {
+    if (i == 0) *rest(b, pl, 0, idx) = d;
+    else *half(b, pl, i - 1, idx) = Cvt<H>::from(d);
   }
   template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
     if (i == 0) *rest(b, pl, 1, idx) = v;
     else *half(b, pl, 7 + i, idx) = Cvt<H>::from(v);
   }
+  template <class PL> __device__ __forceinline__ static double ldf_full(const char* b, PL pl, int i, int idx) {
+    return (double)ldf(b, pl, i, idx) + lat_w<double>(i);
+  }
+  template <class PL> __device__ __forceinline__ static void stf_full(char* b, PL pl, int i, int idx, double v) {
+    stf(b, pl, i, idx, (float)(v - lat_w<double>(i)));
+  }
   // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
   // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
   // to the node's rho and phi (the collision conserves both; the caller passes them): 16-bit
   // rounding then redistributes among directions but does not create or destroy mass or order
-  // parameter.  With deviations d_i = f_i - w_i, f_0 = (rho - 5/9) - sum d_i (sum_{i>0} w_i = 5/9).
+  // parameter.  In deviations (sum_i w_i = 1): d_0 = (rho - 1) - sum_{i>0} d_i.
   template <class PL>
-  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], float rho,
+  __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], float drho,
                                                     float phi) {
     float sf = 0.0f, sg = 0.0f;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-      const H hf = Cvt<H>::from(f[i] - wrest(i));
+      const H hf = Cvt<H>::from(f[i]);
       const H hg = Cvt<H>::from(g[i]);
       *half(b, pl, i - 1, idx) = hf;
       *half(b, pl, 7 + i, idx) = hg;
       sf += Cvt<H>::to(hf);
       sg += Cvt<H>::to(hg);
     }
-    *rest(b, pl, 0, idx) = rest_f(rho, sf);
+    *rest(b, pl, 0, idx) = rest_f(drho, sf);
     *rest(b, pl, 1, idx) = phi - sg;
   }
-  // The f rest closure from rho and the sum of the rounded moving deviations.
-  __device__ __forceinline__ static float rest_f(float rho, float sum_dev) { return (rho - 5.0f / 9.0f) - sum_dev; }
+  // The f rest closure from rho - 1 and the sum of the rounded moving deviations.
+  __device__ __forceinline__ static float rest_f(float drho, float sum_dev) { return drho - sum_dev; }
   // Raw access: 32-bit words holding either the FP32 rest value (i = 0) or the 16-bit pattern of
   // a moving population, decoded only where used so that loads stay in flight.
   using R = uint32_t;
@@ -195,7 +220,7 @@ template <class H> struct PopHalf {
     *reinterpret_cast<unsigned short*>(&h) = (unsigned short)r;
     return Cvt<H>::to(h);
   }
-  __device__ __forceinline__ static C decf(int i, R r) { return i == 0 ? __uint_as_float(r) : h2f(r) + wrest(i); }
+  __device__ __forceinline__ static C decf(int i, R r) { return i == 0 ? __uint_as_float(r) : h2f(r); }
   __device__ __forceinline__ static C decg(int i, R r) { return i == 0 ? __uint_as_float(r) : h2f(r); }
   __device__ __forceinline__ static R keep(C v) { return __float_as_uint(v); }
   __device__ __forceinline__ static C kept(R r) { return __uint_as_float(r); }
@@ -294,7 +319,9 @@ __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometr
     out[8] = LD(8, rp + xm);
     return;
   }
-  // Wall row: the node's own nine post-collision values give s and the reflected links.
+  // Wall row: the node's own nine post-collision values give s (rho for f, phi for g) and the
+  // reflected links.  f values are deviations from w_i; w_i is the same for a link and its
+  // reflection, so the links move as deviations and only s needs the rest density 1.
   C own[9];
   C s = C(0);
 #pragma unroll
@@ -302,6 +329,7 @@ __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometr
     own[i] = LD(i, r0 + x);
     s += own[i];
   }
+  if (!IS_G) s += C(1);
   out[0] = own[0];
   out[1] = LD(1, r0 + xm);
   out[3] = LD(3, r0 + xp);
@@ -380,13 +408,21 @@ __device__ __forceinline__ C lat_dot(int i, C vx, C vy) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Collision of one node.  Inputs: pulled f, g; phi = sum g; the Eq. 12 stencils dx, dy, lap of
-// phi.  Outputs overwrite f and g with the post-collision values.  Returns rho.
+// Collision of one node.  Inputs: pulled f as deviations d_i = f_i - w_i from the rest state,
+// pulled g; phi = sum g; the Eq. 12 stencils dx, dy, lap of phi.  Outputs overwrite f (again as
+// deviations) and g with the post-collision values.  Returns rho - 1.
+//
+// Every moment of f is carried minus its value at rest (rho = 1, u = 0): rho = 1 + drho, the raw
+// second moments m20 = m02 = 1/3 + M, m22 = 1/9 + R22, the central moments k3 = 2/3 + K3 and
+// k8 = 1/9 + K8, the pressure p~ = 1/3 + Pt.  The rest values cancel from Eq. 17 and from the
+// inverse transform, so they never enter the arithmetic and no rounding at the scale of w_i
+// (order 0.1) touches the departures from rest (order u ~ 1e-2 and below) that carry the flow.
 template <class C>
 __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C dx, C dy, C lap) {
   const C cs2 = C(1) / C(3);
-  // Macroscopic moments (paragraph after Eq. 14).
-  const C rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  // Macroscopic moments (paragraph after Eq. 14); sum_i w_i c_i = 0, so j needs no rest value.
+  const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const C rho = C(1) + drho;
   const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
   const C inv_rho = C(1) / rho;
@@ -396,11 +432,12 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
   const C ux = ph.forced ? (jx + C(0.5) * Fx) * inv_rho : jx * inv_rho;
   const C uy = ph.forced ? (jy + C(0.5) * Fy) * inv_rho : jy * inv_rho;
   const C ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-  // Chemical potential (free-energy paragraph), bulk pressure p0 (Eq. 13) and p~ (Eq. 14).
+  // Chemical potential (free-energy paragraph); the non-ideal part q = p~ - rho c_s^2 of the
+  // pressure (Eqs. 13, 14), and Pt = p~ - 1/3.
   const C phi2 = phi * phi;
   const C mu = ph.a * (phi2 * phi - phi) - ph.gamma * lap;
-  const C p0 = rho * cs2 + ph.a * phi2 * (C(0.75) * phi2 - C(0.5));
-  const C pt = p0 - ph.gamma * phi * lap;
+  const C q = ph.a * phi2 * (C(0.75) * phi2 - C(0.5)) - ph.gamma * phi * lap;
+  const C Pt = drho * cs2 + q;
   // Relaxation frequency of f for this phi (paragraph after Eq. 14).
   C om;
   if (ph.visc == 0) om = ph.omega_g + C(0.5) * (phi + C(1)) * (ph.omega_l - ph.omega_g);
@@ -410,10 +447,10 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
     // Pre-collision central moments k3, k4, k5 (Eq. 15 basis, k = T^T f) from the raw second
     // moments: kappa_20 = m_20 - rho ux^2, kappa_02 = m_02 - rho uy^2, kappa_11 = m_11 - rho ux uy.
     const C corners = (f[5] + f[6]) + (f[7] + f[8]);
-    const C m20 = (f[1] + f[3]) + corners;
-    const C m02 = (f[2] + f[4]) + corners;
+    const C M20 = (f[1] + f[3]) + corners;  // m_20 - 1/3
+    const C M02 = (f[2] + f[4]) + corners;  // m_02 - 1/3
     const C m11 = (f[5] - f[6]) + (f[7] - f[8]);
-    C k20 = m20 - rho * ux2, k02 = m02 - rho * uy2, k11 = m11 - rho * uxy;
+    C k20 = M20 - rho * ux2, k02 = M02 - rho * uy2, k11 = m11 - rho * uxy;  // kappa_20 - 1/3, ...
     if (ph.forced) {
       // with the half-force velocity the first central moments are -F/2 before the collision:
       // kappa_20 = m_20 - 2 ux kappa_10 - rho ux^2 and so on
@@ -421,64 +458,70 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
       k02 += uy * Fy;
       k11 += C(0.5) * (ux * Fy + uy * Fx);
     }
-    const C k3 = k20 + k02, k4 = k20 - k02, k5 = k11;
-    // Equilibrium central moments (the k_eq list and Eq. 16).
-    const C k3e = C(2) * pt;
+    const C K3 = k20 + k02, k4 = k20 - k02, k5 = k11;  // K3 = k3 - 2/3
+    // Equilibrium central moments (the k_eq list and Eq. 16): k3e = 2 p~; in k6e, k7e and k8e
+    // the ideal parts rho c_s^2 of p~ cancel against the rho c_s^2 terms, leaving q.
+    const C K3e = C(2) * Pt;
     const C k4e = ph.gamma * (dx * dx - dy * dy);
     const C k5e = ph.gamma * dx * dy;
-    const C k6e = -C(0.5) * uy * k4e - C(2) * ux * k5e + rho * uy * (cs2 - ux2) - pt * uy;
-    const C k7e = C(0.5) * ux * k4e - C(2) * uy * k5e + rho * ux * (cs2 - uy2) - pt * ux;
+    const C k6e = -C(0.5) * uy * k4e - C(2) * ux * k5e - rho * uy * ux2 - q * uy;
+    const C k7e = C(0.5) * ux * k4e - C(2) * uy * k5e - rho * ux * uy2 - q * ux;
     const C grad_term = ph.k8_printed ? lap : (dx * dx + dy * dy);
-    const C k8e = pt * (cs2 + ux2 + uy2) - rho * cs2 * (ux2 + uy2) + C(3) * rho * ux2 * uy2 -
-                  C(0.5) * cs2 * ph.gamma * grad_term + C(0.5) * k4e * (uy2 - ux2) + C(4) * uxy * k5e;
+    const C K8e = Pt * cs2 + q * (ux2 + uy2) + C(3) * rho * ux2 * uy2 - C(0.5) * cs2 * ph.gamma * grad_term +
+                  C(0.5) * k4e * (uy2 - ux2) + C(4) * uxy * k5e;  // k8e - 1/9
     // Eq. 17 with omega_4 = omega_5 = omega_rho, omega_3 free, omega_6..8 = 1.
-    const C k3s = k3 + ph.omega3 * (k3e - k3);
+    const C K3s = K3 + ph.omega3 * (K3e - K3);
     const C k4s = k4 + om * (k4e - k4);
     const C k5s = k5 + om * (k5e - k5);
     // Force: central moments of Guo's source, (T^T S)_j; zero for j = 0, 3, 4, 5, F for j = 1, 2,
     // and for j = 6..8 (omega = 1, so half of each is added):
-    C k6s = k6e, k7s = k7e, k8s = k8e;
+    C k6s = k6e, k7s = k7e, K8s = K8e;
     if (ph.forced) {
       k6s += C(0.5) * (Fy * cs2 - C(2) * Fx * uxy - Fy * ux2);
       k7s += C(0.5) * (Fx * cs2 - Fx * uy2 - C(2) * Fy * uxy);
-      k8s += C(2) * uxy * (Fx * uy + Fy * ux);
+      K8s += C(2) * uxy * (Fx * uy + Fy * ux);
     }
     // f* = (T^T)^-1 k*, k* = [rho, F_x/2, F_y/2, k3*, k4*, k5*, k6*, k7*, k8*] (the paper's
     // [rho, 0, 0, ...] without a force): central -> raw moments by the binomial shift
-    // c = cbar + u, then the D2Q9 raw-moment inversion.
-    const C a20 = C(0.5) * (k3s + k4s), a02 = C(0.5) * (k3s - k4s), a11 = k5s;
-    C r20 = a20 + rho * ux2;
-    C r02 = a02 + rho * uy2;
+    // c = cbar + u, then the D2Q9 raw-moment inversion.  A20 = a20 - 1/3, R20 = r20 - 1/3,
+    // R22 = r22 - 1/9; a20, a02 themselves only multiply velocities.
+    const C A20 = C(0.5) * (K3s + k4s), A02 = C(0.5) * (K3s - k4s), a11 = k5s;
+    const C a20 = A20 + cs2, a02 = A02 + cs2;
+    C R20 = A20 + rho * ux2;
+    C R02 = A02 + rho * uy2;
     C r11 = a11 + rho * uxy;
     C r21 = k6s + C(2) * ux * a11 + uy * a20 + rho * ux2 * uy;
     C r12 = k7s + C(2) * uy * a11 + ux * a02 + rho * ux * uy2;
-    C r22 = k8s + C(2) * (uy * k6s + ux * k7s) + uy2 * a20 + ux2 * a02 + C(4) * uxy * a11 + rho * ux2 * uy2;
+    C R22 = K8s + C(2) * (uy * k6s + ux * k7s) + uy2 * a20 + ux2 * a02 + C(4) * uxy * a11 + rho * ux2 * uy2;
     C r10 = jx, r01 = jy;
     if (ph.forced) {
       const C q1 = C(0.5) * Fx, q2 = C(0.5) * Fy;  // k*_1, k*_2
       r10 = jx + Fx;                               // rho ux + k*_1
       r01 = jy + Fy;
-      r20 += C(2) * ux * q1;
-      r02 += C(2) * uy * q2;
+      R20 += C(2) * ux * q1;
+      R02 += C(2) * uy * q2;
       r11 += ux * q2 + uy * q1;
       r21 += ux2 * q2 + C(2) * uxy * q1;
       r12 += uy2 * q1 + C(2) * uxy * q2;
-      r22 += C(2) * uxy * (uy * q1 + ux * q2);
+      R22 += C(2) * uxy * (uy * q1 + ux * q2);
     }
-    f[0] = rho - r20 - r02 + r22;
-    const C hx = C(0.5) * (r20 - r22), hy = C(0.5) * (r02 - r22);
+    // Deviations: f0 = rho - r20 - r02 + r22 (w_0 = 4/9 = 1 - 2/3 + 1/9), f1 = (r20 - r22)/2 +
+    // (r10 - r12)/2 (w_1 = 1/9 = (1/3 - 1/9)/2), f5 = (r22 + r11 + r21 + r12)/4 (w_5 = 1/36), ...
+    f[0] = drho - R20 - R02 + R22;
+    const C hx = C(0.5) * (R20 - R22), hy = C(0.5) * (R02 - R22);
     const C qx = C(0.5) * (r10 - r12), qy = C(0.5) * (r01 - r21);
     f[1] = hx + qx;
     f[3] = hx - qx;
     f[2] = hy + qy;
     f[4] = hy - qy;
-    const C s22 = C(0.25) * r22, s11 = C(0.25) * r11, s21 = C(0.25) * r21, s12 = C(0.25) * r12;
+    const C s22 = C(0.25) * R22, s11 = C(0.25) * r11, s21 = C(0.25) * r21, s12 = C(0.25) * r12;
     f[5] = s22 + s11 + s21 + s12;
     f[6] = s22 - s11 + s21 - s12;
     f[7] = s22 + s11 - s21 - s12;
     f[8] = s22 - s11 - s21 + s12;
   } else {
-    // Double-BGK baseline, Eq. 6 with f_eq from Eqs. 8, 10, 11.
+    // Double-BGK baseline, Eq. 6 with f_eq from Eqs. 8, 10, 11; 3 p~ = 1 + 3 Pt, so
+    // f_eq,i - w_i = w_i (3 Pt + rho (...)) + the gradient terms, and f_eq,0 - w_0 = drho - sum.
     const C uu = ux2 + uy2;
     const C gxx = ph.gamma * dx * dx, gyy = ph.gamma * dy * dy, gxy = ph.gamma * dx * dy;
     C sum = C(0);
@@ -498,18 +541,18 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
         wyy = -C(1) / C(24);
         wxy = C(0.25 * lat_cx(i) * lat_cy(i));
       }
-      const C feq = w * (C(3) * pt + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu)) +
+      const C deq = w * (C(3) * Pt + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu)) +
                     (wxx * gxx + wyy * gyy + wxy * gxy);
-      sum += feq;
-      f[i] = f[i] + om * (feq - f[i]);
+      sum += deq;
+      f[i] = f[i] + om * (deq - f[i]);
       if (ph.forced) {
         // Guo's source S_i = w_i [3 (c_i - u) . F + 9 (c_i . u)(c_i . F)], weighted 1 - omega/2
         const C cF = lat_dot<C>(i, Fx, Fy);
         f[i] += (C(1) - C(0.5) * om) * w * (C(3) * (cF - (ux * Fx + uy * Fy)) + C(9) * cu * cF);
       }
     }
-    const C feq0 = rho - sum;
-    f[0] = f[0] + om * (feq0 - f[0]);
+    const C deq0 = drho - sum;
+    f[0] = f[0] + om * (deq0 - f[0]);
     if (ph.forced) f[0] += (C(1) - C(0.5) * om) * (C(4) / C(9)) * (-C(3) * (ux * Fx + uy * Fy));
   }
 
@@ -528,7 +571,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
     }
     g[0] = g[0] + ph.omega_phi * ((phi - sum) - g[0]);
   }
-  return rho;
+  return drho;
 }
 
 // Isotropic stencils of Eq. 12 from the 3x3 neighbourhood of phi.  Index convention:

@@ -56,11 +56,14 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
   C gx, gy, lap;
   stencils<C>(s, gx, gy, lap);
   const long long n = (long long)y * geo.nx + x;
-  const C phi = s[1][1], ux = (C)ux0[n], uy = (C)uy0[n], rho = (C)rho0[n];
+  // f is formed as deviations f_i - w_i (the form the collision and the storage take): with
+  // 3 p~ = 1 + 3 Pt, f_eq,i - w_i = w_i (3 Pt + rho poly_i) + the Eq. 11 gradient terms.
+  const C phi = s[1][1], ux = (C)ux0[n], uy = (C)uy0[n];
+  const C drho = (C)(rho0[n] - 1.0), rho = C(1) + drho;
   const C cs2 = C(1) / C(3);
   const C phi2 = phi * phi;
   const C mu = ph.a * (phi2 * phi - phi) - ph.gamma * lap;
-  const C pt = rho * cs2 + ph.a * phi2 * (C(0.75) * phi2 - C(0.5)) - ph.gamma * phi * lap;
+  const C Pt = drho * cs2 + (ph.a * phi2 * (C(0.75) * phi2 - C(0.5)) - ph.gamma * phi * lap);
   const C uu = ux * ux + uy * uy;
   C f[9], g[9];
   C sf = C(0), sg = C(0);
@@ -80,15 +83,15 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
       wyy = -C(1) / C(24);
       wxy = C(0.25) * C(lat_cx(i) * lat_cy(i));
     }
-    f[i] = w * (C(3) * pt + rho * poly) + ph.gamma * (wxx * gx * gx + wyy * gy * gy + wxy * gx * gy);
+    f[i] = w * (C(3) * Pt + rho * poly) + ph.gamma * (wxx * gx * gx + wyy * gy * gy + wxy * gx * gy);
     g[i] = w * (ph.Gamma * mu + phi * poly);
     sf += f[i];
     sg += g[i];
   }
-  f[0] = rho - sf;
+  f[0] = drho - sf;
   g[0] = phi - sg;
-  const C rho_c = collide<C>(ph, f, g, phi, gx, gy, lap);
-  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g, rho_c, phi);
+  const C drho_c = collide<C>(ph, f, g, phi, gx, gy, lap);
+  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g, drho_c, phi);
 }
 
 // -------------------------------------------------------------------------------------------
@@ -104,15 +107,16 @@ __global__ void k_fields(const char* __restrict__ src, const Geometry geo, const
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= geo.nx || y >= geo.ny) return;
   const int idx = y * geo.pitch + x;
-  double rho = 0, jx = 0, jy = 0, phi = 0;
+  double drho = 0, jx = 0, jy = 0, phi = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const double fi = (double)P::ldf(src, geo.plane, i, idx);
-    rho += fi;
-    jx += fi * lat_cx(i);
-    jy += fi * lat_cy(i);
+    const double di = (double)P::ldf(src, geo.plane, i, idx);  // f_i - w_i
+    drho += di;
+    jx += di * lat_cx(i);
+    jy += di * lat_cy(i);
     phi += (double)P::ldg(src, geo.plane, i, idx);
   }
+  const double rho = 1.0 + drho;
   const long long N = (long long)geo.nx * geo.ny;
   const long long n = (long long)y * geo.nx + x;
   const double wf = fmode ? 0.5 * (1.0 + phi) : 1.0;
@@ -139,17 +143,17 @@ k_reduce_partials(const char* __restrict__ src, const Geometry geo, double* __re
        n += (long long)gridDim.x * kRedThreads) {
     const int y = (int)(n / geo.nx), x = (int)(n - (long long)y * geo.nx);
     const int idx = y * geo.pitch + x;
-    double rho = 0, jx = 0, jy = 0, phi = 0;
+    double drho = 0, jx = 0, jy = 0, phi = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const double fi = (double)P::ldf(src, geo.plane, i, idx);
-      rho += fi;
-      jx += fi * lat_cx(i);
-      jy += fi * lat_cy(i);
+      const double di = (double)P::ldf(src, geo.plane, i, idx);  // f_i - w_i
+      drho += di;
+      jx += di * lat_cx(i);
+      jy += di * lat_cy(i);
       phi += (double)P::ldg(src, geo.plane, i, idx);
     }
     acc[0] += phi;
-    acc[1] += rho;
+    acc[1] += 1.0 + drho;
     acc[2] += jx;
     acc[3] += jy;
   }
@@ -194,7 +198,7 @@ __global__ void k_plane_get(const char* __restrict__ src, const Geometry geo, in
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= geo.nx || y >= geo.ny) return;
   const int idx = y * geo.pitch + x;
-  const double v = p < 9 ? (double)P::ldf(src, geo.plane, p, idx) : (double)P::ldg(src, geo.plane, p - 9, idx);
+  const double v = p < 9 ? P::ldf_full(src, geo.plane, p, idx) : (double)P::ldg(src, geo.plane, p - 9, idx);
   out[(long long)y * geo.nx + x] = v;
 }
 
@@ -206,9 +210,9 @@ __global__ void k_plane_set(char* __restrict__ dst, const Geometry geo, int p, c
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= geo.nx || y >= geo.ny) return;
   const int idx = y * geo.pitch + x;
-  const C v = (C)in[(long long)y * geo.nx + x];
-  if (p < 9) P::stf(dst, geo.plane, p, idx, v);
-  else P::stg(dst, geo.plane, p - 9, idx, v);
+  const double v = in[(long long)y * geo.nx + x];
+  if (p < 9) P::stf_full(dst, geo.plane, p, idx, v);
+  else P::stg(dst, geo.plane, p - 9, idx, (C)v);
 }
 
 // -------------------------------------------------------------------------------------------

@@ -110,22 +110,19 @@ __device__ __forceinline__ void pull_pair(const char* __restrict__ src, Plane32 
   o.r0b = r0.y;
 }
 
-// The pulled populations of the pair decoded (lane .x node x, lane .y node x+1): the stored f
-// deviations shifted back by w_i as the one-node kernel's decode does.
-template <int PREC, bool IS_G>
+// The pulled populations of the pair decoded (lane .x node x, lane .y node x+1); f stays in the
+// stored form, deviations from w_i, which is the form the collision takes.
+template <int PREC>
 __device__ __forceinline__ void unpack_pair(const RawPair& rp, F2 out[9]) {
   out[0] = F2(rp.r0a, rp.r0b);
 #pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    const F2 v(Pack<PREC>::unpack(rp.w[i - 1]));
-    out[i] = IS_G ? v : v + F2(Pop<PREC>::wrest(i));
-  }
+  for (int i = 1; i < 9; ++i) out[i] = F2(Pack<PREC>::unpack(rp.w[i - 1]));
 }
 
 template <int PREC>
 __device__ __forceinline__ F2 phi_pair(const RawPair& rp) {
   F2 v[9];
-  unpack_pair<PREC, true>(rp, v);
+  unpack_pair<PREC>(rp, v);
   return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
 }
 
@@ -267,25 +264,24 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       stencils<F2>(s, dxp, dyp, lap);
       const F2 phi = s[1][1];
       F2 f[9], g[9];
-      unpack_pair<PREC, false>(fA, f);
-      unpack_pair<PREC, true>(gA, g);
-      const F2 rho = collide<F2>(ph, f, g, phi, dxp, dyp, lap);
-      if (!(isfinite(rho.v.x) && isfinite(rho.v.y) && isfinite(phi.v.x) && isfinite(phi.v.y))) atomicOr(flag, 1);
-      // Encode: direction i of both nodes rounds into one word (f as the deviation from w_i);
-      // the rest closures are formed from the rounded values in direction order.
+      unpack_pair<PREC>(fA, f);
+      unpack_pair<PREC>(gA, g);
+      const F2 drho = collide<F2>(ph, f, g, phi, dxp, dyp, lap);
+      if (!(isfinite(drho.v.x) && isfinite(drho.v.y) && isfinite(phi.v.x) && isfinite(phi.v.y))) atomicOr(flag, 1);
+      // Encode: direction i of both nodes rounds into one word; the rest closures are formed
+      // from the rounded values in direction order.
       const unsigned e = (unsigned)(r * pitch + x);
       F2 sf(0.0f), sg(0.0f);
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const F2 d = f[i] - F2(P::wrest(i));
-        const uint32_t wf = Pack<PREC>::pack(d.v.x, d.v.y);
+        const uint32_t wf = Pack<PREC>::pack(f[i].v.x, f[i].v.y);
         const uint32_t wg = Pack<PREC>::pack(g[i].v.x, g[i].v.y);
         st_word(dst, ((unsigned)(i - 1) * pl.n + e) * 2u, wf);
         st_word(dst, ((unsigned)(7 + i) * pl.n + e) * 2u, wg);
         sf += F2(Pack<PREC>::unpack(wf));
         sg += F2(Pack<PREC>::unpack(wg));
       }
-      const F2 f0 = (rho - F2(5.0f / 9.0f)) - sf, g0 = phi - sg;
+      const F2 f0 = drho - sf, g0 = phi - sg;
       *reinterpret_cast<float2*>(dst + ((unsigned)P::kRestFirst * pl.n + e) * 4u) = f0.v;
       *reinterpret_cast<float2*>(dst + ((unsigned)(P::kRestFirst + 1) * pl.n + e) * 4u) = g0.v;
     }

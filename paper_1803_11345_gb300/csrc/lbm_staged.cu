@@ -44,38 +44,38 @@ template <int PREC> struct Stage {
   // Output staging: plane q = 0..17 (f_0..f_8, g_0..g_8), n elements each, packed in order.
   __host__ __device__ static constexpr int oes(int q) { return q < 9 ? es(false, q) : es(true, q - 9); }
   __host__ __device__ static constexpr int ooff(int q, int n) { return q == 0 ? 0 : ooff(q - 1, n) + n * oes(q - 1); }
-  // Population value from a staged row (a points at the element).
+  // Population value from a staged row (a points at the element); f as its deviation from w_p,
+  // as Pop<PREC> presents it.
   __device__ __forceinline__ static C sld(const char* a, bool g, int p) {
-    if constexpr (PREC == 0) return *reinterpret_cast<const double*>(a);
-    else if constexpr (PREC == 1) return *reinterpret_cast<const float*>(a);
-    else {
+    if constexpr (!kHalf) {
+      const C v = *reinterpret_cast<const C*>(a);
+      return g ? v : P::fdec(p, v);
+    } else {
       if (p == 0) return *reinterpret_cast<const float*>(a);
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
-      const float v = Cvt<Hf>::to(*reinterpret_cast<const Hf*>(a));
-      return g ? v : v + (float)lat_w36(p) * (1.0f / 36.0f);
+      return Cvt<Hf>::to(*reinterpret_cast<const Hf*>(a));
     }
   }
   // Store the post-collision populations of one node (element e of every output plane of n
   // elements) into the staging buffer, with the same encoding as Pop<PREC>::store_node.
-  __device__ __forceinline__ static void store_node(char* ob, int n, int e, const C f[9], const C g[9], C rho,
+  __device__ __forceinline__ static void store_node(char* ob, int n, int e, const C f[9], const C g[9], C drho,
                                                     C phi) {
     if constexpr (!kHalf) {
 #pragma unroll
-      for (int q = 0; q < 18; ++q) reinterpret_cast<C*>(ob + ooff(q, n))[e] = q < 9 ? f[q] : g[q - 9];
+      for (int q = 0; q < 18; ++q) reinterpret_cast<C*>(ob + ooff(q, n))[e] = q < 9 ? P::fenc(q, f[q]) : g[q - 9];
     } else {
       using Hf = typename std::conditional<PREC == 2, __half, __nv_bfloat16>::type;
       float sf = 0.0f, sg = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const float w = (float)lat_w36(i) * (1.0f / 36.0f);
-        const Hf hf = Cvt<Hf>::from(f[i] - w);
+        const Hf hf = Cvt<Hf>::from(f[i]);
         const Hf hg = Cvt<Hf>::from(g[i]);
         reinterpret_cast<Hf*>(ob + ooff(i, n))[e] = hf;
         reinterpret_cast<Hf*>(ob + ooff(9 + i, n))[e] = hg;
         sf += Cvt<Hf>::to(hf);
         sg += Cvt<Hf>::to(hg);
       }
-      reinterpret_cast<float*>(ob + ooff(0, n))[e] = PopHalf<Hf>::rest_f(rho, sf);
+      reinterpret_cast<float*>(ob + ooff(0, n))[e] = PopHalf<Hf>::rest_f(drho, sf);
       reinterpret_cast<float*>(ob + ooff(9, n))[e] = phi - sg;
     }
   }
@@ -263,6 +263,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       own[i] = L(q.mid, i, 0);
       s += own[i];
     }
+    if (!g) s += C(1);  // f values are deviations from w_i: rho = 1 + their sum
     out[0] = own[0];
     out[1] = L(q.mid, 1, -1);
     out[3] = L(q.mid, 3, 1);
@@ -319,6 +320,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       own[i] = L(q.mid, i, 0);
       s += own[i];
     }
+    if (!g) s += C(1);  // f values are deviations from w_i: rho = 1 + their sum
     out[0] = own[0];
     out[1] = L(q.mid, 1, -1);
     out[3] = L(q.mid, 3, 1);
@@ -427,9 +429,9 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       C dxp, dyp, lap;
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
-      const C rho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
-      if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-      S::store_node(obuf, NOUT, ty * BX + tx, f, gcur, rho, phi);
+      const C drho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
+      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, 1);
+      S::store_node(obuf, NOUT, ty * BX + tx, f, gcur, drho, phi);
       fence_proxy_async_smem();
     }
     __syncthreads();

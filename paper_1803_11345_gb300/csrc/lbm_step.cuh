@@ -158,9 +158,9 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
       C f[9], g[9];
       unpack<PREC, false>(fA, fAd, f);
       unpack<PREC, true>(gA, gAd, g);
-      const C rho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
-      if (!(isfinite(rho) && isfinite(phi))) atomicOr(flag, 1);
-      P::store_node(dst, pl, r * geo.pitch + x, f, g, rho, phi);
+      const C drho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
+      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, 1);
+      P::store_node(dst, pl, r * geo.pitch + x, f, g, drho, phi);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {

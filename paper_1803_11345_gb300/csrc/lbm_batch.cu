@@ -206,6 +206,8 @@ int lbm_batch_state_bytes(const lbm_params* params, int count, size_t* bytes) {
     HostPhys ph;
     const char* msg = validate_params(&params[m], &geo[m], &ph);
     if (msg) return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: member %d: %s", m, msg);
+    if (params[m].rounding != LBM_ROUND_NEAREST)
+      return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: member %d: stochastic rounding is not available in batches", m);
     if (params[m].prec != params[0].prec)
       return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: all members need the same precision");
   }
@@ -229,6 +231,8 @@ int lbm_batch_init(const lbm_params* params, int count, const double* const* phi
   for (int m = 0; m < count; ++m) {
     const char* msg = validate_params(&params[m], &b->geo[m], &b->phys[m]);
     if (!msg && params[m].prec != b->prec) msg = "all members need the same precision";
+    // a batch replays captured CUDA graphs, whose launches cannot carry a new key every step
+    if (!msg && params[m].rounding != LBM_ROUND_NEAREST) msg = "stochastic rounding is not available in batches";
     if (!msg && !phi0[m]) msg = "phi0 is NULL";
     if (msg) {
       fail(nullptr, LBM_ERR_PARAM, "lbm_batch_init: member %d: %s", m, msg);

@@ -65,6 +65,21 @@ std::string tune_key(const lbm_lattice* h, int sms) {
 }
 
 char* state_buf(lbm_lattice* h) { return h->buf + (size_t)h->cur * h->pop_bytes; }
+
+// Key of the stochastic-rounding stream for time step t: the 32-bit finaliser of MurmurHash3
+// (A. Appleby) over the seed and both halves of t; never 0 (0 means round to nearest).
+uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+uint32_t step_key(uint32_t seed, long long t) {
+  const uint32_t k = fmix32(fmix32(seed ^ 0x5bd1e995u) + (uint32_t)t) ^ fmix32((uint32_t)((unsigned long long)t >> 32));
+  return k ? k : 1u;
+}
 char* other_buf(lbm_lattice* h) { return h->buf + (size_t)(1 - h->cur) * h->pop_bytes; }
 
 }  // namespace
@@ -80,6 +95,10 @@ const char* lbmch::validate_params(const lbm_params* p, HostGeometry* g, HostPhy
   if (p->collision != LBM_COLLIDE_CM && p->collision != LBM_COLLIDE_BGK) return "collision must be an lbm_collision";
   if (p->force_mode != LBM_FORCE_UNIFORM && p->force_mode != LBM_FORCE_PHASE_L)
     return "force_mode must be an lbm_force_mode";
+  if (p->rounding != LBM_ROUND_NEAREST && p->rounding != LBM_ROUND_STOCHASTIC)
+    return "rounding must be an lbm_rounding";
+  if (p->rounding == LBM_ROUND_STOCHASTIC && p->prec != LBM_FP16S && p->prec != LBM_BF16S)
+    return "stochastic rounding needs 16-bit storage (FP16S or BF16S)";
   const double vals[] = {p->tau_l,  p->tau_g,      p->M,       p->Gamma,   p->gamma,   p->a,      p->omega3,
                          p->u_top, p->u_bottom, p->wet_bottom, p->wet_top, p->force_x, p->force_y};
   for (double v : vals)
@@ -117,6 +136,9 @@ const char* lbmch::validate_params(const lbm_params* p, HostGeometry* g, HostPhy
   ph->visc = p->visc;
   ph->k8_printed = p->k8_form == LBM_K8_PRINTED;
   ph->bgk = p->collision == LBM_COLLIDE_BGK;
+  ph->rounding = p->rounding;
+  ph->seed = p->seed;
+  ph->sr_key = 0;
   return nullptr;
 }
 
@@ -291,9 +313,10 @@ int lbm_step(lbm_lattice* h, int n) {
     set_err(h->err, "lbm_step: n must be >= 0");
     return LBM_ERR_PARAM;
   }
+  HostPhys ph = h->phys;
   for (int s = 0; s < n; ++s) {
-    cudaError_t e = launch_step(h->p.prec, h->geo, h->phys, h->tile, state_buf(h), other_buf(h),
-                                h->flag, h->stream);
+    if (ph.rounding == LBM_ROUND_STOCHASTIC) ph.sr_key = step_key(ph.seed, h->t);
+    cudaError_t e = launch_step(h->p.prec, h->geo, ph, h->tile, state_buf(h), other_buf(h), h->flag, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, "lbm_step launch", e);
     h->cur = 1 - h->cur;
     ++h->t;
@@ -407,7 +430,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
     t.bx = bx ? bx : 128;
     t.by = by ? by : 1;
   }
-  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t)
+  // The staged kernel stores from shared memory without the node index the rounding stream needs.
+  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) && h->phys.rounding == LBM_ROUND_NEAREST
                   : t.pair ? pair_supported(h->p.prec, h->geo, t.bx, t.by)
                            : tile_supported(h->p.prec, t.bx, t.by);
   if (!ok) {
@@ -464,7 +488,7 @@ int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
   const int stiles[][3] = {{64, 4, 1}, {64, 2, 1}, {128, 2, 1}};
   for (auto& st : stiles) {
     StepTile t{st[0], st[1], 0, 1, st[2]};
-    if (!staged_supported(h->p.prec, h->geo, t)) continue;
+    if (!staged_supported(h->p.prec, h->geo, t) || h->phys.rounding != LBM_ROUND_NEAREST) continue;
     t.rows = rows_for_wave(h->geo, t, sms * staged_blocks_per_sm(h->p.prec, t));
     cands.push_back(t);
   }

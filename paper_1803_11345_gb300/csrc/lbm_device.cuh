@@ -104,7 +104,7 @@ template <class T, bool DEV> struct PopDense {
   // 16-bit closures only).
   template <class PL>
   __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], C /*drho*/,
-                                                    C /*phi*/) {
+                                                    C /*phi*/, uint32_t /*sr_key: 16-bit storage only*/ = 0) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       stf(b, pl, i, idx, f[i]);
@@ -139,6 +139,51 @@ template <> struct Cvt<__half> {
 template <> struct Cvt<__nv_bfloat16> {
   __device__ __forceinline__ static float to(__nv_bfloat16 h) { return __bfloat162float(h); }
   __device__ __forceinline__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Stochastic rounding of the 16-bit storage (an option; round-to-nearest is the default).
+// Rounding to nearest leaves an error that is a fixed function of the value, so on a smooth
+// field the errors of neighbouring nodes are alike and add up (in a slow shear the stored
+// deviations quantise the viscous stress); rounding up with probability equal to the fraction of
+// a unit that is dropped makes every stored value unbiased, and the errors average out.
+//
+// Random bits: a counter-based stream per node and step.  A 32-bit key for the step (host) and
+// the node index go through the MurmurHash3 32-bit finaliser (A. Appleby); a Weyl sequence (adding
+// the 32-bit golden-ratio constant) then gives one word per moving direction i = 1..8, drawn in
+// order: its low half rounds f_i, its high half g_i.  Each field is uniform over nodes and steps,
+// which is what makes every rounding unbiased.
+__device__ __forceinline__ uint32_t sr_mix(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t sr_next(uint32_t x) { return x + 0x9e3779b9u; }
+// First word of node idx at the step whose key is `key` (direction 1); sr_next gives the next.
+__device__ __forceinline__ uint32_t sr_start(unsigned idx, uint32_t key) { return sr_mix(idx * 0x9e3779b9u ^ key); }
+
+// v rounded to the 16-bit type with 16 random bits r (a fraction r / 2^16 of the type's unit at
+// v): the fraction is added to |v| and the result cut toward zero, so v rounds away from zero with
+// probability equal to the dropped fraction of a unit.  FP16: the unit is 2^(e-10) for an exponent
+// e >= -14 and 2^-24 below (its subnormal range); the FMA adds exactly, up to the FP32 rounding of
+// the sum (2^-13 of a unit at most).  BF16: the 16 dropped bits of the FP32 pattern get r added.
+template <class H> struct SRound;
+template <> struct SRound<__half> {
+  __device__ __forceinline__ static __half round(float v, uint32_t r) {
+    const int ef = (int)((__float_as_uint(v) >> 23) & 0xFFu);
+    const float u = __uint_as_float((uint32_t)max(ef - 26, 87) << 23);  // unit * 2^-16
+    const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;    // r as a float, exactly
+    return __float2half_rz(fmaf(copysignf(u, v), rf, v));
+  }
+};
+template <> struct SRound<__nv_bfloat16> {
+  __device__ __forceinline__ static __nv_bfloat16 round(float v, uint32_t r) {
+    const uint32_t b = __float_as_uint(v);
+    if (((b >> 23) & 0xFFu) == 0xFFu) return __float2bfloat16_rn(v);
+    return __float2bfloat16_rz(__uint_as_float((b + r) & 0xFFFF0000u));
+  }
 };
 
 template <class H> struct PopHalf {
@@ -186,18 +231,27 @@ template <class H> struct PopHalf {
   // to the node's rho and phi (the collision conserves both; the caller passes them): 16-bit
   // rounding then redistributes among directions but does not create or destroy mass or order
   // parameter.  In deviations (sum_i w_i = 1): d_0 = (rho - 1) - sum_{i>0} d_i.
+  // sr_key: 0 rounds to nearest; otherwise the step's key for stochastic rounding.
   template <class PL>
   __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], float drho,
-                                                    float phi) {
+                                                    float phi, uint32_t sr_key = 0) {
     float sf = 0.0f, sg = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-      const H hf = Cvt<H>::from(f[i]);
-      const H hg = Cvt<H>::from(g[i]);
+    auto put = [&](int i, H hf, H hg) {
       *half(b, pl, i - 1, idx) = hf;
       *half(b, pl, 7 + i, idx) = hg;
       sf += Cvt<H>::to(hf);
       sg += Cvt<H>::to(hg);
+    };
+    if (!sr_key) {  // one uniform branch: the round-to-nearest loop carries no stochastic code
+#pragma unroll
+      for (int i = 1; i < 9; ++i) put(i, Cvt<H>::from(f[i]), Cvt<H>::from(g[i]));
+    } else {
+      uint32_t w = sr_start((unsigned)idx, sr_key);
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        if (i > 1) w = sr_next(w);
+        put(i, SRound<H>::round(f[i], w & 0xFFFFu), SRound<H>::round(g[i], w >> 16));
+      }
     }
     *rest(b, pl, 0, idx) = rest_f(drho, sf);
     *rest(b, pl, 1, idx) = phi - sg;
@@ -249,6 +303,7 @@ template <class C> struct Phys {
   int bgk;                // 0 central moments (paper), 1 BGK baseline
   int force_mode;         // 0 uniform, 1 on phase l only: F (1 + phi)/2
   int forced;             // force_x or force_y non-zero
+  uint32_t sr_key;        // 16-bit storage: 0 rounds to nearest, else this step's stochastic-rounding key
 };
 
 // Physics in the kernel's arithmetic type from the validated host parameters.
@@ -274,6 +329,7 @@ template <class C> inline Phys<C> make_phys(const HostPhys& h) {
   p.bgk = h.bgk;
   p.force_mode = h.force_mode;
   p.forced = h.force_x != 0.0 || h.force_y != 0.0;
+  p.sr_key = h.sr_key;
   return p;
 }
 

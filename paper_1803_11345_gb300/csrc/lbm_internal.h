@@ -18,6 +18,9 @@ struct HostPhys {
   double omega_l, omega_g, tau_l, tau_g, omega3, omega_phi, gamma, a, Gamma, u_top, u_bottom;
   double wet_bottom, wet_top, force_x, force_y;
   int visc, k8_printed, bgk, force_mode;
+  int rounding = 0;      // lbm_rounding
+  uint32_t seed = 0;     // stochastic-rounding seed
+  uint32_t sr_key = 0;   // per launch: 0 rounds to nearest, else the step's stochastic-rounding key
 };
 
 // Tile of the fused step: BX columns x BY rows of threads, `rows` lattice rows per CTA.

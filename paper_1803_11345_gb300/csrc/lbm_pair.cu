@@ -70,6 +70,7 @@ __device__ __forceinline__ void st_word(char* __restrict__ b, unsigned byte_off,
 // Two floats rounded to the storage type and packed (low half = first), and back.
 template <int PREC> struct Pack;
 template <> struct Pack<2> {
+  using H = __half;
   __device__ __forceinline__ static uint32_t pack(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -79,6 +80,7 @@ template <> struct Pack<2> {
   }
 };
 template <> struct Pack<3> {
+  using H = __nv_bfloat16;
   __device__ __forceinline__ static uint32_t pack(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -272,14 +274,34 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       // from the rounded values in direction order.
       const unsigned e = (unsigned)(r * pitch + x);
       F2 sf(0.0f), sg(0.0f);
-#pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        const uint32_t wf = Pack<PREC>::pack(f[i].v.x, f[i].v.y);
-        const uint32_t wg = Pack<PREC>::pack(g[i].v.x, g[i].v.y);
+      // Stochastic rounding (optional): each node draws the same stream as in the one-node kernel.
+      auto put = [&](int i, uint32_t wf, uint32_t wg) {
         st_word(dst, ((unsigned)(i - 1) * pl.n + e) * 2u, wf);
         st_word(dst, ((unsigned)(7 + i) * pl.n + e) * 2u, wg);
         sf += F2(Pack<PREC>::unpack(wf));
         sg += F2(Pack<PREC>::unpack(wg));
+      };
+      const uint32_t key = ph.sr_key;
+      if (!key) {  // one uniform branch: the round-to-nearest loop carries no stochastic code
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          put(i, Pack<PREC>::pack(f[i].v.x, f[i].v.y), Pack<PREC>::pack(g[i].v.x, g[i].v.y));
+      } else {
+        using H = typename Pack<PREC>::H;
+        auto bits2 = [](H lo, H hi) -> uint32_t {
+          return (uint32_t)*reinterpret_cast<const unsigned short*>(&lo) |
+                 ((uint32_t)*reinterpret_cast<const unsigned short*>(&hi) << 16);
+        };
+        uint32_t ra = sr_start(e, key), rb = sr_start(e + 1u, key);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          if (i > 1) {
+            ra = sr_next(ra);
+            rb = sr_next(rb);
+          }
+          put(i, bits2(SRound<H>::round(f[i].v.x, ra & 0xFFFFu), SRound<H>::round(f[i].v.y, rb & 0xFFFFu)),
+              bits2(SRound<H>::round(g[i].v.x, ra >> 16), SRound<H>::round(g[i].v.y, rb >> 16)));
+        }
       }
       const F2 f0 = drho - sf, g0 = phi - sg;
       *reinterpret_cast<float2*>(dst + ((unsigned)P::kRestFirst * pl.n + e) * 4u) = f0.v;

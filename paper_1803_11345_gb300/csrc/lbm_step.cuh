@@ -160,7 +160,7 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
       unpack<PREC, true>(gA, gAd, g);
       const C drho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
       if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, 1);
-      P::store_node(dst, pl, r * geo.pitch + x, f, g, drho, phi);
+      P::store_node(dst, pl, r * geo.pitch + x, f, g, drho, phi, ph.sr_key);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {

@@ -23,6 +23,7 @@ LBM_OMEGA_LINEAR, LBM_TAU_LINEAR = 0, 1
 LBM_K8_PROJECTED, LBM_K8_PRINTED = 0, 1
 LBM_COLLIDE_CM, LBM_COLLIDE_BGK = 0, 1
 LBM_FORCE_UNIFORM, LBM_FORCE_PHASE_L = 0, 1
+LBM_ROUND_NEAREST, LBM_ROUND_STOCHASTIC = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_STAGED, LBM_KERNEL_GENERIC_WIDE, LBM_KERNEL_PAIR = 0, 1, 2, 3, 4
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
@@ -41,6 +42,7 @@ class lbm_params(ctypes.Structure):
         ("prec", ctypes.c_int), ("collision", ctypes.c_int),
         ("wet_bottom", ctypes.c_double), ("wet_top", ctypes.c_double),
         ("force_x", ctypes.c_double), ("force_y", ctypes.c_double), ("force_mode", ctypes.c_int),
+        ("rounding", ctypes.c_int), ("seed", ctypes.c_uint),
     ]
 
 

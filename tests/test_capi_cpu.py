@@ -49,13 +49,15 @@ def test_defaults_follow_the_paper(lbm):
     assert (p.M, p.Gamma, p.gamma, p.a) == (0.1, 1.0, 0.04, 0.04)
     assert p.tau_l == pytest.approx(0.8) and p.omega3 == 1.0
     assert p.prec == lbm.LBM_FP32 and p.collision == lbm.LBM_COLLIDE_CM
+    assert p.rounding == lbm.LBM_ROUND_NEAREST and p.seed == 0
 
 
 @pytest.mark.parametrize("bad", [
     dict(nx=2), dict(ny=0), dict(tau_l=0.5), dict(tau_g=0.2), dict(M=0.0), dict(Gamma=-1.0),
     dict(gamma=-0.1), dict(omega3=2.0), dict(prec=7), dict(bc=3), dict(visc=5), dict(k8_form=2),
     dict(collision=9), dict(u_top=float("nan")), dict(nx=70000, ny=70000), dict(force_mode=2),
-    dict(force_x=float("inf")), dict(wet_bottom=0.1), dict(bc=1, wet_top=float("nan"))])
+    dict(force_x=float("inf")), dict(wet_bottom=0.1), dict(bc=1, wet_top=float("nan")), dict(rounding=2),
+    dict(rounding=1), dict(rounding=1, prec=0)])
 def test_invalid_parameters_rejected(lbm, bad):
     kw = dict(nx=16, ny=16)
     kw.update(bad)
@@ -97,3 +99,15 @@ def test_wall_gradient_matches_the_oracle(lbm, orc):
             assert math.isclose(lbm.lbm_wall_gradient(math.pi - th, 0.04, 0.04 * ratio), -want, rel_tol=1e-14,
                                 abs_tol=1e-16)
     assert math.isnan(lbm.lbm_wall_gradient(1.0, 0.04, 0.0))
+
+
+def test_stochastic_rounding_only_for_16bit_storage_and_single_lattices(lbm):
+    """Stochastic rounding is accepted for FP16S / BF16S storage and refused for FP32 / FP64 (no
+    16-bit rounding to randomise) and in batches, whose captured graph launches cannot carry a new
+    random key every step."""
+    for prec in (lbm.LBM_FP16S, lbm.LBM_BF16S):
+        assert lbm.lbm_state_bytes(lbm.lbm_default_params(nx=16, ny=16, prec=prec, rounding=1, seed=7)) > 0
+    p = lbm.lbm_default_params(nx=16, ny=16, prec=lbm.LBM_FP16S, rounding=1)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_batch_state_bytes([p, p])
+    assert ei.value.status == lbm.LBM_ERR_PARAM

@@ -153,8 +153,74 @@ def test_taylor_deformation_across_precisions(lbm):
         assert st == lbm.LBM_OK and not any(flags), (prec, st, flags)
         d[prec] = np.array([deformation(bat.fields(m)[3]) for m in range(len(cas))])
         bat.close()
+    # 16-bit storage with stochastic rounding (single lattices: batches round to nearest)
+    for prec in ("fp16s", "bf16s"):
+        vals = []
+        for phi0, kw in members:
+            lat = lbm.Lattice(phi0, prec=prec, rounding=1, seed=1, **kw)
+            lat.step(150000)
+            vals.append(deformation(lat.fields()[3]))
+            lat.close()
+        d[prec + "+sr"] = np.array(vals)
     print("Taylor deformation by Ca", cas, {k: v.tolist() for k, v in d.items()})
     slope = np.polyfit(np.array(cas), d["fp64"], 1)[0]
     assert abs(slope / gold["slope_theory"] - 1) < 0.05, (slope, d["fp64"])
-    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12)):
+    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12), ("fp16s+sr", 0.02), ("bf16s+sr", 0.10)):
         assert np.all(np.abs(d[prec] / d["fp64"] - 1) <= bound), (prec, d[prec], d["fp64"])
+
+
+# -------------------------------------------------------------------------------------------
+# Stochastic rounding of the 16-bit storage (lbm_params.rounding = LBM_ROUND_STOCHASTIC).
+
+W1 = {1: 1.0 / 9.0, 5: 1.0 / 36.0}  # weights of one axis and one diagonal direction
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+@pytest.mark.parametrize("kernel", ["one-node", "paired"])
+def test_stochastic_rounding_is_unbiased(lbm, prec, kernel):
+    """A uniform lattice at rest (phi = 0, rho = 1 + delta, tau = 1 in both phases, so that one
+    collision returns the equilibrium exactly): after one step every node stores the same FP32
+    value d_i = w_i (rho - 1).  Rounded to nearest, all nodes hold one 16-bit value; rounded
+    stochastically they hold the two neighbouring 16-bit values in the proportion that makes the
+    mean equal d_i: within 1% of the 16-bit unit over 65536 nodes (the standard error of that mean
+    is at most 0.2% of the unit).  The diagonal value (w = 1/36, ~2.8e-5) lies in FP16's subnormal
+    range, the axis value (~1.1e-4) in its normal range."""
+    n, delta = 256, 1.0e-3 * math.pi
+    phi0 = np.zeros((n, n))
+    rho0 = np.full((n, n), 1.0 + delta)
+    for rounding in (0, 1):
+        lat = lbm.Lattice(phi0, None, None, rho0, prec=prec, tau_l=1.0, tau_g=1.0, rounding=rounding, seed=11)
+        if kernel == "paired":
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)
+            assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR
+        f0, _ = lat.populations()
+        drho = float(f0[:, 0, 0].sum() - 1.0)  # the stored state's rho - 1 (identical at every node)
+        lat.step(1)
+        f1, _ = lat.populations()
+        lat.close()
+        for i, w in W1.items():
+            d = f1[i] - w  # exact in FP64: the stored value is a 16-bit number
+            levels = np.unique(d)
+            v = w * drho
+            if rounding == 0:
+                assert len(levels) == 1, (i, levels)
+                continue
+            assert len(levels) == 2, (prec, kernel, i, levels)
+            unit = levels[1] - levels[0]
+            assert levels[0] < v < levels[1]
+            assert abs(d.mean() - v) <= 0.01 * unit, (prec, kernel, i, d.mean(), v, unit)
+
+
+def test_stochastic_rounding_is_reproducible(lbm):
+    """The random bits are a counter-based stream of (seed, step, node): the same seed gives the
+    same state bit for bit, another seed another state."""
+    phi0 = W.spinodal(128, 64, seed=5)
+    kw = dict(prec="fp16s", tau_l=0.8, tau_g=0.53, rounding=1)
+    runs = []
+    for seed in (3, 3, 4):
+        lat = lbm.Lattice(phi0, seed=seed, **kw)
+        lat.step(20)
+        runs.append(lat.populations())
+        lat.close()
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0], runs[1]))
+    assert not np.array_equal(runs[0][0], runs[2][0])

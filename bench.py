@@ -259,9 +259,10 @@ def config_dict(args):
 # GPU leg.
 
 def storage_forms(lbm, phi0, params, stream, ms_fp32, steps=500, phi_steps=1000):
-    """The 16-bit storage forms on the same workload and GPU: time per step against the FP32 step
-    just timed, and phi after `phi_steps` steps against an FP32 run from the same state (the error
-    against the FP64 oracle is stated by the tests: 2e-3 FP16, 2e-2 BF16 over 1000 steps)."""
+    """The 16-bit storage forms on the same workload and GPU, rounded to nearest and stochastically:
+    time per step against the FP32 step just timed, and phi after `phi_steps` steps against an FP32
+    run from the same state (the error against the FP64 oracle is stated by the tests: 2e-3 FP16,
+    2e-2 BF16 over 1000 steps; the deformation statistic is stated there too)."""
     import numpy as np
     import torch
     ref = lbm.Lattice(phi0, stream=stream, **params)
@@ -269,8 +270,12 @@ def storage_forms(lbm, phi0, params, stream, ms_fp32, steps=500, phi_steps=1000)
     phi_ref = ref.fields()[3]
     ref.close()
     out = {}
-    for prec in ("fp16s", "bf16s"):
+    # each 16-bit form rounded to nearest (the default) and stochastically (lbm_params.rounding)
+    for form in ("fp16s", "bf16s", "fp16s+sr", "bf16s+sr"):
+        prec = form.split("+")[0]
         kw = dict(params, prec=lbm.PRECISIONS[prec])
+        if form.endswith("+sr"):
+            kw.update(rounding=lbm.LBM_ROUND_STOCHASTIC, seed=1)
         lat = lbm.Lattice(phi0, stream=stream, **kw)
         lat.step(20)
         torch.cuda.synchronize()
@@ -285,7 +290,7 @@ def storage_forms(lbm, phi0, params, stream, ms_fp32, steps=500, phi_steps=1000)
         kernel = {lbm.LBM_KERNEL_PAIR: "k_step_pair (two nodes per thread)"}.get(lat.kernel[0], "k_step")
         lat.close()
         nodes = phi0.size
-        out[prec] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "speedup_vs_fp32": ms_fp32 / ms,
+        out[form] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "speedup_vs_fp32": ms_fp32 / ms,
                      "hbm_frac": BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9 / measured_peaks()[0],
                      "phi_vs_fp32_after_steps": phi_steps, "phi_max_abs_diff": float(d.max()),
                      "phi_rms_diff": float(np.sqrt((d * d).mean())), "kernel": kernel}

@@ -15,7 +15,9 @@ Measured here (the tests print them):
   BF16 -28% to +54%.  The 16-bit forms do not resolve this flow: the wall speed is 2.2e-3, the
   shear changes a moving population's deviation by ~7e-6 per lattice row, and the stored
   deviations (~7e-4) have a rounding unit of 4.8e-7 in FP16 (15 units per row) and 3.8e-6 in
-  BF16 (under 2): the viscous stress the flow runs on is quantised.
+  BF16 (under 2): the viscous stress the flow runs on is quantised.  With stochastic rounding
+  (unbiased rounding of every stored value) the deformation comes within 0.27% (FP16) and 0.45%
+  (BF16) of FP64.
 """
 import json
 import math
@@ -133,7 +135,8 @@ def test_taylor_deformation_across_precisions(lbm):
     0.25, 150000 steps, one batch per precision): the steady deformation in FP32 storage is within
     1% of the FP64 run for every Ca, which itself follows 35/32 Ca within 5%.  FP16 states 12%
     (measured 2.5% to 9.2%); BF16 is printed only (it runs stably, checked above, but does not
-    resolve the shear; see the module notes)."""
+    resolve the shear; see the module notes).  With stochastic rounding both 16-bit forms are
+    within 1% (measured 0.27% FP16, 0.45% BF16); the test states 1% and 2%."""
     gold = json.load(open(GOLDEN))["taylor"]
     n, R, nu, Re = 200, 30, 0.2, 0.1
     H = n / 2
@@ -165,7 +168,7 @@ def test_taylor_deformation_across_precisions(lbm):
     print("Taylor deformation by Ca", cas, {k: v.tolist() for k, v in d.items()})
     slope = np.polyfit(np.array(cas), d["fp64"], 1)[0]
     assert abs(slope / gold["slope_theory"] - 1) < 0.05, (slope, d["fp64"])
-    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12), ("fp16s+sr", 0.02), ("bf16s+sr", 0.10)):
+    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12), ("fp16s+sr", 0.01), ("bf16s+sr", 0.02)):
         assert np.all(np.abs(d[prec] / d["fp64"] - 1) <= bound), (prec, d[prec], d["fp64"])
 
 

@@ -171,18 +171,20 @@ __device__ __forceinline__ uint32_t sr_start(unsigned idx, uint32_t key) { retur
 // the sum (2^-13 of a unit at most).  BF16: the 16 dropped bits of the FP32 pattern get r added.
 template <class H> struct SRound;
 template <> struct SRound<__half> {
-  __device__ __forceinline__ static __half round(float v, uint32_t r) {
+  // v plus the random fraction of its FP16 unit, away from zero; converting it toward zero rounds.
+  __device__ __forceinline__ static float pre(float v, uint32_t r) {
     const int ef = (int)((__float_as_uint(v) >> 23) & 0xFFu);
     const float u = __uint_as_float((uint32_t)max(ef - 26, 87) << 23);  // unit * 2^-16
     const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;    // r as a float, exactly
-    return __float2half_rz(fmaf(copysignf(u, v), rf, v));
+    return fmaf(copysignf(u, v), rf, v);
   }
+  __device__ __forceinline__ static __half round(float v, uint32_t r) { return __float2half_rz(pre(v, r)); }
 };
 template <> struct SRound<__nv_bfloat16> {
+  // The FP32 pattern with r added to its 16 low bits; its high half is the rounded BF16 value.
+  __device__ __forceinline__ static uint32_t bits(float v, uint32_t r) { return __float_as_uint(v) + r; }
   __device__ __forceinline__ static __nv_bfloat16 round(float v, uint32_t r) {
-    const uint32_t b = __float_as_uint(v);
-    if (((b >> 23) & 0xFFu) == 0xFFu) return __float2bfloat16_rn(v);
-    return __float2bfloat16_rz(__uint_as_float((b + r) & 0xFFFF0000u));
+    return __ushort_as_bfloat16((unsigned short)(bits(v, r) >> 16));
   }
 };
 

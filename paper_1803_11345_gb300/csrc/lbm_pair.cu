@@ -60,6 +60,13 @@ __device__ __forceinline__ void finish(const RawPairLoad& l, RawPair& o) {
   o.r0b = l.r0b;
 }
 
+// Two floats converted to FP16 toward zero and packed (low half = lo).
+__device__ __forceinline__ uint32_t cvt_rz_pair(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 __device__ __forceinline__ uint32_t ld_word(const char* __restrict__ b, unsigned byte_off) {
   return __ldg(reinterpret_cast<const unsigned int*>(b + byte_off));
 }
@@ -288,10 +295,6 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
           put(i, Pack<PREC>::pack(f[i].v.x, f[i].v.y), Pack<PREC>::pack(g[i].v.x, g[i].v.y));
       } else {
         using H = typename Pack<PREC>::H;
-        auto bits2 = [](H lo, H hi) -> uint32_t {
-          return (uint32_t)*reinterpret_cast<const unsigned short*>(&lo) |
-                 ((uint32_t)*reinterpret_cast<const unsigned short*>(&hi) << 16);
-        };
         uint32_t ra = sr_start(e, key), rb = sr_start(e + 1u, key);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -299,8 +302,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
             ra = sr_next(ra);
             rb = sr_next(rb);
           }
-          put(i, bits2(SRound<H>::round(f[i].v.x, ra & 0xFFFFu), SRound<H>::round(f[i].v.y, rb & 0xFFFFu)),
-              bits2(SRound<H>::round(g[i].v.x, ra >> 16), SRound<H>::round(g[i].v.y, rb >> 16)));
+          if constexpr (PREC == 3) {  // BF16: the two high halves of the rounded FP32 patterns
+            put(i,
+                __byte_perm(SRound<H>::bits(f[i].v.x, ra & 0xFFFFu), SRound<H>::bits(f[i].v.y, rb & 0xFFFFu), 0x7632),
+                __byte_perm(SRound<H>::bits(g[i].v.x, ra >> 16), SRound<H>::bits(g[i].v.y, rb >> 16), 0x7632));
+          } else {  // FP16: both nodes converted toward zero and packed by one instruction
+            put(i, cvt_rz_pair(SRound<H>::pre(f[i].v.x, ra & 0xFFFFu), SRound<H>::pre(f[i].v.y, rb & 0xFFFFu)),
+                cvt_rz_pair(SRound<H>::pre(g[i].v.x, ra >> 16), SRound<H>::pre(g[i].v.y, rb >> 16)));
+          }
         }
       }
       const F2 f0 = drho - sf, g0 = phi - sg;

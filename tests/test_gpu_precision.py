@@ -227,3 +227,29 @@ def test_stochastic_rounding_is_reproducible(lbm):
         lat.close()
     assert all(np.array_equal(a, b) for a, b in zip(runs[0], runs[1]))
     assert not np.array_equal(runs[0][0], runs[2][0])
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_stochastic_rounding_paired_follows_one_node(lbm, prec):
+    """Both 16-bit kernels draw the same random stream for a node, so one stochastically rounded
+    step from the same non-uniform state stores the same values, except where the two kernels'
+    FP32 results (their multiply-adds are fused at different places) straddle a rounding decision:
+    at most 1% of the moving populations, each by one 16-bit unit.  A mix-up of the pair's lanes
+    would move values by the node-to-node differences of the field instead."""
+    phi0 = W.spinodal(256, 64, seed=8)
+    out = []
+    for variant, bx in ((lbm.LBM_KERNEL_GENERIC, 256), (lbm.LBM_KERNEL_PAIR, 128)):
+        lat = lbm.Lattice(phi0, prec=prec, tau_l=0.8, tau_g=0.53, rounding=1, seed=5)
+        lat.set_kernel(variant, bx, 1)
+        lat.step(1)
+        out.append(lat.populations())
+        lat.close()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    rel = 2.0 ** -10 if prec == "fp16s" else 2.0 ** -7  # a unit relative to the stored value
+    for k in (0, 1):  # f as stored (deviations f_i - w_i), g as is
+        va, vb = out[0][k][1:], out[1][k][1:]
+        if k == 0:
+            va, vb = va - w[1:], vb - w[1:]
+        d = np.abs(va - vb)
+        assert np.mean(d > 0) <= 0.01, (k, np.mean(d > 0))
+        assert np.all(d <= rel * np.maximum(np.maximum(np.abs(va), np.abs(vb)), 2.0 ** -14) * 1.0001), (k, float(d.max()))

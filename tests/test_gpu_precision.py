@@ -229,17 +229,20 @@ def test_stochastic_rounding_is_reproducible(lbm):
     assert not np.array_equal(runs[0][0], runs[2][0])
 
 
+@pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
-def test_stochastic_rounding_paired_follows_one_node(lbm, prec):
+def test_stochastic_rounding_paired_follows_one_node(lbm, prec, bc):
     """Both 16-bit kernels draw the same random stream for a node, so one stochastically rounded
     step from the same non-uniform state stores the same values, except where the two kernels'
     FP32 results (their multiply-adds are fused at different places) straddle a rounding decision:
     at most 1% of the moving populations, each by one 16-bit unit.  A mix-up of the pair's lanes
-    would move values by the node-to-node differences of the field instead."""
+    would move values by the node-to-node differences of the field instead.  Periodic, and between
+    moving walls (the paired kernel's walled variant and its edge-row launch)."""
     phi0 = W.spinodal(256, 64, seed=8)
+    walls = dict(bc=1, u_top=0.01, u_bottom=-0.01) if bc else {}
     out = []
     for variant, bx in ((lbm.LBM_KERNEL_GENERIC, 256), (lbm.LBM_KERNEL_PAIR, 128)):
-        lat = lbm.Lattice(phi0, prec=prec, tau_l=0.8, tau_g=0.53, rounding=1, seed=5)
+        lat = lbm.Lattice(phi0, prec=prec, tau_l=0.8, tau_g=0.53, rounding=1, seed=5, **walls)
         lat.set_kernel(variant, bx, 1)
         lat.step(1)
         out.append(lat.populations())
@@ -253,3 +256,15 @@ def test_stochastic_rounding_paired_follows_one_node(lbm, prec):
         d = np.abs(va - vb)
         assert np.mean(d > 0) <= 0.01, (k, np.mean(d > 0))
         assert np.all(d <= rel * np.maximum(np.maximum(np.abs(va), np.abs(vb)), 2.0 ** -14) * 1.0001), (k, float(d.max()))
+
+
+def test_staged_kernel_refused_with_stochastic_rounding(lbm):
+    """The staged kernel stores from shared memory without the node index the rounding stream is
+    keyed on, so a lattice with stochastic rounding refuses it and lbm_autotune leaves it out."""
+    lat = lbm.Lattice(W.spinodal(128, 64, seed=2), prec="fp16s", rounding=1)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.set_kernel(lbm.LBM_KERNEL_STAGED, 64, 4)
+    assert ei.value.status == lbm.LBM_ERR_PARAM
+    lat.autotune(trial_steps=2)
+    assert lat.kernel[0] != lbm.LBM_KERNEL_STAGED
+    lat.close()

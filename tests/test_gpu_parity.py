@@ -170,12 +170,13 @@ def test_spinodal_fp32_1000_steps(lbm, orc):
     assert rel_err(rg, ro) <= 1e-5
 
 
-@pytest.mark.parametrize("prec,bound", [("fp16s", 2e-3), ("bf16s", 2e-2)])
+@pytest.mark.parametrize("prec,bound", [("fp16s", 2e-3), ("bf16s", 5e-3)])
 def test_sheared_droplet_16bit_storage(lbm, orc, prec, bound):
     """16-bit deviation storage against the FP64 oracle over 1000 steps of a sheared droplet.
-    FP16 (11-bit significand) keeps phi within 2e-3.  BF16 (8-bit significand) rounds the f
-    deviations (~3e-3, mostly 3 w_i c.u) to ~1e-5, which biases the velocity and shifts the
-    interface by ~1e-2 lattice units over 1000 steps; its bound is 2e-2 (|grad phi| <= 0.7)."""
+    FP16 (11-bit significand) keeps phi within 2e-3 (measured 1.0e-3).  BF16 (8-bit significand)
+    rounds the f deviations (~3e-3, mostly 3 w_i c.u) to ~1e-5 and shifts the interface by a few
+    1e-3 lattice units over 1000 steps: measured 3.9e-3 (1.1e-2 while the collision added w_i back
+    before computing), bound 5e-3 (|grad phi| <= 0.7)."""
     phi0 = W.droplet(128, 64, 16, gamma=0.04, a=0.04)
     kw = dict(tau_l=orc.tau_from_nu(0.2), tau_g=orc.tau_from_nu(0.02), bc=lbm.LBM_WALLS_Y,
               u_top=0.01, u_bottom=-0.01)

@@ -183,9 +183,22 @@ LBM_API int lbm_get_populations(lbm_lattice* h, double* f, double* g);
  * checkpoint.  16-bit storage rounds them.  Synchronises.  LBM_ERR_PARAM on NULL input. */
 LBM_API int lbm_set_populations(lbm_lattice* h, const double* f, const double* g);
 
-/* Synchronise and report whether any step since the last check produced a non-finite rho or
- * phi (LBM_ERR_NONFINITE) or a CUDA error occurred (LBM_ERR_CUDA); clears the flag. */
+/* Synchronise and report whether any step since the last check had a bounded device-side wait
+ * give up (LBM_ERR_TIMEOUT, reported first), produced a non-finite rho or phi
+ * (LBM_ERR_NONFINITE), or a CUDA error occurred (LBM_ERR_CUDA); clears the flags.  After
+ * LBM_ERR_TIMEOUT the steps enqueued since the last check may be incomplete: the handle stays
+ * usable, but its state is undefined until lbm_set_populations restores one (a checkpoint). */
 LBM_API int lbm_check(lbm_lattice* h);
+
+/* Probes a bulk-copy wait of the staged kernel (LBM_KERNEL_STAGED) makes before it gives up.
+ * probes < 0 restores the default, 2^22 probes, each a short hardware-timed suspend: far beyond
+ * any legitimate copy latency and well under a second.  probes = 0 makes every wait of the
+ * kernel's main loop give up at once; it exists to exercise the timeout path.  A wait that gives
+ * up makes its CTA stop stepping: it sets the lattice's timeout flag, waits (always with the
+ * default limit) for the copies it has in flight, and returns, so the GPU stays usable and the
+ * next lbm_check reports LBM_ERR_TIMEOUT.  Affects later lbm_step calls only; the other kernels
+ * have no such waits.  Errors: LBM_ERR_PARAM (h NULL). */
+LBM_API int lbm_set_wait_limit(lbm_lattice* h, int probes);
 
 /* Fused-step kernel choice.  AUTO: the fastest measured on GB300 — PAIR for 16-bit storage on
  * lattices of 4 M nodes or more where it can serve them, else GENERIC, each with its default tile
@@ -299,8 +312,9 @@ LBM_API void lbm_batch_free(lbm_batch* b);
  * frees device memory.  All calls share the array and it keeps the last call's contents; every
  * call overwrites what it reads, so nothing needs clearing, but calls that overlap on the GPU
  * (other streams, other host threads) race on it.  The first call on each device looks up the
- * array's device address with that device current; make that first call before any stream
- * capture.
+ * array's device address with that device current and keeps it for the process; make that first
+ * call before any stream capture.  A device reset (cudaDeviceReset) after that call is not
+ * supported: the kept address would be stale.
  * Errors: LBM_ERR_PARAM (NULL pointers, bad sizes or precision, misaligned state), LBM_ERR_CUDA;
  * the message is readable with lbm_last_error(NULL) on the calling thread. */
 LBM_API int lbm_totals_noalloc(const void* state, int nx, int ny, int prec, double* totals, void* stream);

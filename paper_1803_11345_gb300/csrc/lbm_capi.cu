@@ -333,9 +333,20 @@ int lbm_check(lbm_lattice* h) {
   if (flag) {
     cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
     cudaStreamSynchronize(h->stream);
+    if (flag & kFlagTimeout) {
+      set_err(h->err, "a bounded wait of the staged kernel gave up before time step %lld; the state is "
+                      "incomplete until lbm_set_populations restores one", h->t);
+      return LBM_ERR_TIMEOUT;
+    }
     set_err(h->err, "non-finite rho or phi produced before time step %lld", h->t);
     return LBM_ERR_NONFINITE;
   }
+  return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_lattice* h, int probes) {
+  if (!h) return LBM_ERR_PARAM;
+  h->phys.wait_probes = probes < 0 ? -1 : probes;
   return LBM_OK;
 }
 

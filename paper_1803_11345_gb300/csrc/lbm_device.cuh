@@ -111,6 +111,11 @@ template <class T, bool DEV> struct PopDense {
       stg(b, pl, i, idx, g[i]);
     }
   }
+  // The moving-wall term of a bounced link, and the closures' inputs: as computed (the 16-bit
+  // policies put them on a grid).
+  __device__ __forceinline__ static C wall_term(C t, bool /*is_g*/) { return t; }
+  __device__ __forceinline__ static C grid_f(C v) { return v; }
+  __device__ __forceinline__ static C grid_g(C v) { return v; }
   // Raw access: the stored bits, decoded only where used (keeps loads in flight).
   using R = T;
   template <class PL> __device__ __forceinline__ static R rawf(const char* b, PL pl, int i, int idx) {
@@ -164,25 +169,62 @@ __device__ __forceinline__ uint32_t sr_next(uint32_t x) { return x + 0x9e3779b9u
 // First word of node idx at the step whose key is `key` (direction 1); sr_next gives the next.
 __device__ __forceinline__ uint32_t sr_start(unsigned idx, uint32_t key) { return sr_mix(idx * 0x9e3779b9u ^ key); }
 
+// Exact conservation under 16-bit storage.  The collision conserves rho and phi, and the rest
+// populations are stored (FP32) as closures of the rounded moving ones, so a node's stored values
+// sum to its rho and phi -- but only as exactly as FP32 forms those sums.  They are exact when
+// every value involved lies on one fixed binary grid and no partial sum leaves the range in which
+// FP32 holds that grid exactly: f deviations on multiples of 2^-24 with partial sums below 1 in
+// magnitude, g values on multiples of 2^-23 with partial sums below 2 (|phi| stays near 1).  Every
+// FP16 value is a multiple of 2^-24 (its smallest subnormal), and every FP16 or BF16 value of
+// magnitude 2^-13 (FP16) / 2^-16 (BF16) or more is a multiple of 2^-23; values below that are first
+// put on the grid, by an addition and a subtraction of a constant whose unit in the last place is
+// the grid step (the sum is rounded at that step, the subtraction is exact), or by the same
+// addition rounded toward zero for stochastic rounding; that holds while the value is below 1/4
+// (f) or 1/2 (g) in magnitude, as every moving population and moving-wall term of a flow the
+// scheme resolves is.  Values of order one (the rest populations of an initial or restored state)
+// are scaled, rounded to an integer and scaled back instead.  Stored values and the moving-wall
+// terms then sit on the grid, every sum of the step is exact, and the FP64 totals of
+// lbm_conservation (exact sums of grid values) stay the same, bit for bit, from step to step.
+constexpr float kGridF = 0.75f;  // unit in the last place 2^-24: the f grid (for |v| < 1/4)
+constexpr float kGridG = 1.5f;   // unit in the last place 2^-23: the g grid (for |v| < 1/2)
+__device__ __forceinline__ float grid_snap(float v, float k) { return __fsub_rn(__fadd_rn(v, k), k); }
+// v rounded to the nearest multiple of 2^-S for any |v| < 2^(24 - S) (the scalings are exact).
+template <int S> __device__ __forceinline__ float grid_round(float v) {
+  constexpr float up = (float)(1u << S), down = 1.0f / (float)(1u << S);
+  return rintf(v * up) * down;
+}
+// |v| cut toward zero onto the grid of step 2^q, given k = 2^(q + 23) (0.5: the f grid, 1: the g
+// grid; exact for |v| < k), sign kept.
+__device__ __forceinline__ float grid_trunc(float v, float k) { return copysignf(__fsub_rn(__fadd_rz(fabsf(v), k), k), v); }
+
 // v rounded to the 16-bit type with 16 random bits r (a fraction r / 2^16 of the type's unit at
 // v): the fraction is added to |v| and the result cut toward zero, so v rounds away from zero with
-// probability equal to the dropped fraction of a unit.  FP16: the unit is 2^(e-10) for an exponent
-// e >= -14 and 2^-24 below (its subnormal range); the FMA adds exactly, up to the FP32 rounding of
-// the sum (2^-13 of a unit at most).  BF16: the 16 dropped bits of the FP32 pattern get r added.
-template <class H> struct SRound;
-template <> struct SRound<__half> {
-  // v plus the random fraction of its FP16 unit, away from zero; converting it toward zero rounds.
+// probability equal to the dropped fraction of a unit.  The unit is 2^(e-10) (FP16) or 2^(e-7)
+// (BF16) for an exponent e, but never below the grid step 2^Q of the set (Q = -24 for f, -23 for
+// g, see above), which for small values is also the step of the cut; the FMA adds exactly up to
+// the FP32 rounding of the sum (2^-13 of a unit at most).
+template <class H, int Q> struct SRound;
+template <int Q> struct SRound<__half, Q> {
   __device__ __forceinline__ static float pre(float v, uint32_t r) {
     const int ef = (int)((__float_as_uint(v) >> 23) & 0xFFu);
-    const float u = __uint_as_float((uint32_t)max(ef - 26, 87) << 23);  // unit * 2^-16
-    const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;    // r as a float, exactly
-    return fmaf(copysignf(u, v), rf, v);
+    const float u = __uint_as_float((uint32_t)max(ef - 26, Q + 111) << 23);  // unit * 2^-16
+    const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;          // r as a float, exactly
+    const float p = fmaf(copysignf(u, v), rf, v);
+    // FP16's subnormal step 2^-24 is the f grid; g's coarser grid needs its own cut first (the
+    // conversion toward zero then cuts again on FP16's grid, which contains it).
+    return Q == -24 ? p : grid_trunc(p, 1.0f);
   }
   __device__ __forceinline__ static __half round(float v, uint32_t r) { return __float2half_rz(pre(v, r)); }
 };
-template <> struct SRound<__nv_bfloat16> {
-  // The FP32 pattern with r added to its 16 low bits; its high half is the rounded BF16 value.
-  __device__ __forceinline__ static uint32_t bits(float v, uint32_t r) { return __float_as_uint(v) + r; }
+template <int Q> struct SRound<__nv_bfloat16, Q> {
+  // The pre-rounded value cut onto the grid; its high half is then the value cut toward zero.
+  __device__ __forceinline__ static uint32_t bits(float v, uint32_t r) {
+    const int ef = (int)((__float_as_uint(v) >> 23) & 0xFFu);
+    const float u = __uint_as_float((uint32_t)max(ef - 23, Q + 111) << 23);  // unit * 2^-16
+    const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;
+    const float p = fmaf(copysignf(u, v), rf, v);
+    return __float_as_uint(grid_trunc(p, Q == -24 ? 0.5f : 1.0f));
+  }
   __device__ __forceinline__ static __nv_bfloat16 round(float v, uint32_t r) {
     return __ushort_as_bfloat16((unsigned short)(bits(v, r) >> 16));
   }
@@ -190,9 +232,25 @@ template <> struct SRound<__nv_bfloat16> {
 
 template <class H> struct PopHalf {
   using C = float;
+  static constexpr bool kFP16 = std::is_same<H, __half>::value;
   static constexpr size_t kBytesPerElem = 16 * sizeof(H) + 2 * sizeof(float);
   // The two FP32 rest planes follow the 16 half planes: 16 * sizeof(H) / 4 float planes in.
   static constexpr int kRestFirst = 16 * (int)sizeof(H) / (int)sizeof(float);
+  // Values onto the grids of the f and g sets (exact conservation, see above): grid_f / grid_g
+  // for any value the state holds (|v| < 1 for f deviations, < 2 for g), the cheaper snaps for
+  // the small moving populations and wall terms of the step.
+  __device__ __forceinline__ static float grid_f(float v) { return grid_round<24>(v); }
+  __device__ __forceinline__ static float grid_g(float v) { return grid_round<23>(v); }
+  __device__ __forceinline__ static float snap_f(float v) { return grid_snap(v, kGridF); }
+  __device__ __forceinline__ static float snap_g(float v) { return grid_snap(v, kGridG); }
+  // Moving populations rounded to nearest, on the grid: FP16 f needs no snap (FP16 values are
+  // multiples of 2^-24); the others are snapped first (a second rounding of the snapped value can
+  // differ from a single rounding only when the snap lands exactly halfway between two 16-bit
+  // values).
+  __device__ __forceinline__ static H encf(float d) { return Cvt<H>::from(kFP16 ? d : snap_f(d)); }
+  __device__ __forceinline__ static H encg(float v) { return Cvt<H>::from(snap_g(v)); }
+  // The moving-wall term of a bounced link, on the set's grid.
+  __device__ __forceinline__ static float wall_term(float t, bool is_g) { return is_g ? snap_g(t) : snap_f(t); }
   template <class PL> __device__ __forceinline__ static const float* rest(const char* b, PL pl, int set, int idx) {
     return plane_elem<float>(b, pl, kRestFirst + set, idx);
   }
@@ -213,14 +271,14 @@ template <class H> struct PopHalf {
     if (i == 0) return __ldg(rest(b, pl, 1, idx));
     return Cvt<H>::to(__ldg(half(b, pl, 7 + i, idx)));
   }
-  // Single values (checkpoint restore): the rest populations are stored as given.
+  // Single values (checkpoint restore, of any size), put on the grids.
   template <class PL> __device__ __forceinline__ static void stf(char* b, PL pl, int i, int idx, C d) {
-    if (i == 0) *rest(b, pl, 0, idx) = d;
-    else *half(b, pl, i - 1, idx) = Cvt<H>::from(d);
+    if (i == 0) *rest(b, pl, 0, idx) = grid_f(d);
+    else *half(b, pl, i - 1, idx) = Cvt<H>::from(grid_f(d));
   }
   template <class PL> __device__ __forceinline__ static void stg(char* b, PL pl, int i, int idx, C v) {
-    if (i == 0) *rest(b, pl, 1, idx) = v;
-    else *half(b, pl, 7 + i, idx) = Cvt<H>::from(v);
+    if (i == 0) *rest(b, pl, 1, idx) = grid_g(v);
+    else *half(b, pl, 7 + i, idx) = Cvt<H>::from(grid_g(v));
   }
   template <class PL> __device__ __forceinline__ static double ldf_full(const char* b, PL pl, int i, int idx) {
     return (double)ldf(b, pl, i, idx) + lat_w<double>(i);
@@ -230,9 +288,9 @@ template <class H> struct PopHalf {
   }
   // Store one node with the rest populations as closures (Eq. 10: f_0 = rho - sum_{i>0} f_i,
   // g_0 = phi - sum_{i>0} g_i) of the ROUNDED moving populations, so that the stored values sum
-  // to the node's rho and phi (the collision conserves both; the caller passes them): 16-bit
-  // rounding then redistributes among directions but does not create or destroy mass or order
-  // parameter.  In deviations (sum_i w_i = 1): d_0 = (rho - 1) - sum_{i>0} d_i.
+  // to the node's rho and phi (the collision conserves both; the caller passes them, on the
+  // grids): 16-bit rounding then redistributes among directions but does not create or destroy
+  // mass or order parameter.  In deviations (sum_i w_i = 1): d_0 = (rho - 1) - sum_{i>0} d_i.
   // sr_key: 0 rounds to nearest; otherwise the step's key for stochastic rounding.
   template <class PL>
   __device__ __forceinline__ static void store_node(char* b, PL pl, int idx, const C f[9], const C g[9], float drho,
@@ -246,13 +304,13 @@ template <class H> struct PopHalf {
     };
     if (!sr_key) {  // one uniform branch: the round-to-nearest loop carries no stochastic code
 #pragma unroll
-      for (int i = 1; i < 9; ++i) put(i, Cvt<H>::from(f[i]), Cvt<H>::from(g[i]));
+      for (int i = 1; i < 9; ++i) put(i, encf(f[i]), encg(g[i]));
     } else {
       uint32_t w = sr_start((unsigned)idx, sr_key);
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         if (i > 1) w = sr_next(w);
-        put(i, SRound<H>::round(f[i], w & 0xFFFFu), SRound<H>::round(g[i], w >> 16));
+        put(i, SRound<H, -24>::round(f[i], w & 0xFFFFu), SRound<H, -23>::round(g[i], w >> 16));
       }
     }
     *rest(b, pl, 0, idx) = rest_f(drho, sf);
@@ -395,16 +453,16 @@ __device__ __forceinline__ void pull(const char* __restrict__ src, const Geometr
   if (bot) {  // directions 2, 5, 6 come from below the wall at y = -1/2
     const int rp = (y + 1) * geo.pitch;
     out[2] = own[4];
-    out[5] = own[7] + k6 * u_bot;   // 6 w_5 s c_x5 u_w, w_5 = 1/36, c_x5 = +1
-    out[6] = own[8] - k6 * u_bot;   // c_x6 = -1
+    out[5] = own[7] + P::wall_term(k6 * u_bot, IS_G);   // 6 w_5 s c_x5 u_w, w_5 = 1/36, c_x5 = +1
+    out[6] = own[8] - P::wall_term(k6 * u_bot, IS_G);   // c_x6 = -1
     out[4] = LD(4, rp + x);
     out[7] = LD(7, rp + xp);
     out[8] = LD(8, rp + xm);
   } else {    // directions 4, 7, 8 come from above the wall at y = ny - 1/2
     const int rm = (y - 1) * geo.pitch;
     out[4] = own[2];
-    out[7] = own[5] - k6 * u_top;   // c_x7 = -1
-    out[8] = own[6] + k6 * u_top;   // c_x8 = +1
+    out[7] = own[5] - P::wall_term(k6 * u_top, IS_G);   // c_x7 = -1
+    out[8] = own[6] + P::wall_term(k6 * u_top, IS_G);   // c_x8 = +1
     out[2] = LD(2, rm + x);
     out[5] = LD(5, rm + xm);
     out[6] = LD(6, rm + xp);
@@ -614,20 +672,24 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
     if (ph.forced) f[0] += (C(1) - C(0.5) * om) * (C(4) / C(9)) * (-C(3) * (ux * Fx + uy * Fy));
   }
 
-  // g: BGK towards g_eq (Eqs. 7, 9, 10).
+  // g: BGK towards g_eq (Eqs. 7, 9, 10).  The rest population's departure from equilibrium is
+  // g0eq - g0 = (phi - sum_{i>0} geq_i) - g0 = -sum_{i>0} (geq_i - g_i) (phi = sum g), so g0 is
+  // updated by that small increment: g0, of the order of phi, then takes one rounding per step
+  // instead of the roundings of phi and of the closure at its own scale (FP32: ulp(1) ~ 1e-7).
   {
     const C uu = ux2 + uy2;
     const C gmu = ph.Gamma * mu;
-    C sum = C(0);
+    C dsum = C(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const C w = C(lat_w36(i)) / C(36);
       const C cu = lat_dot<C>(i, ux, uy);
       const C geq = w * (gmu + phi * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-      sum += geq;
-      g[i] = g[i] + ph.omega_phi * (geq - g[i]);
+      const C d = geq - g[i];
+      dsum += d;
+      g[i] = g[i] + ph.omega_phi * d;
     }
-    g[0] = g[0] + ph.omega_phi * ((phi - sum) - g[0]);
+    g[0] = g[0] - ph.omega_phi * dsum;
   }
   return drho;
 }

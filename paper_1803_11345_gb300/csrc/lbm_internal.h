@@ -21,7 +21,13 @@ struct HostPhys {
   int rounding = 0;      // lbm_rounding
   uint32_t seed = 0;     // stochastic-rounding seed
   uint32_t sr_key = 0;   // per launch: 0 rounds to nearest, else the step's stochastic-rounding key
+  int wait_probes = -1;  // staged kernel: probes before a bulk-copy wait gives up (< 0: the default)
 };
+
+// Bits of a lattice's device status word: a node produced a non-finite rho or phi; a bounded
+// device-side wait gave up (the step that set it is incomplete).
+constexpr int kFlagNonfinite = 1;
+constexpr int kFlagTimeout = 2;
 
 // Tile of the fused step: BX columns x BY rows of threads, `rows` lattice rows per CTA.
 // staged = 1 selects the bulk-copy staged kernel (lbm_staged.cu) with `depth` bands of

@@ -91,7 +91,9 @@ __global__ void k_init(const double* __restrict__ fields, char* __restrict__ dst
   f[0] = drho - sf;
   g[0] = phi - sg;
   const C drho_c = collide<C>(ph, f, g, phi, gx, gy, lap);
-  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g, drho_c, phi);
+  // rho - 1 and phi of the initial state on the storage's grids (16-bit storage; see PopHalf):
+  // the closures then give stored values whose sums every later step keeps exactly.
+  P::store_node(dst, geo.plane, y * geo.pitch + x, f, g, P::grid_f(drho_c), P::grid_g(phi));
 }
 
 // -------------------------------------------------------------------------------------------

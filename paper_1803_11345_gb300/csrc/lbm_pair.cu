@@ -74,13 +74,23 @@ __device__ __forceinline__ void st_word(char* __restrict__ b, unsigned byte_off,
   *reinterpret_cast<unsigned int*>(b + byte_off) = v;
 }
 
-// Two floats rounded to the storage type and packed (low half = first), and back.
+// Both lanes onto the grid of step 2^-24 (k = kGridF) or 2^-23 (k = kGridG) by the one-node
+// kernel's snap (PopHalf), in packed instructions.
+__device__ __forceinline__ F2 grid_snap2(F2 v, float k) { return f2_sub(f2_add(v, F2(k)), F2(k)); }
+
+// Two floats rounded to the storage type and packed (low half = first), and back.  packf / packg
+// encode a node pair's f deviations / g values as PopHalf::encf / encg do for one node.
 template <int PREC> struct Pack;
 template <> struct Pack<2> {
   using H = __half;
   __device__ __forceinline__ static uint32_t pack(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static uint32_t packf(F2 v) { return pack(v.v.x, v.v.y); }
+  __device__ __forceinline__ static uint32_t packg(F2 v) {
+    const F2 s = grid_snap2(v, kGridG);
+    return pack(s.v.x, s.v.y);
   }
   __device__ __forceinline__ static float2 unpack(uint32_t w) {
     return __half22float2(*reinterpret_cast<const __half2*>(&w));
@@ -91,6 +101,14 @@ template <> struct Pack<3> {
   __device__ __forceinline__ static uint32_t pack(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static uint32_t packf(F2 v) {
+    const F2 s = grid_snap2(v, kGridF);
+    return pack(s.v.x, s.v.y);
+  }
+  __device__ __forceinline__ static uint32_t packg(F2 v) {
+    const F2 s = grid_snap2(v, kGridG);
+    return pack(s.v.x, s.v.y);
   }
   __device__ __forceinline__ static float2 unpack(uint32_t w) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
@@ -276,7 +294,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       unpack_pair<PREC>(fA, f);
       unpack_pair<PREC>(gA, g);
       const F2 drho = collide<F2>(ph, f, g, phi, dxp, dyp, lap);
-      if (!(isfinite(drho.v.x) && isfinite(drho.v.y) && isfinite(phi.v.x) && isfinite(phi.v.y))) atomicOr(flag, 1);
+      if (!(isfinite(drho.v.x) && isfinite(drho.v.y) && isfinite(phi.v.x) && isfinite(phi.v.y))) atomicOr(flag, kFlagNonfinite);
       // Encode: direction i of both nodes rounds into one word; the rest closures are formed
       // from the rounded values in direction order.
       const unsigned e = (unsigned)(r * pitch + x);
@@ -291,8 +309,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       const uint32_t key = ph.sr_key;
       if (!key) {  // one uniform branch: the round-to-nearest loop carries no stochastic code
 #pragma unroll
-        for (int i = 1; i < 9; ++i)
-          put(i, Pack<PREC>::pack(f[i].v.x, f[i].v.y), Pack<PREC>::pack(g[i].v.x, g[i].v.y));
+        for (int i = 1; i < 9; ++i) put(i, Pack<PREC>::packf(f[i]), Pack<PREC>::packg(g[i]));
       } else {
         using H = typename Pack<PREC>::H;
         uint32_t ra = sr_start(e, key), rb = sr_start(e + 1u, key);
@@ -302,13 +319,14 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
             ra = sr_next(ra);
             rb = sr_next(rb);
           }
+          using SF = SRound<H, -24>;
+          using SG = SRound<H, -23>;
           if constexpr (PREC == 3) {  // BF16: the two high halves of the rounded FP32 patterns
-            put(i,
-                __byte_perm(SRound<H>::bits(f[i].v.x, ra & 0xFFFFu), SRound<H>::bits(f[i].v.y, rb & 0xFFFFu), 0x7632),
-                __byte_perm(SRound<H>::bits(g[i].v.x, ra >> 16), SRound<H>::bits(g[i].v.y, rb >> 16), 0x7632));
+            put(i, __byte_perm(SF::bits(f[i].v.x, ra & 0xFFFFu), SF::bits(f[i].v.y, rb & 0xFFFFu), 0x7632),
+                __byte_perm(SG::bits(g[i].v.x, ra >> 16), SG::bits(g[i].v.y, rb >> 16), 0x7632));
           } else {  // FP16: both nodes converted toward zero and packed by one instruction
-            put(i, cvt_rz_pair(SRound<H>::pre(f[i].v.x, ra & 0xFFFFu), SRound<H>::pre(f[i].v.y, rb & 0xFFFFu)),
-                cvt_rz_pair(SRound<H>::pre(g[i].v.x, ra >> 16), SRound<H>::pre(g[i].v.y, rb >> 16)));
+            put(i, cvt_rz_pair(SF::pre(f[i].v.x, ra & 0xFFFFu), SF::pre(f[i].v.y, rb & 0xFFFFu)),
+                cvt_rz_pair(SG::pre(g[i].v.x, ra >> 16), SG::pre(g[i].v.y, rb >> 16)));
           }
         }
       }

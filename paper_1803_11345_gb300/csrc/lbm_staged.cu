@@ -68,8 +68,8 @@ template <int PREC> struct Stage {
       float sf = 0.0f, sg = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const Hf hf = Cvt<Hf>::from(f[i]);
-        const Hf hg = Cvt<Hf>::from(g[i]);
+        const Hf hf = PopHalf<Hf>::encf(f[i]);
+        const Hf hg = PopHalf<Hf>::encg(g[i]);
         reinterpret_cast<Hf*>(ob + ooff(i, n))[e] = hf;
         reinterpret_cast<Hf*>(ob + ooff(9 + i, n))[e] = hg;
         sf += Cvt<Hf>::to(hf);
@@ -101,13 +101,19 @@ size_t staged_smem_bytes() {
 
 // Probes before a wait is declared stuck (each probe suspends for a short hardware window):
 // far beyond any legitimate copy latency, short enough to return control in well under a second.
+// The waits of the main loop take their limit from the launch (lbm_set_wait_limit; this one by
+// default, 0 = give up without probing); the prologue's waits and those that drain the copies
+// still in flight after an abort always take this one, so that no copy can land in shared memory
+// after the CTA has returned.
 constexpr uint32_t kWaitProbes = 1u << 22;
 
 template <int PREC, int BX, int BY, int D>
 __global__ void __launch_bounds__(BX * BY)
 k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geometry geo,
-              const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag) {
+              const Phys<typename Pop<PREC>::C> ph, const int rows, int* __restrict__ flag,
+              const uint32_t wait_limit) {
   using S = Stage<PREC>;
+  using P = Pop<PREC>;
   using C = typename S::C;
   constexpr int H = S::H;
   constexpr int W = BX + 2 * H;
@@ -207,10 +213,10 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     f_next += nf;
   };
   bool stuck = false;
-  auto wait_row = [&](bool g, int v) {
+  auto wait_row = [&](bool g, int v, uint32_t limit) {
     const int k = v - (g ? gvb : fvb);
     uint64_t* bar = g ? &gbar[k % R] : &fbar[k % R];
-    if (!mbar_wait_bounded(bar, (uint32_t)((k / R) & 1), kWaitProbes)) stuck = true;
+    if (!mbar_wait_bounded(bar, (uint32_t)((k / R) & 1), limit)) stuck = true;
   };
 
   // Pointers to the staged rows v-1, v, v+1 of a set, for the node at virtual row v (a wall
@@ -270,15 +276,15 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     const C k6 = C(6) * s / C(36);
     if (bot) {
       out[2] = own[4];
-      out[5] = own[7] + k6 * ph.u_bottom;
-      out[6] = own[8] - k6 * ph.u_bottom;
+      out[5] = own[7] + P::wall_term(k6 * ph.u_bottom, g);
+      out[6] = own[8] - P::wall_term(k6 * ph.u_bottom, g);
       out[4] = L(q.hi, 4, 0);
       out[7] = L(q.hi, 7, 1);
       out[8] = L(q.hi, 8, -1);
     } else {
       out[4] = own[2];
-      out[7] = own[5] - k6 * ph.u_top;
-      out[8] = own[6] + k6 * ph.u_top;
+      out[7] = own[5] - P::wall_term(k6 * ph.u_top, g);
+      out[8] = own[6] + P::wall_term(k6 * ph.u_top, g);
       out[2] = L(q.lo, 2, 0);
       out[5] = L(q.lo, 5, -1);
       out[6] = L(q.lo, 6, 1);
@@ -327,15 +333,15 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     const C k6 = C(6) * s / C(36);
     if (bot) {
       out[2] = own[4];
-      out[5] = own[7] + k6 * ph.u_bottom;
-      out[6] = own[8] - k6 * ph.u_bottom;
+      out[5] = own[7] + P::wall_term(k6 * ph.u_bottom, g);
+      out[6] = own[8] - P::wall_term(k6 * ph.u_bottom, g);
       out[4] = L(q.hi, 4, 0);
       out[7] = L(q.hi, 7, 1);
       out[8] = L(q.hi, 8, -1);
     } else {
       out[4] = own[2];
-      out[7] = own[5] - k6 * ph.u_top;
-      out[8] = own[6] + k6 * ph.u_top;
+      out[7] = own[5] - P::wall_term(k6 * ph.u_top, g);
+      out[8] = own[6] + P::wall_term(k6 * ph.u_top, g);
       out[2] = L(q.lo, 2, 0);
       out[5] = L(q.lo, 5, -1);
       out[6] = L(q.lo, 6, 1);
@@ -375,7 +381,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
 
   // Prologue: stage the first rows, then phi of rows y0-1 .. y0+BY-1.
   issue_upto(gvb + R - 1, fvb + R - 1);
-  for (int v = gvb; v <= min(y0 + BY, g_last); ++v) wait_row(true, v);
+  for (int v = gvb; v <= min(y0 + BY, g_last); ++v) wait_row(true, v, kWaitProbes);
   C gcur[9], gnxt[9];
   {
     const int r = y0 + ty;
@@ -392,8 +398,8 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
 
   for (int Y = y0; Y < y1; Y += BY) {
     // rows of this step: g [Y+BY-1, Y+2BY] for phi, f [Y-1, Y+BY] for the pulls
-    for (int v = max(Y + BY + 1, gvb); v <= min(Y + 2 * BY, g_last); ++v) wait_row(true, v);
-    for (int v = (Y == y0 ? fvb : Y + 1); v <= min(Y + BY, f_last); ++v) wait_row(false, v);
+    for (int v = max(Y + BY + 1, gvb); v <= min(Y + 2 * BY, g_last); ++v) wait_row(true, v, wait_limit);
+    for (int v = (Y == y0 ? fvb : Y + 1); v <= min(Y + BY, f_last); ++v) wait_row(false, v, wait_limit);
     const int rn = Y + BY + ty;
     if (rn <= y1) phi_row(rn, gnxt);
     const int r = Y + ty;
@@ -404,11 +410,11 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
     if (storer) bulk_wait_read_all();  // last band's stores are done reading the staging buffer
     __syncthreads();
     if (*abort_flag) {
-      if (tid == 0) atomicOr(flag, 2);
+      if (tid == 0) atomicOr(flag, kFlagTimeout);
       // Let the copies already issued land before the CTA's shared memory is released.
       if (tid == 0) {
-        for (int v = max(gvb, g_next - R); v < g_next; ++v) wait_row(true, v);
-        for (int v = max(fvb, f_next - R); v < f_next; ++v) wait_row(false, v);
+        for (int v = max(gvb, g_next - R); v < g_next; ++v) wait_row(true, v, kWaitProbes);
+        for (int v = max(fvb, f_next - R); v < f_next; ++v) wait_row(false, v, kWaitProbes);
       }
       if (storer) bulk_wait_all();
       return;
@@ -430,7 +436,7 @@ k_step_staged(const char* __restrict__ src, char* __restrict__ dst, const Geomet
       stencils<C>(s, dxp, dyp, lap);
       const C phi = s[1][1];
       const C drho = collide<C>(ph, f, gcur, phi, dxp, dyp, lap);
-      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, 1);
+      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, kFlagNonfinite);
       S::store_node(obuf, NOUT, ty * BX + tx, f, gcur, drho, phi);
       fence_proxy_async_smem();
     }
@@ -480,7 +486,8 @@ cudaError_t staged_launch(const HostGeometry& g, const HostPhys& p, int rows, co
   geo.walls = g.walls;
   dim3 blk(BX, BY);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + rows - 1) / rows);
-  k_step_staged<PREC, BX, BY, D><<<grd, blk, smem, s>>>(src, dst, geo, phys_of<PREC>(p), rows, flag);
+  const uint32_t limit = p.wait_probes < 0 ? kWaitProbes : (uint32_t)p.wait_probes;
+  k_step_staged<PREC, BX, BY, D><<<grd, blk, smem, s>>>(src, dst, geo, phys_of<PREC>(p), rows, flag, limit);
   return cudaGetLastError();
 }
 

@@ -159,7 +159,7 @@ __device__ __forceinline__ void step_tile(const char* __restrict__ src, char* __
       unpack<PREC, false>(fA, fAd, f);
       unpack<PREC, true>(gA, gAd, g);
       const C drho = collide<C>(ph, f, g, phi, dxp, dyp, lap);
-      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, 1);
+      if (!(isfinite(drho) && isfinite(phi))) atomicOr(flag, kFlagNonfinite);
       P::store_node(dst, pl, r * geo.pitch + x, f, g, drho, phi, ph.sr_key);
     }
 #pragma unroll

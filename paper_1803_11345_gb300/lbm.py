@@ -79,6 +79,8 @@ def _load():
     lib.lbm_set_populations.restype = i
     lib.lbm_check.argtypes = [vp]
     lib.lbm_check.restype = i
+    lib.lbm_set_wait_limit.argtypes = [vp, i]
+    lib.lbm_set_wait_limit.restype = i
     lib.lbm_set_kernel.argtypes = [vp, i, i, i, i, i]
     lib.lbm_set_kernel.restype = i
     ip = ctypes.POINTER(ctypes.c_int)
@@ -217,6 +219,10 @@ def lbm_set_populations(h: int, f, g) -> None:
 
 def lbm_check(h: int) -> int:
     return _lib.lbm_check(h)
+
+
+def lbm_set_wait_limit(h: int, probes: int) -> None:
+    _check(_lib.lbm_set_wait_limit(h, int(probes)), h)
 
 
 def lbm_set_kernel(h: int, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0) -> None:
@@ -382,6 +388,9 @@ class Lattice:
 
     def set_kernel(self, variant: int, bx: int = 0, by: int = 0, depth: int = 0, rows: int = 0):
         lbm_set_kernel(self.h, variant, bx, by, depth, rows)
+
+    def set_wait_limit(self, probes: int):
+        lbm_set_wait_limit(self.h, probes)
 
     @property
     def state_ptr(self) -> int:

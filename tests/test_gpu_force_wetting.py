@@ -115,27 +115,38 @@ def test_every_tile_with_wetting_and_force_fp64(lbm, orc):
             lat.close()
 
 
-def test_contact_angle_setup_fp32_and_fp16(lbm, orc):
-    """FP32 storage within 2e-5 on phi and FP16 storage within 2e-3 after 1000 steps of the
-    contact-angle set-up (droplet falling under a force onto a wall with the 60-degree gradient).
-    The FP32 bound is twice the periodic spinodal's: here the interface moves (the droplet falls
-    and relaxes from its tanh start next to a wall), which carries the per-step FP32 rounding of
-    the velocity into phi; the same droplet without force or wetting already differs by 4.4e-6,
-    and FP64 storage agrees with the oracle to 1e-13."""
+@pytest.fixture(scope="module")
+def contact_angle_setup(orc):
+    """The contact-angle set-up (a droplet falling under a force of 1e-5 onto a wall with the
+    60-degree gradient of Eq. 18) and the oracle's fields after 1000 steps."""
     h = orc.wall_gradient(math.radians(60), 0.04, 0.04)
     phi0 = W.droplet(100, 100, 20, gamma=0.04, a=0.04, cy=30.0)
-    kw = dict(tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.05), bc=lbm.LBM_WALLS_Y, wet_bottom=h,
+    kw = dict(tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.05), bc=1, wet_bottom=h,
               force_y=-1e-5, force_mode=1)
     o = orc.Oracle(phi0, **oracle_kwargs(kw))
     o.step(1000)
-    _, uxo, uyo, po = o.fields()
-    for prec, bound in (("fp32", 2e-5), ("fp16s", 2e-3)):
-        lat = lbm.Lattice(phi0, prec=prec, **kw)
-        lat.step(1000)
-        _, uxg, uyg, pg = lat.fields()
-        assert abs_err(pg, po) <= bound, (prec, abs_err(pg, po))
-        assert abs_err(uxg, uxo) <= 2 * bound and abs_err(uyg, uyo) <= 2 * bound, prec
-        lat.close()
+    return phi0, kw, o.fields()
+
+
+@pytest.mark.parametrize("prec,bound", [
+    ("fp32", 1e-5), ("fp16s", 2e-3),
+    pytest.param("bf16s", 2e-3, marks=pytest.mark.xfail(
+        strict=True, reason="BF16 storage does not resolve the 1e-5 body force: the per-step momentum it adds "
+                            "(~3e-6 per population) is below BF16's rounding unit of the stored deviations; "
+                            "measured 4.5e-2 on phi"))])
+def test_contact_angle_setup_reduced_precision(lbm, contact_angle_setup, prec, bound):
+    """The contact-angle set-up after 1000 steps against the FP64 oracle: the contract on phi,
+    1e-5 for FP32 storage (measured 5.3e-7) and 2e-3 for 16-bit storage (FP16 3.4e-4); velocities
+    within twice those."""
+    phi0, kw, (_, uxo, uyo, po) = contact_angle_setup
+    lat = lbm.Lattice(phi0, prec=prec, **kw)
+    lat.step(1000)
+    _, uxg, uyg, pg = lat.fields()
+    lat.close()
+    print(prec, "contact-angle set-up, max |phi - phi_oracle|:", abs_err(pg, po),
+          "max |u - u_oracle|:", max(abs_err(uxg, uxo), abs_err(uyg, uyo)))
+    assert abs_err(pg, po) <= bound, (prec, abs_err(pg, po))
+    assert abs_err(uxg, uxo) <= 2 * bound and abs_err(uyg, uyo) <= 2 * bound, prec
 
 
 def test_batch_members_with_wetting_and_force_fp64(lbm, orc):

@@ -61,11 +61,12 @@ def test_laplace_droplet_fp64_1000_steps(lbm, orc):
 
 
 def test_spinodal_fp64_viscosity_ratio(lbm, orc):
-    """256x256 spinodal, phi ~ U[-0.05, 0.05], viscosity ratio 10 interpolated linearly in tau."""
+    """256x256 spinodal, phi ~ U[-0.05, 0.05], viscosity ratio 10 interpolated linearly in tau,
+    1000 steps."""
     phi0 = W.spinodal(256, 256, seed=11)
     kw = dict(prec=lbm.LBM_FP64, tau_l=orc.tau_from_nu(0.1), tau_g=orc.tau_from_nu(0.01),
               visc=lbm.LBM_TAU_LINEAR)
-    lat, o = run_pair(lbm, orc, phi0, 300, **kw)
+    lat, o = run_pair(lbm, orc, phi0, 1000, **kw)
     assert_fp64_parity(lat, o)
 
 
@@ -156,6 +157,38 @@ def test_nonfinite_state_is_reported(lbm):
     assert lbm.lbm_check(lat.h) == lbm.LBM_OK  # flag cleared by the report
 
 
+def test_staged_wait_timeout_is_reported(lbm):
+    """Failure detection of the bounded device-side waits, without a fault: with the staged
+    kernel's wait limit set to 0 probes every wait of its main loop gives up at once, so each CTA
+    sets the timeout flag, lets the copies it has in flight land (waited for with the default
+    limit) and returns.  The next check reports LBM_ERR_TIMEOUT (not a non-finite state) and
+    clears the flag; with the default limit restored and a checkpoint put back, the handle steps
+    exactly like a fresh lattice stepped from that checkpoint with the same kernel."""
+    nx, ny = 128, 64
+    phi0 = W.droplet(nx, ny, 12, gamma=0.04, a=0.04)
+    kw = dict(prec=lbm.LBM_FP32, tau_l=0.8, tau_g=0.6)
+    lat = lbm.Lattice(phi0, **kw)
+    lat.set_kernel(lbm.LBM_KERNEL_STAGED, 64, 4, 1)
+    lat.step(5)
+    f, g = lat.populations()
+    lat.set_wait_limit(0)
+    lat.step(2)
+    assert lbm.lbm_check(lat.h) == lbm.LBM_ERR_TIMEOUT
+    assert "bounded wait" in lbm.lbm_last_error(lat.h)
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK  # cleared by the report
+    lat.set_wait_limit(-1)
+    lat.set_populations(f, g)
+    ref = lbm.Lattice(phi0, **kw)
+    ref.set_kernel(lbm.LBM_KERNEL_STAGED, 64, 4, 1)
+    ref.set_populations(f, g)
+    lat.step(20)
+    ref.step(20)
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK
+    fa, ga = lat.populations()
+    fb, gb = ref.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
 # -------------------------------------------------------------------------------------------
 # Reduced precision against the FP64 oracle.
 
@@ -170,38 +203,70 @@ def test_spinodal_fp32_1000_steps(lbm, orc):
     assert rel_err(rg, ro) <= 1e-5
 
 
-@pytest.mark.parametrize("prec,bound", [("fp16s", 2e-3), ("bf16s", 5e-3)])
-def test_sheared_droplet_16bit_storage(lbm, orc, prec, bound):
-    """16-bit deviation storage against the FP64 oracle over 1000 steps of a sheared droplet.
-    FP16 (11-bit significand) keeps phi within 2e-3 (measured 1.0e-3).  BF16 (8-bit significand)
-    rounds the f deviations (~3e-3, mostly 3 w_i c.u) to ~1e-5 and shifts the interface by a few
-    1e-3 lattice units over 1000 steps: measured 3.9e-3 (1.1e-2 while the collision added w_i back
-    before computing), bound 5e-3 (|grad phi| <= 0.7)."""
+@pytest.mark.parametrize("form,bound", [("fp16s", 2e-3), ("fp16s+sr", 2e-3), ("bf16s", 2e-3), ("bf16s+sr", 6e-3)])
+def test_sheared_droplet_16bit_storage(lbm, orc, form, bound):
+    """16-bit deviation storage against the FP64 oracle over 1000 steps of a sheared droplet
+    (128 x 64, walls +-0.01, contrast 10).  The 16-bit contract is 2e-3 on phi.  Measured: FP16
+    1.5e-4 rounded to nearest, 3.5e-4 to 6.4e-4 stochastically; BF16 1.25e-3 rounded to nearest.
+    BF16 rounded stochastically measures 3.7e-3 to 4.8e-3: its 8-bit significand gives every stored
+    deviation (~3e-3) a random rounding of ~1e-5 per step, whose noise then sets the maximum; that
+    bound is a regression guard at the measured level, not the contract."""
     phi0 = W.droplet(128, 64, 16, gamma=0.04, a=0.04)
     kw = dict(tau_l=orc.tau_from_nu(0.2), tau_g=orc.tau_from_nu(0.02), bc=lbm.LBM_WALLS_Y,
               u_top=0.01, u_bottom=-0.01)
-    lat, o = run_pair(lbm, orc, phi0, 1000, prec=lbm.PRECISIONS[prec], **kw)
+    gkw = dict(kw, prec=lbm.PRECISIONS[form.split("+")[0]])
+    if form.endswith("+sr"):
+        gkw.update(rounding=lbm.LBM_ROUND_STOCHASTIC, seed=3)
+    lat = lbm.Lattice(phi0, **gkw)
+    o = orc.Oracle(phi0, **oracle_kwargs(kw))
+    lat.step(1000)
+    o.step(1000)
     _, _, _, pg = lat.fields()
     _, _, _, po = o.fields()
+    print(form, "max |phi - phi_oracle|:", abs_err(pg, po))
     assert abs_err(pg, po) <= bound, abs_err(pg, po)
 
 
+CONSERVE_CASES = {
+    # kernel, boundaries, rounding: every 16-bit path that stores populations
+    "generic_periodic": dict(kernel=1),
+    "generic_walls_force_wetting": dict(kernel=1, walls=True),
+    "generic_walls_stochastic": dict(kernel=1, walls=True, sr=True),
+    "pair_periodic": dict(kernel=4),
+    "pair_periodic_stochastic": dict(kernel=4, sr=True),
+    "pair_walls_stochastic": dict(kernel=4, walls=True, sr=True),
+    "staged_walls": dict(kernel=2, walls=True),
+}
+
+
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
-def test_16bit_storage_conserves_phi_and_mass(lbm, prec):
-    """The rest populations are stored (FP32) as closures of the rounded moving ones (Eq. 10),
-    so the 16-bit rounding itself moves no order parameter or mass between nodes' totals.
-    sum phi stays within FP32 accumulation error (measured ~1e-6 over 500 steps of 12288 nodes).
-    sum rho drifts by the FP32 rounding of the closure sums, which correlates across nodes
-    because the stored values sit on a 16-bit grid offset by the constant w_i: stated bound
-    1e-7 per node per step (measured 3.4e-8 FP16, 7e-9 BF16)."""
+@pytest.mark.parametrize("case", sorted(CONSERVE_CASES))
+def test_16bit_storage_conserves_phi_and_mass_exactly(lbm, prec, case):
+    """The rest populations are stored (FP32) as closures of the rounded moving ones (Eq. 10), and
+    every stored value and moving-wall term lies on a fixed binary grid (f: 2^-24, g: 2^-23), so
+    every sum the step forms is exact: the 16-bit rounding moves no mass or order parameter, and
+    the FP64 totals (exact sums of grid values) are the same bit for bit after 400 steps, with
+    moving walls, wetting gradients and a body force, rounding to nearest or stochastically, in
+    the one-node, paired and staged kernels."""
+    c = CONSERVE_CASES[case]
     nx, ny = 128, 96
-    steps = 500
-    lat = lbm.Lattice(W.spinodal(nx, ny, seed=21), prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53)
+    kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53)
+    if c.get("walls"):
+        phi0 = W.droplet(nx, ny, 20, gamma=0.04, a=0.04, cy=30.0)
+        kw.update(bc=lbm.LBM_WALLS_Y, u_top=0.01, u_bottom=-0.007, wet_bottom=0.1, wet_top=-0.05,
+                  force_x=1e-6, force_y=-2e-5, force_mode=lbm.LBM_FORCE_PHASE_L)
+    else:
+        phi0 = W.spinodal(nx, ny, seed=21)
+    if c.get("sr"):
+        kw.update(rounding=lbm.LBM_ROUND_STOCHASTIC, seed=5)
+    lat = lbm.Lattice(phi0, **kw)
+    lat.set_kernel(c["kernel"])
     s0 = lat.conservation()
-    lat.step(steps)
+    lat.step(400)
     s1 = lat.conservation()
-    assert abs(s1[0] - s0[0]) <= 1e-5, (s0[0], s1[0])
-    assert abs(s1[1] - s0[1]) <= 1e-7 * nx * ny * steps, (s0[1], s1[1])
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK
+    assert s1[0] == s0[0], (s0[0], s1[0])
+    assert s1[1] == s0[1], (s0[1], s1[1])
 
 
 # -------------------------------------------------------------------------------------------
@@ -323,8 +388,9 @@ def test_paired_16bit_kernel_follows_one_node_kernel(lbm, orc, prec):
             lat.step(200)
             f, g = lat.populations()
             assert abs_err(f, fr) <= 1e-3 and abs_err(g, gr) <= 1e-3, (bx, by, rows, abs_err(f, fr), abs_err(g, gr))
-            bound = 2e-3 if prec == "fp16s" else 2e-2
-            assert abs_err(lat.fields()[3], po) <= bound
+            err = abs_err(lat.fields()[3], po)
+            print(prec, "paired", bx, by, rows, "max |phi - phi_oracle| after 200 steps:", err)
+            assert err <= 2e-3
             lat.close()
 
 
@@ -373,7 +439,8 @@ def test_paired_16bit_kernel_with_walls(lbm, orc, prec):
     o = orc.Oracle(phi0, **oracle_kwargs(kw))
     o.step(200)
     po = o.fields()[3]
-    bound = 2e-3 if prec == "fp16s" else 2e-2
+    bound = 2e-3
+    print(prec, "walled one-node max |phi - phi_oracle| after 200 steps:", abs_err(ref.fields()[3], po))
     assert abs_err(ref.fields()[3], po) <= bound
     for bx, by in PAIR_TILES:
         for rows in (0, 7):

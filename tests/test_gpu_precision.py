@@ -3,21 +3,19 @@ full size, and the statistics the paper's experiments report.
 
 Measured here (the tests print them):
 * Sheared-droplet channel, 1024 x 512, walls at +-0.01, droplet R = 64, nu_l = 0.2, viscosity
-  contrast 100, 1000 steps, max |phi - phi_oracle|: FP64 7e-14, FP32 2.8e-5, FP16 8.6e-4,
-  BF16 1.3e-2.  The FP32 difference sits on the interface and levels off near 1e-4; FP64 shows
-  the same growth (rounding differences of ~1e-16 per step against the oracle reach 7e-14 after
-  1000 steps, a factor ~700), so it is this configuration's sensitivity to any rounding, not an
-  FP32 defect; FP32 states 5e-5 here (1e-5 on the spinodal workload, where it measures 7e-7).
+  contrasts 1 to 1000, 1000 steps, max |phi - phi_oracle|: FP64 ~7e-14, FP32 2.7e-6 to 5.4e-6,
+  FP16 9.8e-4 to 1.8e-3 (3.4e-4 to 6.5e-4 rounded stochastically), BF16 8.7e-3 to 1.4e-2 (3.2e-3
+  to 5.2e-3 stochastically).  FP32 and FP16 meet the contract (1e-5, 2e-3); BF16 does not.
 * Laplace droplet (64^2, R = 16, a = 0.04, gamma = 0.02, tau = 1), converged pressure jump
-  against the oracle's: FP32 +0.012%, FP16 +0.23%, BF16 -1.2%.
+  against the oracle's: FP32 +0.009%, FP16 +0.18%, BF16 -0.03%.
 * Taylor deformation in shear (the paper's set-up, 2H = 200, R = 30, Ca 0.05 to 0.25) against
-  the FP64 run: FP32 within 0.25% (identical for four of the five Ca), FP16 2.5% to 9.2% high,
-  BF16 -28% to +54%.  The 16-bit forms do not resolve this flow: the wall speed is 2.2e-3, the
-  shear changes a moving population's deviation by ~7e-6 per lattice row, and the stored
-  deviations (~7e-4) have a rounding unit of 4.8e-7 in FP16 (15 units per row) and 3.8e-6 in
-  BF16 (under 2): the viscous stress the flow runs on is quantised.  With stochastic rounding
-  (unbiased rounding of every stored value) the deformation comes within 0.27% (FP16) and 0.45%
-  (BF16) of FP64.
+  the FP64 run: FP32 within 0.4%; rounded stochastically FP16 within 0.27% and BF16 within 0.79%.
+  Rounded to nearest the 16-bit forms do not resolve this flow (FP16 +2.7% to +9.0%, BF16 -27% to
+  +48%): the wall speed is 2.2e-3, the shear changes a moving population's deviation by ~7e-6 per
+  lattice row, and the stored deviations (~7e-4) have a rounding unit of 4.8e-7 in FP16 (15 units
+  per row) and 3.8e-6 in BF16 (under 2): the viscous stress the flow runs on is quantised, and
+  rounding to nearest quantises it the same way at neighbouring nodes.  Stochastic rounding
+  (unbiased rounding of every stored value) removes that bias.
 """
 import json
 import math
@@ -50,32 +48,90 @@ def tau(nu):
     return 3.0 * nu + 0.5
 
 
-def test_sheared_channel_full_size_against_oracle(lbm, orc):
-    """Every storage precision against the FP64 oracle after 1000 steps of the full-size
-    sheared-droplet channel at viscosity contrast 100 (the oracle runs on all host cores: about
-    half a minute).  Bounds: FP64 1e-12 relative; FP32 5e-5 on phi (see the module notes);
-    FP16 2e-3 on phi, the 16-bit bound of the parity suite; BF16 2e-2 (measured 1.3e-2: at this
-    contrast the interface moves further under BF16's rounding than on the parity suite's 128 x 64
-    droplet at contrast 10, 3.9e-3)."""
-    nx, ny, R, ga = 1024, 512, 64, 0.04
-    phi0 = W.droplet(nx, ny, R, gamma=ga, a=ga)
-    kw = dict(tau_l=tau(0.2), tau_g=tau(0.2 / 100), gamma=ga, a=ga, M=0.1, Gamma=1.0, bc=1, u_top=0.01,
-              u_bottom=-0.01)
-    o = orc.Oracle(phi0, **oracle_kwargs(kw))
-    o.step(1000)
-    ro, uxo, uyo, po = o.fields()
+ZETAS = (1, 10, 100, 1000)
+CHANNEL_FORMS = ("fp64", "fp32", "fp16s", "fp16s+sr", "bf16s", "bf16s+sr")
+# The contract on phi after 1000 steps: FP32 1e-5, 16-bit storage 2e-3 (absolute; phi's bulk
+# values are +-1).  BF16 does not meet it (see test_sheared_channel_bf16_contract); its errors are
+# held at the measured level only so that a regression shows.
+CONTRACT = {"fp32": 1e-5, "fp16s": 2e-3, "fp16s+sr": 2e-3}
+BF16_GUARD = {"bf16s": 2e-2, "bf16s+sr": 6e-3}
+
+
+def channel_kw(zeta):
+    """The sheared-droplet channel: 1024 x 512, walls moving at +-0.01, nu_l = 0.2 (the paper's
+    shear set-up), nu_g = nu_l / zeta, gamma = a = 0.04, M = 0.1, Gamma = 1."""
+    return dict(tau_l=tau(0.2), tau_g=tau(0.2 / zeta), gamma=0.04, a=0.04, M=0.1, Gamma=1.0, bc=1,
+                u_top=0.01, u_bottom=-0.01)
+
+
+@pytest.fixture(scope="module")
+def channel(orc):
+    """Oracle fields of the channel after 1000 steps, one run per contrast (about 30 s each on
+    the host's cores), cached for the module."""
+    cache = {}
+
+    def run(zeta):
+        if zeta not in cache:
+            phi0 = W.droplet(1024, 512, 64, gamma=0.04, a=0.04)
+            o = orc.Oracle(phi0, **oracle_kwargs(channel_kw(zeta)))
+            o.step(1000)
+            cache[zeta] = (phi0, o.fields())
+            o.close()
+        return cache[zeta]
+    return run
+
+
+def channel_form(lbm, phi0, zeta, form, steps=1000):
+    prec = form.split("+")[0]
+    kw = dict(channel_kw(zeta), prec=prec)
+    if form.endswith("+sr"):
+        kw.update(rounding=lbm.LBM_ROUND_STOCHASTIC, seed=7)
+    lat = lbm.Lattice(phi0, **kw)
+    s0 = lat.conservation()
+    lat.step(steps)
+    out = lat.fields()
+    s1 = lat.conservation()
+    lat.close()
+    return out, s0, s1
+
+
+@pytest.mark.parametrize("zeta", ZETAS)
+def test_sheared_channel_contrast_sweep(lbm, channel, zeta):
+    """The sheared-droplet channel at full size (1024 x 512, R = 64) for viscosity contrasts
+    1, 10, 100 and 1000, 1000 steps, every storage form against the FP64 oracle.  FP64 matches to
+    1e-12 (relative); FP32 and FP16 (rounded to nearest or stochastically) meet the contract on
+    phi, 1e-5 and 2e-3.  Measured max |phi - phi_oracle|: FP32 2.7e-6 to 5.4e-6, FP16 9.8e-4 to
+    1.8e-3, FP16 stochastic 3.4e-4 to 6.5e-4; BF16 8.7e-3 to 1.4e-2 and 3.2e-3 to 5.2e-3 stochastic
+    (above the contract: see test_sheared_channel_bf16_contract).  16-bit storage keeps sum rho and
+    sum phi exactly (bit for bit)."""
+    phi0, (ro, uxo, uyo, po) = channel(zeta)
     errs = {}
-    for prec in PRECS:
-        lat = lbm.Lattice(phi0, prec=prec, **kw)
-        lat.step(1000)
-        rg, uxg, uyg, pg = lat.fields()
-        errs[prec] = abs_err(pg, po)
-        if prec == "fp64":
+    for form in CHANNEL_FORMS:
+        (rg, uxg, uyg, pg), s0, s1 = channel_form(lbm, phi0, zeta, form)
+        errs[form] = abs_err(pg, po)
+        if form == "fp64":
             assert rel_err(pg, po) <= 1e-12 and rel_err(rg, ro) <= 1e-12
             assert abs_err(uxg, uxo) <= 1e-12 and abs_err(uyg, uyo) <= 1e-12
-        lat.close()
-    print("max |phi - phi_oracle| after 1000 steps:", errs)
-    assert errs["fp32"] <= 5e-5 and errs["fp16s"] <= 2e-3 and errs["bf16s"] <= 2e-2, errs
+        if form.startswith(("fp16s", "bf16s")):
+            assert s1[0] == s0[0] and s1[1] == s0[1], (form, s0, s1)
+    print(f"zeta {zeta}: max |phi - phi_oracle| after 1000 steps:", errs)
+    for form, bound in CONTRACT.items():
+        assert errs[form] <= bound, (form, errs)
+    for form, guard in BF16_GUARD.items():
+        assert errs[form] <= guard, (form, errs)
+
+
+@pytest.mark.xfail(strict=True, reason="BF16 storage misses the 2e-3 bound on phi: its 8-bit significand rounds "
+                                       "the stored deviations (~3e-3) to ~1e-5 each step; measured 8.7e-3 to 1.4e-2 "
+                                       "(nearest) and 3.2e-3 to 5.2e-3 (stochastic) over contrasts 1 to 1000")
+def test_sheared_channel_bf16_contract(lbm, channel):
+    """The 16-bit contract (2e-3 on phi after 1000 steps) applied to BF16 storage at contrast 100,
+    rounded to nearest and stochastically.  Expected to fail, strictly: should BF16 ever meet it,
+    this test fails and the statement of the miss must be revised."""
+    phi0, (_, _, _, po) = channel(100)
+    for form in ("bf16s", "bf16s+sr"):
+        (_, _, _, pg), _, _ = channel_form(lbm, phi0, 100, form)
+        assert abs_err(pg, po) <= 2e-3, (form, abs_err(pg, po))
 
 
 def laplace_jump(rho, phi, a):
@@ -91,9 +147,10 @@ def test_laplace_jump_across_precisions(lbm, orc):
     steps).  FP64 equals the oracle's jump; it is 0.846 sigma/R, for both, and the oracle gives
     the same ratio for R = 32 on 128^2 once converged (0.841 after 32000 steps): a deficit that
     does not depend on R, i.e. the discrete interface of width sqrt(gamma/a) = 0.71 carries ~16%
-    less tension than the continuum sigma (the sweep at gamma = a lands within 3% of sigma).  FP32 and FP16 storage are within 1% of it (measured 0.012% and 0.23%);
-    BF16 is 1.2% low (its 8-bit significand rounds the density deviations of ~4e-4 that carry the
-    jump to 2^-9 of themselves) and states 2%."""
+    less tension than the continuum sigma (the sweep at gamma = a lands within 3% of sigma).  Every
+    storage form is within the 1% the statistics are held to: measured FP32 +0.009%, FP16 +0.18%,
+    BF16 -0.03% (BF16 was 1.2% low while the order-one rest population g_0 took several FP32
+    roundings per step and the 16-bit closures were inexact)."""
     a, ga = 0.04, 0.02
     phi0 = W.droplet(64, 64, 16, gamma=ga, a=a)
     kw = dict(tau_l=1.0, tau_g=1.0, gamma=ga, a=a, M=0.1, Gamma=1.0)
@@ -112,8 +169,8 @@ def test_laplace_jump_across_precisions(lbm, orc):
     sigma = math.sqrt(8 * ga * a / 9)
     assert abs(jumps["fp64"] / ref - 1) <= 1e-9
     assert abs(ref / (sigma / 16) - 0.846) < 0.01
-    assert abs(jumps["fp32"] / ref - 1) <= 0.01 and abs(jumps["fp16s"] / ref - 1) <= 0.01, jumps
-    assert abs(jumps["bf16s"] / ref - 1) <= 0.02, jumps
+    for prec in ("fp32", "fp16s", "bf16s"):
+        assert abs(jumps[prec] / ref - 1) <= 0.01, (prec, jumps)
 
 
 def deformation(phi):
@@ -134,11 +191,12 @@ def deformation(phi):
 
 def test_taylor_deformation_across_precisions(lbm):
     """The paper's droplet-in-shear set-up (2H = 200, R = 30, nu = 0.2, Re = 0.1, Ca 0.05 to
-    0.25, 150000 steps, one batch per precision): the steady deformation in FP32 storage is within
-    1% of the FP64 run for every Ca, which itself follows 35/32 Ca within 5%.  FP16 states 12%
-    (measured 2.5% to 9.2%); BF16 is printed only (it runs stably, checked above, but does not
-    resolve the shear; see the module notes).  With stochastic rounding both 16-bit forms are
-    within 1% (measured 0.27% FP16, 0.45% BF16); the test states 1% and 2%."""
+    0.25, 150000 steps, one batch per precision), the deformation D_f against the FP64 run, which
+    itself follows 35/32 Ca within 5%.  The contract holds statistics within 1%: FP32 storage
+    (measured within 0.4%) and both 16-bit forms rounded stochastically (FP16 0.27%, BF16 0.79%)
+    meet it.  Rounded to nearest the 16-bit forms do not resolve this slow shear (FP16 +2.7% to
+    +9.0%, BF16 -27% to +48%; see the module notes): the test checks that they miss, so that the
+    statement of the miss is revised should they ever meet it."""
     gold = json.load(open(GOLDEN))["taylor"]
     n, R, nu, Re = 200, 30, 0.2, 0.1
     H = n / 2
@@ -170,8 +228,10 @@ def test_taylor_deformation_across_precisions(lbm):
     print("Taylor deformation by Ca", cas, {k: v.tolist() for k, v in d.items()})
     slope = np.polyfit(np.array(cas), d["fp64"], 1)[0]
     assert abs(slope / gold["slope_theory"] - 1) < 0.05, (slope, d["fp64"])
-    for prec, bound in (("fp32", 0.01), ("fp16s", 0.12), ("fp16s+sr", 0.01), ("bf16s+sr", 0.02)):
-        assert np.all(np.abs(d[prec] / d["fp64"] - 1) <= bound), (prec, d[prec], d["fp64"])
+    for prec in ("fp32", "fp16s+sr", "bf16s+sr"):
+        assert np.all(np.abs(d[prec] / d["fp64"] - 1) <= 0.01), (prec, d[prec], d["fp64"])
+    for prec in ("fp16s", "bf16s"):  # rounded to nearest: a known miss, checked as such
+        assert np.max(np.abs(d[prec] / d["fp64"] - 1)) > 0.01, (prec, d[prec], d["fp64"])
 
 
 # -------------------------------------------------------------------------------------------
@@ -276,9 +336,9 @@ def test_staged_kernel_refused_with_stochastic_rounding(lbm):
 def test_sheared_droplet_stochastic_rounding_against_oracle(lbm, orc, prec):
     """The parity suite's sheared droplet (128 x 64, walls at +-0.01, R = 16, nu_l = 0.2, contrast
     10) after 1000 steps against the FP64 oracle, with the 16-bit storage rounded stochastically.
-    FP16: 5.0e-4 (1.0e-3 rounded to nearest), bound 2e-3.  BF16: 3.7e-3 (3.9e-3 to nearest): the
-    maximum difference is then set by BF16's own rounding noise (a unit of ~1.5e-5 on every stored
-    deviation each step), not by a bias, so stochastic rounding leaves it; bound 5e-3."""
+    FP16: 3.5e-4 (1.5e-4 rounded to nearest), within the 2e-3 contract.  BF16: 3.7e-3 (1.25e-3 to
+    nearest): the maximum difference is then set by BF16's own rounding noise (a unit of ~1.5e-5
+    on every stored deviation each step), not by a bias; held at 5e-3 as a regression guard."""
     phi0 = W.droplet(128, 64, 16, gamma=0.04, a=0.04)
     kw = dict(tau_l=tau(0.2), tau_g=tau(0.02), bc=1, u_top=0.01, u_bottom=-0.01)
     o = orc.Oracle(phi0, **oracle_kwargs(kw))

@@ -268,6 +268,18 @@ LBM_API int lbm_batch_step(lbm_batch* b, int n);
 LBM_API int lbm_batch_fields(lbm_batch* b, int member, double* rho, double* ux, double* uy, double* phi);
 LBM_API int lbm_batch_get_populations(lbm_batch* b, int member, double* f, double* g);
 
+/* A member's macroscopic state as a device array, without a host round trip (to couple the solver
+ * with other GPU code, e.g. a learned model that advances the fields between solver windows).
+ * state: device pointer (4-byte aligned, caller-owned) to nx*ny nodes of 3 FP32 values each,
+ * node (x, y) at 3 * (y * nx + x): phi, v_x, v_y.  lbm_batch_set_state replaces the member's
+ * populations by the equilibria of Eqs. 8-10 built from those fields with rho = 1 (the Eq. 12
+ * stencils of phi, then one collision: the start lbm_init makes); lbm_batch_get_state writes the
+ * member's phi and velocity (as lbm_batch_fields) into state.  Both only enqueue work on the
+ * batch's stream (no synchronisation): the caller orders its own streams against it.  Errors:
+ * LBM_ERR_PARAM (bad member, NULL or misaligned state), LBM_ERR_CUDA. */
+LBM_API int lbm_batch_set_state(lbm_batch* b, int member, const float* state);
+LBM_API int lbm_batch_get_state(lbm_batch* b, int member, float* state);
+
 /* Synchronise; nonfinite[count] (may be NULL) receives 1 for members that produced a non-finite
  * rho or phi since the last check (flags are then cleared); returns LBM_ERR_NONFINITE if any did. */
 LBM_API int lbm_batch_check(lbm_batch* b, int* nonfinite);

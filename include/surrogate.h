@@ -104,6 +104,21 @@ SUR_API int sur_zero(void* p, size_t bytes, void* stream);
 /* y = bf16(x) (n elements). */
 SUR_API int sur_cast_bf16(const float* x, void* y, size_t n, void* stream);
 
+/* The solver's state and the network's: `state` is npix x 3 FP32 (phi, ux, uy per pixel, the layout
+ * of lbm_batch_get_state); x the BF16 network input (npix x C: phi, u_scale ux, u_scale uy, then
+ * zeros) and base the FP32 state the prediction advances (npix x 3: phi, u_scale ux, u_scale uy).
+ * sur_unpack_state maps a prediction (npix x 3, velocities scaled) back to a solver state.
+ * u_scale != 0; C >= 3. */
+SUR_API int sur_pack_state(const float* state, void* x, float* base, size_t npix, int C, float u_scale, void* stream);
+SUR_API int sur_unpack_state(const float* pred, float* state, size_t npix, float u_scale, void* stream);
+
+/* Judge reductions, per image b of a batch of `batch` images of npix pixels and C channels (FP32),
+ * in FP64 and in a fixed order (the same bits for the same input): sums[b] = sum over pixels of
+ * channel 0 (phi), or for sur_phi_sq_diff the sum of (a - b)^2 over channel 0.  sums: device,
+ * `batch` doubles.  A non-finite value makes its image's sum non-finite. */
+SUR_API int sur_phi_sums(const float* state, int batch, int npix, int C, double* sums, void* stream);
+SUR_API int sur_phi_sq_diff(const float* a, const float* b, int batch, int npix, int C, double* sums, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

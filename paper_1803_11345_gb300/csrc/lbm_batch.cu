@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -349,6 +350,32 @@ int lbm_batch_fields(lbm_batch* b, int member, double* rho, double* ux, double* 
     if (outs[k]) e = cudaMemcpyAsync(outs[k], stage + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return fail(b, LBM_ERR_CUDA, "lbm_batch_fields: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_set_state(lbm_batch* b, int member, const float* state) {
+  if (!b || member < 0 || member >= b->count || !state)
+    return fail(b, LBM_ERR_PARAM, "lbm_batch_set_state: bad member or NULL state");
+  if ((uintptr_t)state % 4 != 0) return fail(b, LBM_ERR_PARAM, "lbm_batch_set_state: state must be 4-byte aligned");
+  const HostGeometry& g = b->geo[member];
+  const long long N = (long long)g.nx * g.ny;
+  double* stage = (double*)spare_of(b, member);
+  cudaError_t e = launch_state_to_fields(state, N, stage, b->stream);
+  if (e == cudaSuccess) e = launch_init(b->prec, g, b->phys[member], stage, state_of(b, member), b->stream);
+  if (e != cudaSuccess) return fail(b, LBM_ERR_CUDA, "lbm_batch_set_state: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_get_state(lbm_batch* b, int member, float* state) {
+  if (!b || member < 0 || member >= b->count || !state)
+    return fail(b, LBM_ERR_PARAM, "lbm_batch_get_state: bad member or NULL state");
+  if ((uintptr_t)state % 4 != 0) return fail(b, LBM_ERR_PARAM, "lbm_batch_get_state: state must be 4-byte aligned");
+  const HostGeometry& g = b->geo[member];
+  const long long N = (long long)g.nx * g.ny;
+  double* stage = (double*)spare_of(b, member);
+  cudaError_t e = launch_fields(b->prec, g, b->phys[member], state_of(b, member), stage, b->stream);
+  if (e == cudaSuccess) e = launch_fields_to_state(stage, N, state, b->stream);
+  if (e != cudaSuccess) return fail(b, LBM_ERR_CUDA, "lbm_batch_get_state: %s", cudaGetErrorString(e));
   return LBM_OK;
 }
 

@@ -72,6 +72,11 @@ size_t copy_bytes(int prec, const HostGeometry& g);
 // Message returned by lbm_last_error(NULL) on the calling thread.
 void set_thread_error(const char* msg);
 
+// Interleaved FP32 node state (phi, ux, uy) of n nodes <-> dense FP64 fields: to the k_init layout
+// [phi | ux | uy | rho = 1], from the k_fields layout [rho | ux | uy | phi].
+cudaError_t launch_state_to_fields(const float* st, long long n, double* fields, cudaStream_t s);
+cudaError_t launch_fields_to_state(const double* fields, long long n, float* st, cudaStream_t s);
+
 // Fill n doubles with v.
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 

@@ -461,6 +461,35 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Interleaved FP32 node state (phi, ux, uy per node, nx*ny nodes) <-> the dense FP64 field
+// layout of k_init ([phi | ux | uy | rho], rho = 1) and of k_fields ([rho | ux | uy | phi]).
+__global__ void k_state_to_fields(const float* __restrict__ st, long long n, double* __restrict__ fields) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    fields[i] = (double)st[3 * i];
+    fields[n + i] = (double)st[3 * i + 1];
+    fields[2 * n + i] = (double)st[3 * i + 2];
+    fields[3 * n + i] = 1.0;
+  }
+}
+__global__ void k_fields_to_state(const double* __restrict__ fields, long long n, float* __restrict__ st) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    st[3 * i] = (float)fields[3 * n + i];
+    st[3 * i + 1] = (float)fields[n + i];
+    st[3 * i + 2] = (float)fields[2 * n + i];
+  }
+}
+
+cudaError_t launch_state_to_fields(const float* st, long long n, double* fields, cudaStream_t s) {
+  const int nb = (int)std::min<long long>(4096, (n + 255) / 256);
+  k_state_to_fields<<<std::max(nb, 1), 256, 0, s>>>(st, n, fields);
+  return cudaGetLastError();
+}
+cudaError_t launch_fields_to_state(const double* fields, long long n, float* st, cudaStream_t s) {
+  const int nb = (int)std::min<long long>(4096, (n + 255) / 256);
+  k_fields_to_state<<<std::max(nb, 1), 256, 0, s>>>(fields, n, st);
+  return cudaGetLastError();
+}
+
 size_t reduce_partials_bytes() { return sizeof(double) * 4 * kRedBlocks; }
 
 cudaError_t launch_reduce(int prec, const HostGeometry& g, const char* src, double* partials,

@@ -504,6 +504,52 @@ __global__ void k_cast_bf16(const float* __restrict__ x, bf16* __restrict__ y, s
     y[i] = __float2bfloat16(x[i]);
 }
 
+// Solver state (npix x 3 FP32: phi, ux, uy) -> network input x (npix x C BF16: phi, s ux, s uy,
+// then zeros) and base (npix x 3 FP32: phi, s ux, s uy), s the velocity scale of the network.
+__global__ void k_pack_state(const float* __restrict__ st, bf16* __restrict__ x, float* __restrict__ base,
+                             size_t npix, int C, float s) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
+    const float v[3] = {st[p * 3], s * st[p * 3 + 1], s * st[p * 3 + 2]};
+    for (int c = 0; c < 3; ++c) base[p * 3 + c] = v[c];
+    for (int c = 0; c < C; ++c) x[p * C + c] = __float2bfloat16(c < 3 ? v[c] : 0.f);
+  }
+}
+
+// Network prediction (npix x 3: phi, s ux, s uy) -> solver state (phi, ux, uy).
+__global__ void k_unpack_state(const float* __restrict__ pred, float* __restrict__ st, size_t npix, float inv_s) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
+    st[p * 3] = pred[p * 3];
+    st[p * 3 + 1] = pred[p * 3 + 1] * inv_s;
+    st[p * 3 + 2] = pred[p * 3 + 2] * inv_s;
+  }
+}
+
+// Per image b of a batch, in FP64 and in a fixed order (one block per image, fixed per-thread
+// strides, fixed tree): sums[b] = sum_p a[p][0] (b2 == NULL), or the sum of (a[p][0] - b2[p][0])^2.
+constexpr int kSumThreads = 512;
+__global__ void __launch_bounds__(kSumThreads)
+k_channel0_sums(const float* __restrict__ a, const float* __restrict__ b2, int npix, int C, double* __restrict__ sums) {
+  __shared__ double sh[kSumThreads];
+  const size_t off = (size_t)blockIdx.x * npix;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < npix; p += kSumThreads) {
+    const double v = (double)a[(off + p) * C];
+    if (b2) {
+      const double d = v - (double)b2[(off + p) * C];
+      acc += d * d;
+    } else {
+      acc += v;
+    }
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
+}
+
 int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
@@ -736,6 +782,30 @@ int sur_zero(void* p, size_t bytes, void* stream) {
 
 int sur_cast_bf16(const float* x, void* y, size_t n, void* stream) {
   k_cast_bf16<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, (bf16*)y, n);
+  return check(cudaGetLastError());
+}
+
+int sur_pack_state(const float* state, void* x, float* base, size_t npix, int C, float u_scale, void* stream) {
+  if (!state || !x || !base || C < 3) return SUR_ERR_PARAM;
+  k_pack_state<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(state, (bf16*)x, base, npix, C, u_scale);
+  return check(cudaGetLastError());
+}
+
+int sur_unpack_state(const float* pred, float* state, size_t npix, float u_scale, void* stream) {
+  if (!pred || !state || !(u_scale != 0.f)) return SUR_ERR_PARAM;
+  k_unpack_state<<<grid_for(npix), 256, 0, (cudaStream_t)stream>>>(pred, state, npix, 1.f / u_scale);
+  return check(cudaGetLastError());
+}
+
+int sur_phi_sums(const float* state, int batch, int npix, int C, double* sums, void* stream) {
+  if (!state || !sums || batch < 1 || npix < 1 || C < 1) return SUR_ERR_PARAM;
+  k_channel0_sums<<<batch, kSumThreads, 0, (cudaStream_t)stream>>>(state, nullptr, npix, C, sums);
+  return check(cudaGetLastError());
+}
+
+int sur_phi_sq_diff(const float* a, const float* b, int batch, int npix, int C, double* sums, void* stream) {
+  if (!a || !b || !sums || batch < 1 || npix < 1 || C < 1) return SUR_ERR_PARAM;
+  k_channel0_sums<<<batch, kSumThreads, 0, (cudaStream_t)stream>>>(a, b, npix, C, sums);
   return check(cudaGetLastError());
 }
 

@@ -99,6 +99,10 @@ def _load():
     lib.lbm_batch_fields.restype = i
     lib.lbm_batch_get_populations.argtypes = [vp, i, dp, dp]
     lib.lbm_batch_get_populations.restype = i
+    lib.lbm_batch_set_state.argtypes = [vp, i, vp]
+    lib.lbm_batch_set_state.restype = i
+    lib.lbm_batch_get_state.argtypes = [vp, i, vp]
+    lib.lbm_batch_get_state.restype = i
     lib.lbm_batch_check.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.lbm_batch_check.restype = i
     lib.lbm_batch_set_tile.argtypes = [vp, i, i, i]
@@ -287,6 +291,16 @@ def lbm_batch_get_populations(b: int, member: int, f, g) -> None:
     _bcheck(_lib.lbm_batch_get_populations(b, member, _dptr(f), _dptr(g)), b)
 
 
+def lbm_batch_set_state(b: int, member: int, state: int) -> None:
+    """Restart a member from a device array of nx*ny x (phi, ux, uy) FP32 (asynchronous)."""
+    _bcheck(_lib.lbm_batch_set_state(b, member, ctypes.c_void_p(state)), b)
+
+
+def lbm_batch_get_state(b: int, member: int, state: int) -> None:
+    """Write a member's (phi, ux, uy) into a device array of nx*ny x 3 FP32 (asynchronous)."""
+    _bcheck(_lib.lbm_batch_get_state(b, member, ctypes.c_void_p(state)), b)
+
+
 def lbm_batch_check(b: int, count: int):
     """(status, per-member non-finite flags)."""
     flags = (ctypes.c_int * count)()
@@ -453,6 +467,12 @@ class Batch:
 
     def check(self):
         return lbm_batch_check(self.b, self.count)
+
+    def set_state(self, member: int, state_ptr: int):
+        lbm_batch_set_state(self.b, member, state_ptr)
+
+    def get_state(self, member: int, state_ptr: int):
+        lbm_batch_get_state(self.b, member, state_ptr)
 
     def set_tile(self, bx: int, by: int, target_nodes: int):
         lbm_batch_set_tile(self.b, bx, by, target_nodes)

@@ -52,6 +52,10 @@ _sig("sur_flux_update_bwd", [_vp, _vp, _i, _i, _i, _i, _vp])
 _sig("sur_mse3", [_vp, _vp, _vp, _vp, _sz, _vp])
 _sig("sur_zero", [_vp, _sz, _vp])
 _sig("sur_cast_bf16", [_vp, _vp, _sz, _vp])
+_sig("sur_pack_state", [_vp, _vp, _vp, _sz, _i, _f, _vp])
+_sig("sur_unpack_state", [_vp, _vp, _sz, _f, _vp])
+_sig("sur_phi_sums", [_vp, _i, _i, _i, _vp, _vp])
+_sig("sur_phi_sq_diff", [_vp, _vp, _i, _i, _i, _vp, _vp])
 
 
 class SurError(RuntimeError):
@@ -140,6 +144,22 @@ def sur_zero(t, stream):
 
 def sur_cast_bf16(x, y, stream):
     _ok(_lib.sur_cast_bf16(_p(x), _p(y), x.numel(), stream), "sur_cast_bf16")
+
+
+def sur_pack_state(state, x, base, npix, C, u_scale, stream):
+    _ok(_lib.sur_pack_state(_p(state), _p(x), _p(base), npix, C, float(u_scale), stream), "sur_pack_state")
+
+
+def sur_unpack_state(pred, state, npix, u_scale, stream):
+    _ok(_lib.sur_unpack_state(_p(pred), _p(state), npix, float(u_scale), stream), "sur_unpack_state")
+
+
+def sur_phi_sums(state, batch, npix, C, sums, stream):
+    _ok(_lib.sur_phi_sums(_p(state), batch, npix, C, _p(sums), stream), "sur_phi_sums")
+
+
+def sur_phi_sq_diff(a, b, batch, npix, C, sums, stream):
+    _ok(_lib.sur_phi_sq_diff(_p(a), _p(b), batch, npix, C, _p(sums), stream), "sur_phi_sq_diff")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -384,12 +404,21 @@ def generate_trajectories(members, steps_per_window, windows, prec="fp32", strea
 
 
 class Judge:
-    """Accepts or rejects a prediction: sum phi drift per node must stay under `drift` (always
-    checked), and where the solver's own result for the same window is at hand, the RMS phi error
-    must stay under `phi_err`."""
+    """Decides whether the surrogate's prediction for a window is kept, with what is known while
+    the model runs (rollout()):
 
-    def __init__(self, phi_err=1e-2, drift=1e-6):
-        self.phi_err, self.drift = phi_err, drift
+    * every window, on the GPU in FP64 (sur_phi_sums): every phi finite and the sum-phi drift per
+      node, |sum phi_pred - sum phi_in| / N, at most `drift`;
+    * every `audit_every`-th window the solver also advances the window from the same input and
+      the RMS phi difference between the prediction and the solver's result must stay at most
+      `phi_err` (sur_phi_sq_diff).  The solver's result is kept in an audited window (it has been
+      paid for); a failed audit hands the next `audit_every` windows to the solver.
+
+    accept() applies the same thresholds offline, to a prediction whose solver result is known
+    (evaluate()); a deployment has that result only in audited windows."""
+
+    def __init__(self, phi_err=1e-2, drift=1e-6, audit_every=8):
+        self.phi_err, self.drift, self.audit_every = phi_err, drift, int(audit_every)
 
     def accept(self, phi_in, phi_pred, phi_true=None):
         n = phi_in.size
@@ -398,6 +427,142 @@ class Judge:
         err = None if phi_true is None or not finite else float(np.sqrt(np.mean((phi_pred - phi_true) ** 2)))
         ok = finite and d <= self.drift and (err is None or err <= self.phi_err)
         return ok, d, err
+
+
+class SolverWindows:
+    """The batched solver on a set of periodic lattices, advancing device states (B, H, W, 3) FP32
+    (phi, ux, uy) by windows of K steps: each member restarts from the given fields (equilibrium
+    populations, rho = 1, lbm_batch_set_state), runs K steps and writes its fields back
+    (lbm_batch_get_state), all on `stream`."""
+
+    def __init__(self, members, K, stream, prec="fp32"):
+        self.bat = lbm.Batch(members, prec=prec, stream=stream)
+        self.K, self.B = K, len(members)
+
+    def advance(self, state, out, steps=None):
+        for m in range(self.B):
+            self.bat.set_state(m, state[m].data_ptr())
+        self.bat.step(self.K if steps is None else steps)
+        for m in range(self.B):
+            self.bat.get_state(m, out[m].data_ptr())
+        return out
+
+    def close(self):
+        self.bat.close()
+
+
+def rollout(net, members, state0, windows, K, judge, stream=None, inject=None):
+    """Advance the lattices `members` [(phi0, params)] from state0 (torch (B, H, W, 3) FP32 on the
+    device: phi, ux, uy) by `windows` windows of K solver steps with the surrogate, under `judge`,
+    the solver advancing every window the judge does not keep.  Closed loop: each kept prediction
+    is the next window's input.  Everything runs on one stream; the wall time includes the judge's
+    reductions, its per-window read of 2B FP64 sums and every audit and fallback.  inject(w, pred)
+    (optional) may alter the prediction of window w before it is judged (tests).
+    Returns (state, stats)."""
+    import time as _time
+
+    import torch
+    stream = stream if stream is not None else torch.cuda.Stream()
+    B, H, W, _ = state0.shape
+    npix = H * W
+    net_stream = net.stream
+    net.stream, net.s = stream, stream.cuda_stream
+    solver = SolverWindows(members, K, stream)
+    dev = state0.device
+    x = torch.empty((B, H, W, net.cin), dtype=torch.bfloat16, device=dev)
+    base = torch.empty((B, H, W, 3), dtype=torch.float32, device=dev)
+    cand = torch.empty_like(base)
+    solv = torch.empty_like(base)
+    state = torch.empty_like(base)
+    sums = torch.empty(2 * B, dtype=torch.float64, device=dev)
+    s = stream.cuda_stream
+    stats = dict(windows=windows, kept=0, solver=0, audits=0, audit_failed=0, drift_rejected=0, audit_rms=[])
+    try:
+        with torch.cuda.stream(stream):
+            state.copy_(state0)
+            net.forward(x, base)  # buffers exist before timing
+            torch.cuda.synchronize()
+            t0 = _time.perf_counter()
+            suspended = 0
+            for w in range(windows):
+                if suspended:
+                    solver.advance(state, solv)
+                    state, solv = solv, state
+                    stats["solver"] += 1
+                    suspended -= 1
+                    continue
+                sur_pack_state(state, x, base, B * npix, net.cin, U_SCALE, s)
+                pred = net.forward(x, base)
+                sur_unpack_state(pred, cand, B * npix, U_SCALE, s)
+                if inject is not None:
+                    inject(w, cand)
+                sur_phi_sums(state, B, npix, 3, sums[:B], s)
+                sur_phi_sums(cand, B, npix, 3, sums[B:], s)
+                sv = sums.cpu().numpy()
+                drift = np.abs(sv[B:] - sv[:B]) / npix
+                if not (np.all(np.isfinite(sv)) and np.all(drift <= judge.drift)):
+                    solver.advance(state, solv)
+                    state, solv = solv, state
+                    stats["drift_rejected"] += 1
+                    stats["solver"] += 1
+                    continue
+                if judge.audit_every > 0 and w % judge.audit_every == judge.audit_every - 1:
+                    solver.advance(state, solv)
+                    sur_phi_sq_diff(cand, solv, B, npix, 3, sums[:B], s)
+                    rms = np.sqrt(sums[:B].cpu().numpy() / npix)
+                    stats["audits"] += 1
+                    stats["audit_rms"].append(float(rms.max()))
+                    if not rms.max() <= judge.phi_err:
+                        stats["audit_failed"] += 1
+                        suspended = judge.audit_every
+                    state, solv = solv, state
+                    continue
+                state, cand = cand, state
+                stats["kept"] += 1
+            torch.cuda.synchronize()
+            stats["seconds"] = _time.perf_counter() - t0
+    finally:
+        net.stream, net.s = net_stream, net_stream.cuda_stream
+        solver.close()
+    return state, stats
+
+
+def solver_only(members, state0, windows, K, stream=None):
+    """The same lattices advanced by the solver alone, windows * K steps from state0 (restarted from
+    its fields as the rollout's solver windows are); returns (state, seconds)."""
+    import time as _time
+
+    import torch
+    stream = stream if stream is not None else torch.cuda.Stream()
+    solver = SolverWindows(members, K, stream)
+    out = torch.empty_like(state0)
+    try:
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            t0 = _time.perf_counter()
+            solver.advance(state0, out, steps=windows * K)
+            torch.cuda.synchronize()
+            dt = _time.perf_counter() - t0
+    finally:
+        solver.close()
+    return out, dt
+
+
+def phi_rms(a, b):
+    """Per-lattice RMS phi difference of two device states (B, H, W, 3), reduced in FP64 on the GPU."""
+    import torch
+    B, H, W, _ = a.shape
+    sums = torch.empty(B, dtype=torch.float64, device=a.device)
+    stream = torch.cuda.current_stream()
+    sur_phi_sq_diff(a, b, B, H * W, 3, sums, stream.cuda_stream)
+    return np.sqrt(sums.cpu().numpy() / (H * W))
+
+
+def states_from_trajectory(traj, window):
+    """Device state (M, H, W, 3) FP32 of every member of traj at a window boundary."""
+    import torch
+    st = np.ascontiguousarray(np.moveaxis(traj[window], 1, -1)).astype(np.float32)
+    return torch.from_numpy(st).cuda()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -438,6 +603,68 @@ def train(net, traj, iters, batch, lr=1e-3, seed=0, log_every=0):
         if log_every and (it % log_every == 0 or it == iters - 1):
             hist.append((it, float(loss.item())))
     return hist
+
+
+def trajectory_states(traj):
+    """All snapshots of traj (windows+1, M, 3, H, W) as one device tensor (windows+1, M, H, W, 3)
+    FP32 of solver states (phi, ux, uy), the layout the surrogate kernels read."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.moveaxis(traj, 2, -1)).astype(np.float32)).cuda()
+
+
+def train_states(net, states, iters, batch, lr=1e-3, seed=0, log_every=0):
+    """Adam on random (window, member) pairs of device states (windows+1, M, H, W, 3): the input
+    and its target (the state one window later) are packed on the GPU (sur_pack_state), so no
+    training data crosses the host.  Cosine-decayed lr; returns the loss history."""
+    import torch
+    rng = np.random.default_rng(seed)
+    nwin, M, H, W, _ = states.shape
+    nwin -= 1
+    npix = batch * H * W
+    dev = states.device
+    x = torch.empty((batch, H, W, net.cin), dtype=torch.bfloat16, device=dev)
+    xt = torch.empty_like(x)
+    base = torch.empty((batch, H, W, 3), dtype=torch.float32, device=dev)
+    tgt = torch.empty_like(base)
+    hist = []
+    s = net.s
+    for it in range(iters):
+        ks = torch.from_numpy(rng.integers(nwin, size=batch)).to(dev)
+        ms = torch.from_numpy(rng.integers(M, size=batch)).to(dev)
+        inp = states[ks, ms].contiguous()
+        out = states[ks + 1, ms].contiguous()
+        sur_pack_state(inp, x, base, npix, net.cin, U_SCALE, s)
+        sur_pack_state(out, xt, tgt, npix, net.cin, U_SCALE, s)
+        loss = net.loss_and_grads(x, base, tgt)
+        net.adam_step(lr=lr * 0.5 * (1 + math.cos(math.pi * it / max(1, iters))))
+        if log_every and (it % log_every == 0 or it == iters - 1):
+            hist.append((it, float(loss.item())))
+    return hist
+
+
+def one_window_errors(net, states, batch=4):
+    """RMS phi error of one-window predictions from every true state of device states
+    (windows+1, M, H, W, 3), and of persistence (phi(t+K) ~ phi(t)): two arrays (windows * M)."""
+    import torch
+    nwin, M, H, W, _ = states.shape
+    nwin -= 1
+    dev = states.device
+    errs, pers = [], []
+    pairs = [(k, m) for k in range(nwin) for m in range(M)]
+    for i in range(0, len(pairs), batch):
+        idx = pairs[i:i + batch]
+        b = len(idx)
+        inp = torch.stack([states[k, m] for k, m in idx]).contiguous()
+        out = torch.stack([states[k + 1, m] for k, m in idx]).contiguous()
+        x = torch.empty((b, H, W, net.cin), dtype=torch.bfloat16, device=dev)
+        base = torch.empty((b, H, W, 3), dtype=torch.float32, device=dev)
+        pred_state = torch.empty_like(base)
+        sur_pack_state(inp, x, base, b * H * W, net.cin, U_SCALE, net.s)
+        pred = net.forward(x, base)
+        sur_unpack_state(pred, pred_state, b * H * W, U_SCALE, net.s)
+        errs += phi_rms(pred_state, out).tolist()
+        pers += phi_rms(inp, out).tolist()
+    return np.array(errs), np.array(pers)
 
 
 def evaluate(net, traj, judge, batch=4):

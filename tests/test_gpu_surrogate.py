@@ -221,3 +221,84 @@ def test_graph_replayed_forward_equals_eager(S):
         torch.cuda.synchronize()
         assert torch.equal(got, want)
     assert net.launches_per_forward() == 2 * 3 + 2 + 4 + 2
+
+
+# -------------------------------------------------------------------------------------------
+# The surrogate as used: trained on the solver's own trajectories, advancing lattices window by
+# window under the judge, with the solver as audit and fallback.
+
+@pytest.fixture(scope="module")
+def trained(S):
+    """A U-Net (32/64/128/256 channels) trained for 800 Adam steps on 12 solver trajectories of
+    256^2 periodic spinodal decomposition (viscosity ratio 10, 30 windows of K = 50 steps), and 8
+    held-out trajectories of the same workload."""
+    import torch
+    ntr, nte, wins, K = 12, 8, 30, 50
+    members = S.spinodal_members(ntr + nte, 256, seed=100)
+    traj = S.generate_trajectories(members, K, wins)
+    states = S.trajectory_states(traj)
+    del traj
+    net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
+    S.train_states(net, states[:, :ntr], 800, 8, lr=1e-3, seed=2)
+    torch.cuda.synchronize()
+    return dict(net=net, states=states, test_members=members[ntr:], ntr=ntr, K=K)
+
+
+def test_trained_network_beats_persistence(S, trained):
+    """On held-out trajectories the trained network's one-window phi error (median over every
+    window and lattice) is well below that of persistence (phi(t+K) ~ phi(t)): it has learned the
+    dynamics, not the identity (measured 1.7e-4 against 8.6e-4)."""
+    e, p = S.one_window_errors(trained["net"], trained["states"][:, trained["ntr"]:])
+    print("one-window phi RMS error: median", float(np.median(e)), "persistence", float(np.median(p)))
+    assert np.median(e) < 0.5 * np.median(p), (np.median(e), np.median(p))
+
+
+def test_judged_rollout_against_the_solver(S, trained):
+    """Closed loop: 8 held-out lattices advanced by 16 windows (800 steps) from step 500, each
+    kept prediction feeding the next window, the judge checking every window's sum-phi drift on
+    the GPU and auditing every 8th window with the solver.  Every window is accounted for (kept,
+    audited or handed to the solver), and the final phi stays within 1e-2 RMS of the solver run
+    alone from the same state (measured ~1.3e-3; doing nothing would be 1.3e-2 off).  The wall
+    times of both are printed with their ratio."""
+    net, K = trained["net"], trained["K"]
+    st0 = trained["states"][10, trained["ntr"]:].contiguous()
+    judge = S.Judge(phi_err=1e-2, drift=1e-6, audit_every=8)
+    S.rollout(net, trained["test_members"], st0, 2, K, judge)  # warm-up (graphs, buffers)
+    fin, stats = S.rollout(net, trained["test_members"], st0, 16, K, judge)
+    ref, t_solver = S.solver_only(trained["test_members"], st0, 16, K)
+    err = S.phi_rms(fin, ref)
+    pers = S.phi_rms(st0, ref)
+    print("rollout:", {k: v for k, v in stats.items()}, "solver alone %.4f s" % t_solver,
+          "speed-up %.3f" % (t_solver / stats["seconds"]), "final phi RMS", err.tolist(), "persistence", pers.tolist())
+    assert stats["kept"] + stats["solver"] + stats["audits"] == stats["windows"] == 16
+    assert stats["audits"] == 2 and stats["audit_failed"] == 0 and stats["drift_rejected"] == 0, stats
+    assert max(stats["audit_rms"]) <= 1e-2
+    assert err.max() <= 1e-2, err
+    assert err.max() < 0.5 * np.median(pers), (err, pers)
+
+
+def test_judge_rejects_a_drifting_prediction_and_falls_back_exactly(S, trained):
+    """A prediction made to create order parameter (0.1 added to every phi of one lattice: a drift
+    of 0.1 per node against the 1e-6 threshold) is rejected by the judge's FP64 sum check, and the
+    window is advanced by the solver instead: the state after that window equals, bit for bit, the
+    solver's own advance of the window's input."""
+    import torch
+    net, K = trained["net"], trained["K"]
+    members = trained["test_members"][:4]
+    st0 = trained["states"][10, trained["ntr"]:trained["ntr"] + 4].contiguous()
+    judge = S.Judge(phi_err=1e-2, drift=1e-6, audit_every=0)
+    mid, stats1 = S.rollout(net, members, st0, 1, K, judge)
+    assert stats1["kept"] == 1
+
+    def inject(w, pred):
+        if w == 1:
+            pred[2, ..., 0] += 0.1
+
+    fin, stats = S.rollout(net, members, st0, 2, K, judge, inject=inject)
+    assert stats["kept"] == 1 and stats["drift_rejected"] == 1 and stats["solver"] == 1, stats
+    solver = S.SolverWindows(members, K, torch.cuda.Stream())
+    want = torch.empty_like(mid)
+    solver.advance(mid, want)
+    torch.cuda.synchronize()
+    solver.close()
+    assert torch.equal(fin, want)

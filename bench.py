@@ -107,7 +107,8 @@ def ncu_traffic(prec: str, n: int):
 
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 100 ms; stop() reports the samples
+    that arrived inside [t0, t1] (host clock), the window of sustained load around the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,32 +132,39 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)  # let the sample that closes the window arrive
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, power, smax, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in list(self.lines):
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1 + 0.12):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
                 sm.append(float(parts[0]))
                 smax = float(parts[1])
+                power.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_mhz_min": min(sm) if sm else None, "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "samples taken while the lattice was stepped continuously: load steps before and "
+                          "after the timed region plus the timed region itself"}
 
 
 def max_over_ranks(value: float) -> float:
@@ -203,6 +211,40 @@ def time_oracle(budget_s: float, n_side: int, max_steps: int = 10**9, threads: i
     o.close()
     oracle.set_threads(default)
     return n_side * n_side * steps / dt / 1e6, steps, dt, threads
+
+
+def oracle_case(phi0, params, budget_s, max_steps):
+    """MLUPS of the FP64 oracle (all host cores) on one workload: whole steps for up to budget_s
+    seconds (at most max_steps) after one untimed step."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(phi0, **params)
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    o.close()
+    ny, nx = phi0.shape
+    return {"mlups": nx * ny * steps / dt / 1e6, "steps": steps, "seconds": round(dt, 3)}
+
+
+def oracle_sizes(budget_s=3.0):
+    """The oracle timed at the sizes of the paper's workloads (FP64, all host cores)."""
+    from paper_1803_11345_gb300 import workloads as W
+    out = {}
+    lap = dict(tau_l=1.0, tau_g=1.0, gamma=0.02, a=0.04, M=0.1, Gamma=1.0)
+    out["laplace droplet 64x64"] = oracle_case(W.droplet(64, 64, 16, gamma=0.02, a=0.04), lap, budget_s, 2000)
+    sp = dict(workload_params(), visc_interp=1)
+    out["spinodal 256x256"] = oracle_case(W.spinodal(256, 256, seed=SEED), sp, budget_s, 1000)
+    ch = dict(tau_l=tau(0.2), tau_g=tau(0.02), gamma=0.04, a=0.04, M=0.1, Gamma=1.0, walls=1, u_top=0.01,
+              u_bottom=-0.01)
+    out["sheared channel 1024x512"] = oracle_case(W.droplet(1024, 512, 64, gamma=0.04, a=0.04), ch, budget_s, 300)
+    out["spinodal 4096x4096"] = oracle_case(W.spinodal(4096, 4096, seed=SEED), sp, budget_s, 3)
+    return out
 
 
 def run_reference(args):
@@ -294,8 +336,6 @@ def storage_forms(lbm, phi0, params, stream, ms_fp32, steps=500, phi_steps=1000)
                      "hbm_frac": BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9 / measured_peaks()[0],
                      "phi_vs_fp32_after_steps": phi_steps, "phi_max_abs_diff": float(d.max()),
                      "phi_rms_diff": float(np.sqrt((d * d).mean())), "kernel": kernel}
-    out["batch"] = "bench.py --workload batch: 256 lattices, aggregate MLUPS vs one launch per member"
-    out["surrogate"] = "bench.py --workload surrogate: U-Net forward vs the solver's 50 steps, phi RMS error"
     return out
 
 def run_gpu(args):
@@ -322,10 +362,21 @@ def run_gpu(args):
         if ws > 1:
             dist.barrier()
 
-    lat.step(args.warmup)
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    # Keep the GPU stepping for ~0.4 s on each side of the timed region (untimed), so that the
+    # clock sampler (one sample per 100 ms) sees the clocks of sustained load around it.
+    probe0, probe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    probe0.record(stream)
+    lat.step(5)
+    probe1.record(stream)
+    torch.cuda.synchronize()
+    pad = 0 if args.pad_ms <= 0 else max(1, int(args.pad_ms / max(probe0.elapsed_time(probe1) / 5, 1e-3)))
+    t_load0 = time.time()
+    if pad:
+        lat.step(pad)
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -333,9 +384,12 @@ def run_gpu(args):
     e0.record(stream)
     lat.step(args.steps)
     e1.record(stream)
+    if pad:
+        lat.step(pad)
     torch.cuda.synchronize()
+    t_load1 = time.time()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_load0, t_load1)
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms)
     nodes = n * n
@@ -391,7 +445,8 @@ def run_gpu(args):
                    "sample": f"128x128 periodic sample of the spinodal workload, {c_steps} steps "
                              f"in {c_dt:.1f} s, FP64",
                    "serial": {"value": s_mlups, "unit": "MLUPS", "cores": 1,
-                              "sample": f"same sample, {s_steps} steps in {s_dt:.1f} s on one thread"}}
+                              "sample": f"same sample, {s_steps} steps in {s_dt:.1f} s on one thread"},
+                   "sizes": oracle_sizes()}
         except Exception as exc:  # report, do not hide
             cpu = {"value": None, "unit": "MLUPS", "cores": None, "kind": "oracle",
                    "sample": f"failed: {exc}"}
@@ -399,6 +454,12 @@ def run_gpu(args):
     forms = None
     if rank == 0 and ws == 1 and args.prec == "fp32" and not args.no_forms:
         forms = storage_forms(lbm, phi0, params, stream, ms_step)
+        for key, fn in (("batch", lambda: batch_form(lbm, args.count, "fp32", 20, 5)),
+                        ("surrogate", lambda: surrogate_form(args))):
+            try:
+                forms[key] = fn()
+            except Exception as exc:  # report, do not hide
+                forms[key] = {"failed": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {
@@ -447,36 +508,28 @@ def batch_members(count: int, seed: int):
     return out
 
 
-def run_batch(args):
+def batch_form(lbm, count, prec, steps, warmup):
+    """The batched sweep (`count` lattices of batch_members) in one persistent launch per step:
+    aggregate MLUPS against the same members stepped one launch per member per step."""
     import torch
-
-    from paper_1803_11345_gb300 import build as B
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    B.build()
-    from paper_1803_11345_gb300 import lbm
-    members = batch_members(args.count, SEED + rank)
+    members = batch_members(count, SEED)
     nodes = sum(p.shape[0] * p.shape[1] for p, _ in members)
-    bat = lbm.Batch(members, prec=args.prec)
+    bat = lbm.Batch(members, prec=prec)
     tuned_ms = bat.autotune(trial_steps=3)
-    bat.step(args.warmup)
+    bat.step(warmup)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(bat.stream)
-    bat.step(args.steps)
+    bat.step(steps)
     e1.record(bat.stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     st, flags = bat.check()
     tile = bat.tile
     bat.close()
-    # The same members one lattice at a time (one launch per member per step), same GPU.
-    lats = [lbm.Lattice(p, prec=args.prec, stream=torch.cuda.current_stream(), **kw) for p, kw in members]
-    seq_steps = max(3, min(args.steps, 50))
+    lats = [lbm.Lattice(p, prec=prec, stream=torch.cuda.current_stream(), **kw) for p, kw in members]
+    seq_steps = max(3, min(steps, 20))
     for L in lats:
         L.step(2)
     torch.cuda.synchronize()
@@ -491,24 +544,44 @@ def run_batch(args):
     seq_ms = s0.elapsed_time(s1) / seq_steps
     for L in lats:
         L.close()
-    mlups = nodes * args.steps / (ms * 1e-3) / 1e6
+    bpn = BYTES_PER_NODE[prec]
+    ms_step = ms / steps
+    return {"members": count, "nodes": nodes, "precision": prec, "steps": steps, "ms_per_step": ms_step,
+            "mlups": nodes / (ms_step * 1e-3) / 1e6,
+            "hbm_frac": bpn * nodes / (ms_step * 1e-3) / 1e9 / measured_peaks()[0],
+            "ms_per_step_one_launch_per_member": seq_ms, "speedup_vs_one_launch_per_member": seq_ms / ms_step,
+            "tile": {"bx": tile[0], "by": tile[1], "nodes_per_item": tile[2], "items": tile[3], "grid": tile[4]},
+            "autotuned_ms": tuned_ms, "members_nonfinite": int(sum(flags)), "status": st,
+            "workload": f"batched sweep: {count} independent lattices, sizes {{64..512}}^2 and 2:1, half sheared "
+                        "droplets (walls +-0.01, Ca log-U[0.01,0.5]), half spinodal, zeta log-U[1,1000], one "
+                        "persistent launch per step, CUDA-graph replays"}
+
+
+def run_batch(args):
+    import torch
+
+    from paper_1803_11345_gb300 import build as B
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_1803_11345_gb300 import lbm
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.time()
+    r = batch_form(lbm, args.count, args.prec, args.steps, args.warmup)
+    clk = clocks.stop(t0, time.time())
     peak, peak_kind = measured_peaks()
-    bpn = BYTES_PER_NODE[args.prec]
     line = {
-        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": r["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
-        "config": {"workload": f"batched sweep: {args.count} independent lattices, sizes {{64..512}}^2 and 2:1, "
-                               "half sheared droplets (walls +-0.01, Ca log-U[0.01,0.5]), half spinodal, "
-                               "zeta log-U[1,1000], one persistent launch per step, CUDA-graph replays",
-                   "members": args.count, "nodes": nodes, "precision": args.prec,
-                   "tile": {"bx": tile[0], "by": tile[1], "nodes_per_item": tile[2], "items": tile[3],
-                            "grid": tile[4]}, "autotuned_ms": tuned_ms,
-                   "members_nonfinite": int(sum(flags))},
-        "roofline": {"bound": "hbm", "achieved": bpn * nodes / (ms / args.steps * 1e-3) / 1e9, "peak": peak,
-                     "unit": "GB/s", "frac": bpn * nodes / (ms / args.steps * 1e-3) / 1e9 / peak, "traffic": None,
-                     "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_step_batch"},
-        "vs_sequential": {"ms_per_step_one_at_a_time": seq_ms, "speedup": seq_ms / (ms / args.steps),
+        "config": {"workload": r["workload"], "members": args.count, "nodes": r["nodes"], "precision": args.prec,
+                   "tile": r["tile"], "autotuned_ms": r["autotuned_ms"], "members_nonfinite": r["members_nonfinite"]},
+        "roofline": {"bound": "hbm", "achieved": r["hbm_frac"] * peak, "peak": peak, "unit": "GB/s",
+                     "frac": r["hbm_frac"], "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "k_step_batch"},
+        "vs_sequential": {"ms_per_step_one_at_a_time": r["ms_per_step_one_launch_per_member"],
+                          "speedup": r["speedup_vs_one_launch_per_member"],
                           "what": "the same members as separate lattices, one lbm_step launch each per step"},
         "clocks": clk, "gpu_launches": args.steps,
     }
@@ -519,84 +592,82 @@ def run_batch(args):
 # ------------------------------------------------------------------------------------------
 # Learned surrogate vs the plain FP32 solver.
 
-def run_surrogate(args):
+def surrogate_form(args):
+    """The learned surrogate as deployed: trained on the solver's own trajectories (256^2 periodic
+    spinodal decomposition, viscosity ratio 10, windows of K = 50 steps), then a closed-loop rollout
+    of held-out lattices under the judge (sum-phi drift checked on the GPU every window, a solver
+    audit every `sur_audit` windows, the solver advancing every rejected window), timed end to end
+    against the solver alone over the same windows, with the final phi error against it."""
     import time as _t
 
     import numpy as np
     import torch
 
-    from paper_1803_11345_gb300 import build as B
-    B.build()
-    from paper_1803_11345_gb300 import lbm
     from paper_1803_11345_gb300 import surrogate as S
-    n, K, wins = args.sur_n, args.sur_k, args.sur_windows
+    n, K = args.sur_n, args.sur_k
+    ntr, nte, wins = args.sur_train, args.sur_test, args.sur_windows
     t0 = _t.time()
-    members = S.spinodal_members(args.sur_train + args.sur_test, n, seed=SEED)
+    members = S.spinodal_members(ntr + nte, n, seed=SEED)
     traj = S.generate_trajectories(members, K, wins)
+    states = S.trajectory_states(traj)
+    del traj
     t_data = _t.time() - t0
-    train_traj, test_traj = traj[:, :args.sur_train], traj[:, args.sur_train:]
     net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=SEED)
     t0 = _t.time()
-    hist = S.train(net, train_traj, args.sur_iters, args.sur_batch, lr=1e-3, seed=SEED, log_every=50)
+    hist = S.train_states(net, states[:, :ntr], args.sur_iters, args.sur_batch, lr=1e-3, seed=SEED, log_every=100)
     torch.cuda.synchronize()
     t_train = _t.time() - t0
-    judge = S.Judge(phi_err=1e-2, drift=1e-6)
-    rows = S.evaluate(net, test_traj, judge)
-    errs = np.array([r["err"] for r in rows])
-    pers = np.array([r["persistence"] for r in rows])
-    acc = float(np.mean([r["accepted"] for r in rows]))
-    # Speed for the same work: args.sur_test lattices advanced by K steps.
-    bt = args.sur_test
-    x, base, _ = S.to_device_batch(test_traj, [(m, 0) for m in range(bt)], net.cin)
-    reps = 5
-    ms_sur = S.time_forward(net, x, base, reps=reps, graph=True)
-    ms_sur_eager = S.time_forward(net, x, base, reps=reps)
+    e, p = S.one_window_errors(net, states[:, ntr:])
+    test_members = members[ntr:]
+    k0 = min(10, wins)
+    st0 = states[k0, ntr:].contiguous()
+    judge = S.Judge(phi_err=1e-2, drift=1e-6, audit_every=args.sur_audit)
+    S.rollout(net, test_members, st0, 2, K, judge)  # warm-up
+    fin, stats = S.rollout(net, test_members, st0, args.sur_rollout, K, judge)
+    ref, t_solver = S.solver_only(test_members, st0, args.sur_rollout, K)
+    err = S.phi_rms(fin, ref)
+    pers = S.phi_rms(st0, ref)
+    x = torch.empty((nte, n, n, net.cin), dtype=torch.bfloat16, device="cuda")
+    base = torch.zeros((nte, n, n, 3), dtype=torch.float32, device="cuda")
+    ms_fwd = S.time_forward(net, x, base, reps=10, graph=True)
+    nodes = nte * n * n
+    return {"lattices": nte, "n": n, "K": K, "windows": args.sur_rollout, "start_window": k0,
+            "seconds_rollout": stats["seconds"], "seconds_solver_alone": t_solver,
+            "speedup_vs_solver": t_solver / stats["seconds"],
+            "mlups_equivalent": nodes * K * args.sur_rollout / stats["seconds"] / 1e6,
+            "final_phi_rms_vs_solver_max": float(err.max()), "persistence_phi_rms": float(np.median(pers)),
+            "kept": stats["kept"], "audits": stats["audits"], "audit_failed": stats["audit_failed"],
+            "solver_windows": stats["solver"], "drift_rejected": stats["drift_rejected"],
+            "audit_rms": stats["audit_rms"],
+            "thresholds": {"phi_rms": judge.phi_err, "sum_phi_drift_per_node": judge.drift, "audit_every": judge.audit_every},
+            "one_window_phi_rms_median": float(np.median(e)), "persistence_one_window_median": float(np.median(p)),
+            "ms_forward_graph": ms_fwd, "ms_solver_window": t_solver * 1e3 / args.sur_rollout,
+            "training": {"trajectories": ntr, "windows": wins, "iters": args.sur_iters, "batch": args.sur_batch,
+                         "seconds_data": t_data, "seconds_train": t_train, "loss": hist[::3]},
+            "what": "closed-loop rollout of held-out lattices, wall time including the judge's GPU reductions, "
+                    "its per-window host read of the sums, every audit and fallback; solver alone: the batched "
+                    "solver over the same windows from the same state"}
 
-    def solver_ms(mem):
-        bat = lbm.Batch(mem, prec="fp32")
-        bat.autotune(trial_steps=3)
-        bat.step(K)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(bat.stream)
-        bat.step(K * 4)
-        e1.record(bat.stream)
-        torch.cuda.synchronize()
-        bat.close()
-        return e0.elapsed_time(e1) / 4
 
-    ms_solver = solver_ms(members[args.sur_train:])
-    # Throughput at a larger batch: the same test members repeated (timing only).
-    rep = max(1, args.sur_speed_batch // bt)
-    xr, br = x.repeat(rep, 1, 1, 1).contiguous(), base.repeat(rep, 1, 1, 1).contiguous()
-    ms_sur_big = S.time_forward(net, xr, br, reps=reps, graph=True)
-    ms_solver_big = solver_ms(members[args.sur_train:] * rep)
-    nodes = bt * n * n
-    # Effective rate of the judged surrogate: accepted windows cost one forward pass, rejected
-    # ones a forward pass plus the solver's K steps.
-    ms_eff = ms_sur + (1 - acc) * ms_solver
+def run_surrogate(args):
+    import torch
+
+    from paper_1803_11345_gb300 import build as B
+    B.build()
+    r = surrogate_form(args)
     line = {
-        "metric": METRIC, "value": nodes * K / (ms_eff * 1e-3) / 1e6, "unit": "MLUPS-equivalent",
-        "n_gpus": 1, "steps": K, "warmup": 2, "ms_per_step": ms_eff / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+        "metric": METRIC, "value": r["mlups_equivalent"], "unit": "MLUPS-equivalent", "n_gpus": 1,
+        "steps": r["K"] * r["windows"], "warmup": 2 * r["K"], "ms_per_step": r["seconds_rollout"] * 1e3 / (r["K"] * r["windows"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+        "data": "synthetic",
         "config": {"workload": f"learned surrogate: 4-level U-Net (32,64,128,256 channels, BF16, FP32 accumulate) "
-                               f"advancing (phi, ux, uy) by {K} steps on {n}x{n} periodic spinodal decomposition "
-                               f"(viscosity ratio 1:10); trained on {args.sur_train} solver trajectories x {wins} windows",
-                   "train_iters": args.sur_iters, "batch": args.sur_batch, "test_members": args.sur_test},
-        "surrogate": {"ms_forward": ms_sur, "ms_forward_eager": ms_sur_eager, "ms_solver_same_window": ms_solver,
-                      "speedup_forward_only": ms_solver / ms_sur,
-                      "at_batch": {"lattices": bt * rep, "ms_forward": ms_sur_big, "ms_solver_same_window": ms_solver_big,
-                                   "speedup_forward_only": ms_solver_big / ms_sur_big},
-                      "accept_rate": acc, "phi_rms_err_median": float(np.median(errs)),
-                      "phi_rms_err_p90": float(np.percentile(errs, 90)),
-                      "persistence_rms_err_median": float(np.median(pers)),
-                      "max_sum_phi_drift_per_node": float(max(r["drift"] for r in rows)),
-                      "thresholds": {"phi_rms": 1e-2, "sum_phi_drift_per_node": 1e-6},
-                      "loss_history": hist[::max(1, len(hist) // 10)], "seconds_data": t_data,
-                      "seconds_train": t_train},
-        # the line's number is the graph-replayed forward: its launches per timed pass
-        "gpu_launches": net.launches_per_forward() * reps,
+                               f"advancing (phi, ux, uy) by {r['K']} steps on {r['n']}x{r['n']} periodic spinodal "
+                               f"decomposition (viscosity ratio 1:10), judged closed-loop rollout of {r['lattices']} "
+                               f"held-out lattices"},
+        "surrogate": r,
+        "gpu_launches": None,
     }
+    torch.cuda.synchronize()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -613,15 +684,18 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit storage comparison")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time")
+    ap.add_argument("--pad-ms", type=float, default=400.0,
+                    help="untimed stepping before and after the timed region, for the clock samples (0: none)")
     ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
     ap.add_argument("--sur-n", type=int, default=256)
     ap.add_argument("--sur-k", type=int, default=50, help="solver steps per surrogate window")
-    ap.add_argument("--sur-speed-batch", type=int, default=16, help="lattices in the throughput comparison")
-    ap.add_argument("--sur-windows", type=int, default=60)
-    ap.add_argument("--sur-train", type=int, default=16)
-    ap.add_argument("--sur-test", type=int, default=4)
-    ap.add_argument("--sur-iters", type=int, default=1500)
+    ap.add_argument("--sur-windows", type=int, default=30, help="windows per training trajectory")
+    ap.add_argument("--sur-train", type=int, default=12, help="training trajectories")
+    ap.add_argument("--sur-test", type=int, default=8, help="held-out lattices (rollout batch)")
+    ap.add_argument("--sur-iters", type=int, default=800)
     ap.add_argument("--sur-batch", type=int, default=8)
+    ap.add_argument("--sur-rollout", type=int, default=16, help="windows of the judged rollout")
+    ap.add_argument("--sur-audit", type=int, default=8, help="audit every this many windows")
     ap.add_argument("--count", type=int, default=256, help="members of the batched sweep")
     args = ap.parse_args(argv)
     if args.warmup < 3:

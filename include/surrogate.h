@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-typedef enum { SUR_OK = 0, SUR_ERR_PARAM = -1, SUR_ERR_CUDA = -3 } sur_status;
+typedef enum { SUR_OK = 0, SUR_ERR_PARAM = -1, SUR_ERR_CUDA = -3, SUR_ERR_TIMEOUT = -5 } sur_status;
 
 /* Periodic 3x3 convolution as an implicit GEMM on the BF16 tensor cores, FP32 accumulation:
  *   y[p][n] = sum_tap sum_k x[p + sgn*off(tap)][k] * w'(tap, k, n) (+ bias[n]) (then ReLU if relu)
@@ -38,6 +38,29 @@ typedef enum { SUR_OK = 0, SUR_ERR_PARAM = -1, SUR_ERR_CUDA = -3 } sur_status;
  * K, N multiples of 16; batch*H*W <= 2^30. */
 SUR_API int sur_conv3x3(const void* x, const void* w, const float* bias, void* y, int batch, int H, int W, int K,
                         int N, int transposed_weights, int sgn, int relu, int out_f32, void* stream);
+
+/* The same forward convolution on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulator
+ * in tensor memory): y[p][n] = sum_tap sum_k x[p + off(tap)][k] * wt[tap][n][k] (+ bias[n])
+ * (+ addend[p][n]) (then ReLU if relu), BF16 operands, y BF16 or FP32 (out_f32).  wt holds the
+ * weights K-major, [tap][N][K] (sur_transpose_taps makes it from the [tap][K][N] layout).
+ * upsampled = 1: x is the coarse (batch, H/2, W/2, K) image read through the 2x nearest
+ * upsampling (the decoder), as sur_conv3x3_up_add.  bias and addend may be NULL; an addend needs
+ * BF16 output.  The kernel tiles 128 pixels (R rows of TW = min(W, 128) columns) by up to 128
+ * output channels: W must be a multiple of 128 or divide 128, H a multiple of 128 / TW (H, W even
+ * when upsampled), K and N multiples of 16, N <= 128 or a multiple of 128;
+ * sur_conv3x3_tc_supported (1 / 0) says whether a shape qualifies.  Errors: SUR_ERR_PARAM (a shape
+ * it cannot serve, NULL or misaligned pointers), SUR_ERR_CUDA.  Its waits are bounded: see
+ * sur_check. */
+SUR_API int sur_conv3x3_tc(const void* x, const void* wt, const float* bias, const void* addend, void* y, int batch,
+                           int H, int W, int K, int N, int relu, int out_f32, int upsampled, void* stream);
+SUR_API int sur_conv3x3_tc_supported(int batch, int H, int W, int K, int N, int upsampled);
+
+/* wt[tap][n][k] = w[tap][k][n] for 9 taps (BF16). */
+SUR_API int sur_transpose_taps(const void* w, void* wt, int K, int N, void* stream);
+
+/* Synchronise `stream` and report whether a bounded wait of a tensor-core kernel gave up since the
+ * last call (SUR_ERR_TIMEOUT; that launch wrote no output for the CTAs concerned), clearing it. */
+SUR_API int sur_check(void* stream);
 
 /* Gradient of the weights: dw[tap][ci][co] += sum_p x[p + off(tap)][ci] * dy[p][co] (FP32 atomics,
  * so dw must be zeroed first).  Cin, Cout multiples of 16; batch*H*W <= 7.4e6. */

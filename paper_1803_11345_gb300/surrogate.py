@@ -56,6 +56,11 @@ _sig("sur_pack_state", [_vp, _vp, _vp, _sz, _i, _f, _vp])
 _sig("sur_unpack_state", [_vp, _vp, _sz, _f, _vp])
 _sig("sur_phi_sums", [_vp, _i, _i, _i, _vp, _vp])
 _sig("sur_phi_sq_diff", [_vp, _vp, _i, _i, _i, _vp, _vp])
+_sig("sur_conv3x3_tc", [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp])
+_sig("sur_conv3x3_tc_supported", [_i, _i, _i, _i, _i, _i])
+_sig("sur_transpose_taps", [_vp, _vp, _i, _i, _vp])
+_sig("sur_check", [_vp])
+SUR_ERR_TIMEOUT = -5
 
 
 class SurError(RuntimeError):
@@ -146,6 +151,24 @@ def sur_cast_bf16(x, y, stream):
     _ok(_lib.sur_cast_bf16(_p(x), _p(y), x.numel(), stream), "sur_cast_bf16")
 
 
+def sur_conv3x3_tc(x, wt, bias, addend, y, batch, H, W, K, N, relu, out_f32, upsampled, stream):
+    _ok(_lib.sur_conv3x3_tc(_p(x), _p(wt), _p(bias), _p(addend), _p(y), batch, H, W, K, N, relu, out_f32,
+                            upsampled, stream), "sur_conv3x3_tc")
+
+
+def sur_conv3x3_tc_supported(batch, H, W, K, N, upsampled=0):
+    return bool(_lib.sur_conv3x3_tc_supported(batch, H, W, K, N, upsampled))
+
+
+def sur_transpose_taps(w, wt, K, N, stream):
+    _ok(_lib.sur_transpose_taps(_p(w), _p(wt), K, N, stream), "sur_transpose_taps")
+
+
+def sur_check(stream):
+    """SUR_OK, or SUR_ERR_TIMEOUT if a bounded wait of a tensor-core kernel gave up (cleared)."""
+    return _lib.sur_check(stream)
+
+
 def sur_pack_state(state, x, base, npix, C, u_scale, stream):
     _ok(_lib.sur_pack_state(_p(state), _p(x), _p(base), npix, C, float(u_scale), stream), "sur_pack_state")
 
@@ -180,15 +203,19 @@ class UNet:
     """The surrogate network on one CUDA device.  ``ch`` = channels per level (multiples of 16),
     ``cin`` = input/output channels (16; the first three carry phi, ux, uy)."""
 
-    def __init__(self, ch=(32, 64, 128, 256), cin=16, seed=0, stream=None, device="cuda"):
+    def __init__(self, ch=(32, 64, 128, 256), cin=16, seed=0, stream=None, device="cuda", tensor_cores=True):
         import torch
         self.torch = torch
+        # forward convolutions on the tcgen05 kernel (sur_conv3x3_tc) where it serves the shape;
+        # False: the mma.sync kernels only (the reference path of the same arithmetic)
+        self.tensor_cores = tensor_cores
         self.ch, self.cin = tuple(ch), cin
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.s = self.stream.cuda_stream
         self.layers = layer_specs(cin, self.ch)
         rng = np.random.default_rng(seed)
         self.w, self.b, self.wb, self.gw, self.gb, self.mw, self.vw, self.mb, self.vb = ({} for _ in range(9))
+        self.wt = {}  # K-major BF16 copies [tap][Cout][Cin] for the tcgen05 convolution
         f32 = dict(dtype=torch.float32, device=device)
         for name, ci, co in self.layers:
             scale = 0.0 if name == "out" else math.sqrt(2.0 / (9 * ci))  # He init; zero output layer
@@ -198,6 +225,8 @@ class UNet:
             sur_zero(self.b[name], self.s)
             self.wb[name] = torch.empty((9, ci, co), dtype=torch.bfloat16, device=device)
             sur_cast_bf16(self.w[name], self.wb[name], self.s)
+            self.wt[name] = torch.empty((9, co, ci), dtype=torch.bfloat16, device=device)
+            sur_transpose_taps(self.wb[name], self.wt[name], ci, co, self.s)
             for d in (self.gw, self.mw, self.vw):
                 d[name] = torch.empty((9, ci, co), **f32)
                 sur_zero(d[name], self.s)
@@ -225,10 +254,16 @@ class UNet:
             self._bufs[key] = t
         return t
 
+    def _tc(self, B, H, W, ci, co, up=0):
+        return self.tensor_cores and sur_conv3x3_tc_supported(B, H, W, ci, co, up)
+
     def _conv(self, x, name, B, H, W, relu, out_f32=False, key=None):
         _, ci, co = next(l for l in self.layers if l[0] == name)
         y = self._buf(key or name, (B, H, W, co), self.torch.float32 if out_f32 else self.torch.bfloat16)
-        sur_conv3x3(x, self.wb[name], self.b[name], y, B, H, W, ci, co, 0, 1, int(relu), int(out_f32), self.s)
+        if self._tc(B, H, W, ci, co):
+            sur_conv3x3_tc(x, self.wt[name], self.b[name], None, y, B, H, W, ci, co, int(relu), int(out_f32), 0, self.s)
+        else:
+            sur_conv3x3(x, self.wb[name], self.b[name], y, B, H, W, ci, co, 0, 1, int(relu), int(out_f32), self.s)
         return y
 
     # -- forward / backward --------------------------------------------------------------------
@@ -256,8 +291,12 @@ class UNet:
             hh, ww = self._sizes[l]
             # s = conv(up2(h)) + skip in one kernel (upsampling read through the coarse index)
             sk = self._buf(f"s{l}", (B, hh, ww, self.ch[l]), bf)
-            sur_conv3x3_up_add(h, self.wb[f"u{l}"], self.b[f"u{l}"], skips[l], sk, B, hh, ww, self.ch[l + 1],
-                               self.ch[l], self.s)
+            if self._tc(B, hh, ww, self.ch[l + 1], self.ch[l], 1):
+                sur_conv3x3_tc(h, self.wt[f"u{l}"], self.b[f"u{l}"], skips[l], sk, B, hh, ww, self.ch[l + 1],
+                               self.ch[l], 0, 0, 1, self.s)
+            else:
+                sur_conv3x3_up_add(h, self.wb[f"u{l}"], self.b[f"u{l}"], skips[l], sk, B, hh, ww, self.ch[l + 1],
+                                   self.ch[l], self.s)
             h = self._conv(sk, f"d{l}", B, hh, ww, True)
         out = self._conv(h, "out", B, H, W, False, out_f32=True)
         pred = self._buf("pred", (B, H, W, 3), self.torch.float32)
@@ -355,9 +394,11 @@ class UNet:
 
     def adam_step(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1
-        for n, _, _ in self.layers:
+        for n, ci, co in self.layers:
             sur_adam(self.w[n], self.gw[n], self.mw[n], self.vw[n], self.wb[n], lr, b1, b2, eps, self.step_count, self.s)
             sur_adam(self.b[n], self.gb[n], self.mb[n], self.vb[n], None, lr, b1, b2, eps, self.step_count, self.s)
+            if self.tensor_cores:
+                sur_transpose_taps(self.wb[n], self.wt[n], ci, co, self.s)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -713,7 +754,9 @@ def time_forward(net, x, base, reps=5, graph=False):
 
 
 def _main(argv=None):
-    """Time the forward pass of the default network on a random batch (eager and graph-replayed)."""
+    """Time the forward pass of the default network on a random batch (eager and graph-replayed),
+    or with --layer H,Cin,Cout[,up] one 3x3 convolution of that shape (up: read through the 2x
+    upsampling of an H/2 image, with a skip addend) on the tcgen05 kernel and on the mma.sync one."""
     import argparse
 
     import torch
@@ -721,15 +764,56 @@ def _main(argv=None):
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--n", type=int, default=256, help="image side")
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--layer", type=str, default="", help="H,Cin,Cout[,up]: time one convolution")
+    ap.add_argument("--kernel", choices=["both", "tc", "mma"], default="both")
+    ap.add_argument("--mma-sync", action="store_true", help="network forward on the mma.sync kernels only")
     a = ap.parse_args(argv)
-    net = UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
+    s = torch.cuda.current_stream().cuda_stream
+    if a.layer:
+        parts = [int(v) for v in a.layer.split(",")]
+        H, ci, co = parts[:3]
+        up = parts[3] if len(parts) > 3 else 0
+        g = torch.Generator(device="cuda").manual_seed(1)
+        hs = H // 2 if up else H
+        x = torch.randn((a.batch, hs, hs, ci), device="cuda", generator=g).to(torch.bfloat16)
+        w = (torch.randn((9, ci, co), device="cuda", generator=g) * 0.1).to(torch.bfloat16)
+        wt = torch.empty((9, co, ci), dtype=torch.bfloat16, device="cuda")
+        sur_transpose_taps(w, wt, ci, co, s)
+        b = torch.zeros(co, device="cuda")
+        y = torch.empty((a.batch, H, H, co), dtype=torch.bfloat16, device="cuda")
+        add = torch.zeros((a.batch, H, H, co), dtype=torch.bfloat16, device="cuda") if up else None
+        runs = {}
+        if a.kernel in ("both", "tc"):
+            runs["tcgen05"] = lambda: sur_conv3x3_tc(x, wt, b, add, y, a.batch, H, H, ci, co, 0 if up else 1, 0, up, s)
+        if a.kernel in ("both", "mma"):
+            runs["mma.sync"] = ((lambda: sur_conv3x3_up_add(x, w, b, add, y, a.batch, H, H, ci, co, s)) if up else
+                                (lambda: sur_conv3x3(x, w, b, y, a.batch, H, H, ci, co, 0, 1, 1, 0, s)))
+        flop = 2.0 * 9 * ci * co * a.batch * H * H
+        for name, fn in runs.items():
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / a.reps * 1e3
+            print(f"{name}: batch {a.batch} {H}x{H} {ci}->{co}{' (upsampled, skip)' if up else ''}: {us:.1f} us, "
+                  f"{flop / us / 1e6:.0f} TFLOP/s")
+        if sur_check(s) != SUR_OK:
+            raise SurError("a bounded wait of the tensor-core kernel gave up")
+        return
+    net = UNet(ch=(32, 64, 128, 256), cin=16, seed=1, tensor_cores=not a.mma_sync)
     g = torch.Generator(device="cuda").manual_seed(1)
     x = torch.randn((a.batch, a.n, a.n, 16), device="cuda", generator=g).to(torch.bfloat16)
     base = x[..., :3].float().contiguous()
     eager = time_forward(net, x, base, reps=a.reps)
     graph = time_forward(net, x, base, reps=a.reps, graph=True)
     print(f"batch {a.batch} image {a.n}x{a.n}: {eager:.4f} ms/forward eager, {graph:.4f} ms/forward graph "
-          f"({net.launches_per_forward()} launches per forward)")
+          f"({net.launches_per_forward()} launches per forward, "
+          f"{'mma.sync' if a.mma_sync else 'tcgen05 where supported'})")
 
 
 if __name__ == "__main__":

@@ -10,27 +10,38 @@
 // rows = pixels (A) or output channels (B), whose 8-row groups are 128 bytes apart (SBO) and whose
 // two 8-channel halves ("octets") are one block apart (LBO).  A core matrix may start at any
 // 16-byte row, so a shifted window of staged pixels is the same memory seen from another start:
-//   * row mode (W >= 128): a CTA owns RT image rows x 128 columns (RT accumulators).  A is the
-//     RT + 2 rows around them, each row staged with one wrapped halo column on either side
-//     (130 pixels): [octet][halo row][130 pixels][8 x BF16].  The operand of tap (dy, dx) for
-//     output row r starts at pixel (r + dy + 1) * 130 + dx + 1: 9 RT descriptors, no copies.
+//   * row mode (W >= 128): a tile is RT image rows x 128 columns (RT accumulators).  A is the
+//     RT + 2 rows around them, each row staged with one wrapped halo column on either side, in a
+//     row of 144 pixel slots whose 128 centre pixels start at slot 8 (a 128-byte boundary):
+//     [octet][halo row][144 slots][8 x BF16].  The operand of tap (dy, dx) for output row r
+//     starts at slot (r + dy + 1) * 144 + 8 + dx: 9 RT descriptors, no copies.  Without the
+//     upsampling the rows come in by TMA (a tensor map over the NHWC input, one 128-pixel box
+//     per row and octet, and 16-byte bulk copies for the two wrapped halo pixels) issued by one
+//     thread, completing the stage's mbarrier by byte count.
 //   * copy mode (W < 128, W a power of two dividing 128): one accumulator of R = 128/W full rows,
 //     which a start offset cannot shift by a column across the row seams, so A holds the R + 2
 //     rows around them in three copies shifted by dx = -1, 0, +1 with the periodic wrap applied
 //     while staging: [dx][octet][halo-tile pixel][8 x BF16]; tap (dy, dx) starts at pixel
 //     (dy + 1) * W of copy dx.
 //   * B: the 9 taps' weights for the N tile, from the K-major copy [tap][N][K] (see
-//     sur_transpose_taps): [tap][octet][output channel][8 x BF16], shared by every accumulator.
-// Stages are filled by 16-byte cp.async copies (double-buffered when there is more than one
-// channel chunk); one thread issues the chunk's MMAs and commits them to an mbarrier, whose
-// completion frees the stage.  Every mbarrier wait is bounded: a wait that gives up sets the
+//     sur_transpose_taps): [octet][tap][output channel][8 x BF16] (by TMA: one box per octet),
+//     shared by every accumulator.
+// A persistent CTA walks its tiles; every (tile, 16-channel chunk) is an item of a ring of S
+// shared-memory stages, filled by TMA or, in copy mode and when upsampling, by four producer
+// warps' 16-byte cp.async copies; one thread issues each item's MMAs into one of two
+// accumulator sets (the epilogue of a tile overlaps the next tile's MMAs) and commits them to
+// the stage's "empty" mbarrier.  Every mbarrier wait is bounded: a wait that gives up sets the
 // status word read by sur_check, lets the copies and MMAs it issued finish (again bounded), frees
 // the tensor memory and returns.  The epilogue reads the accumulators with tcgen05.ld (each warp
 // its 32 lanes), adds the bias and an optional addend (the decoder's skip), applies ReLU, and
 // stores BF16 or FP32 NHWC rows.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "../../include/surrogate.h"
 #include "lbm_tma.cuh"
@@ -38,6 +49,8 @@
 namespace {
 
 using bf16 = __nv_bfloat16;
+using lbmch::bulk_g2s;
+using lbmch::mbar_arrive_expect_tx;
 using lbmch::mbar_fence_init;
 using lbmch::mbar_init;
 using lbmch::mbar_try_wait;
@@ -48,7 +61,6 @@ using lbmch::smem_u32;
 __device__ int g_tc_status;
 
 constexpr uint32_t kWaitProbes = 1u << 22;
-constexpr int kThreads = 128;
 constexpr int kTileM = 128;
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity) {
@@ -119,206 +131,329 @@ struct ConvTC {
   int K, N;             // input / output channels
   int rows_mode;        // 1: row mode (W >= 128), 0: copy mode
   int TW, R;            // copy mode: tile of R rows x TW = W columns; row mode: TW = 128, R = 1
-  int RT;               // row mode: output rows (accumulators) per CTA; copy mode: 1
+  int RT;               // row mode: output rows (accumulators) per tile; copy mode: 1
   int tw_shift;         // log2(TW)
-  int tiles_x, tiles_y; // tiles per image along x and y
-  int nchunks, stages;  // K / 16; staging buffers (1 or 2)
-  int ntile;            // output channels per CTA
-  uint32_t ncols;       // TMEM columns allocated (accumulators x N tile, a power of two >= 32)
-  uint32_t acc_cols;    // TMEM column stride between accumulators
+  int tiles_x, tiles_y; // M tiles per image along x and y
+  int ntiles_n;         // N tiles
+  int ntiles;           // all tiles: batch x tiles_y x tiles_x x ntiles_n
+  int nchunks;          // K / 16
+  int ntile;            // output channels per tile
+  uint32_t ncols;       // TMEM columns allocated: two accumulator sets (double buffer)
+  uint32_t acc_cols;    // TMEM column stride between accumulators of a set
+  uint32_t set_cols;    // columns of one set (RT accumulators)
   uint32_t a_block, a_stage, b_block, stage_bytes;
+  uint32_t tx_bytes;    // bytes one item brings in (TMA mode: the stage's expected transaction count)
   uint32_t idesc;
   int relu, out_f32, up;
+  int tma;              // 1: row mode without upsampling, staged by TMA
 };
 
-constexpr int kHaloW = kTileM + 2;  // staged pixels per halo row in row mode
+constexpr int kRowSlots = 144;  // pixel slots per staged row in row mode (16 bytes each)
+constexpr int kRowFirst = 7;    // slot of the left halo pixel; the 128 centre pixels start at slot 8
+// Warp roles of the persistent kernel: 4 producer warps (copies), 1 MMA warp (also allocates the
+// tensor memory), 4 epilogue warps (one per TMEM lane quarter).
+constexpr int kProducers = 128;
+constexpr int kMmaWarp = 4;
+constexpr int kThreadsP = 288;
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool wait_role(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t k = 0; k < kWaitProbes; ++k) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((k & 63u) == 63u && *abort) return false;
+  }
+  return false;
+}
+
+// Tensor-map box loads into shared memory, completing `bar` by byte count.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct TileCoord {
+  int b, y0, x0, n0;
+};
+__device__ __forceinline__ TileCoord tile_coord(const ConvTC& c, int t) {
+  TileCoord q;
+  const int nt = t % c.ntiles_n;
+  const int m = t / c.ntiles_n;
+  const int per_img = c.tiles_x * c.tiles_y;
+  q.b = m / per_img;
+  const int rem = m - q.b * per_img;
+  q.y0 = (rem / c.tiles_x) * (c.rows_mode ? c.RT : c.R);
+  q.x0 = (rem % c.tiles_x) * c.TW;
+  q.n0 = nt * c.ntile;
+  return q;
+}
+
+// Persistent kernel: CTA j takes tiles j, j + gridDim.x, ...; every (tile, channel chunk) is one
+// item of a ring of S shared-memory stages.
+template <int S>
+__global__ void __launch_bounds__(kThreadsP)
 k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const float* __restrict__ bias,
-             const bf16* __restrict__ addend, void* __restrict__ y, const ConvTC c) {
+             const bf16* __restrict__ addend, void* __restrict__ y, const ConvTC c,
+             const __grid_constant__ CUtensorMap tm_rows, const __grid_constant__ CUtensorMap tm_w) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int per_img = c.tiles_x * c.tiles_y;
-  const int b = blockIdx.x / per_img;
-  const int rem = blockIdx.x - b * per_img;
-  const int rows_per_tile = c.rows_mode ? c.RT : c.R;
-  const int y0 = (rem / c.tiles_x) * rows_per_tile, x0 = (rem % c.tiles_x) * c.TW;
-  const int n0 = blockIdx.y * c.ntile;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + c.stages * c.stage_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * c.stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  volatile int* abort = reinterpret_cast<volatile int*>(done + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1) + 1;
 
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(tslot), c.ncols);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], c.tma ? 1 : kProducers);
+      mbar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&tfull[k], 1);
+      mbar_init(&tempty[k], 128);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
     mbar_fence_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-
-  auto src_pixel = [&](int yy, int xx) -> size_t {
-    return c.up ? ((size_t)b * c.Hs + (yy >> 1)) * c.Ws + (xx >> 1) : ((size_t)b * c.H + yy) * c.W + xx;
-  };
-  auto load_chunk = [&](int ch, int st) {
-    unsigned char* A = smem + (uint32_t)st * c.stage_bytes;
-    unsigned char* Bm = A + c.a_stage;
-    const int k0 = ch * 16;
-    if (c.rows_mode) {
-      const int hrows = c.RT + 2;
-      for (int kc = 0; kc < 2; ++kc)
-        for (int hr = 0; hr < hrows; ++hr) {
-          const int yy = wrap(y0 + hr - 1, c.H);
-          unsigned char* dst = A + kc * c.a_block + hr * (kHaloW * 16);
-          for (int j = tid; j < kHaloW; j += kThreads) {
-            const int xx = wrap(x0 + j - 1, c.W);
-            cp_async16(smem_u32(dst + j * 16), x + src_pixel(yy, xx) * c.K + k0 + kc * 8);
-          }
-        }
-    } else {
-      const int arows = (c.R + 2) * c.TW;
-      for (int blk = 0; blk < 6; ++blk) {  // dx * 2 + octet
-        const int dx = blk >> 1, kc = blk & 1;
-        for (int j = tid; j < arows; j += kThreads) {
-          const int yy = wrap(y0 + (j >> c.tw_shift) - 1, c.H);
-          const int xx = wrap(x0 + (j & (c.TW - 1)) + dx - 1, c.W);
-          cp_async16(smem_u32(A + blk * c.a_block + j * 16), x + src_pixel(yy, xx) * c.K + k0 + kc * 8);
-        }
-      }
-    }
-    for (int q = tid; q < 18 * c.ntile; q += kThreads) {
-      const int blk = q / c.ntile;  // tap * 2 + octet
-      const int n = q - blk * c.ntile;
-      const int tap = blk >> 1, kc = blk & 1;
-      cp_async16(smem_u32(Bm + blk * c.b_block + n * 16), wt + ((size_t)tap * c.N + n0 + n) * c.K + k0 + kc * 8);
-    }
-    cp_async_commit();
+  auto give_up = [&]() {
+    *abort = 1;
+    atomicOr(&g_tc_status, 1);
   };
 
-  // ok is the same in every thread: each bounded wait is followed by a block-wide AND.
-  bool ok = true;
-  int committed = -1;  // last chunk whose MMAs were committed
-  load_chunk(0, 0);
-  for (int ch = 0; ch < c.nchunks; ++ch) {
-    const int st = c.stages == 2 ? (ch & 1) : 0;
-    const bool prefetch = c.stages == 2 && ch + 1 < c.nchunks;
-    if (prefetch && ch >= 1) {
-      // the MMAs of chunk ch - 1 read the stage chunk ch + 1 goes to: wait for them first
-      ok = __syncthreads_and(wait_bounded(&mbar[(ch + 1) & 1], (uint32_t)((ch - 1) >> 1) & 1u));
-      if (!ok) break;
-    }
-    if (prefetch) {
-      load_chunk(ch + 1, (ch + 1) & 1);
-      cp_async_wait_one();  // this thread's copies of chunk ch have landed
-    } else {
-      cp_async_wait_all();
-    }
-    fence_proxy_async();
-    __syncthreads();
+  if (c.tma && tid < kProducers) {
+    // ---- TMA producer: one thread; stage i % S is full once its bytes have landed.
     if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a_base = smem_u32(smem + (uint32_t)st * c.stage_bytes);
-      const uint32_t b_base = a_base + c.a_stage;
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dxi = tap % 3;  // dxi = dx + 1
-        const uint64_t bd = smem_desc(b_base + (uint32_t)(tap * 2) * c.b_block, c.b_block, 128);
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x) {
+        const TileCoord q = tile_coord(c, t);
+        for (int ch = 0; ch < c.nchunks; ++ch, ++i) {
+          const int st = i % S;
+          if (i >= S && !wait_role(&empty[st], (uint32_t)((i / S) - 1) & 1u, abort)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          unsigned char* A = smem + (uint32_t)st * c.stage_bytes;
+          unsigned char* Bm = A + c.a_stage;
+          mbar_arrive_expect_tx(&full[st], c.tx_bytes);
+          const int k0 = ch * 16;
+          const int xl = wrap(q.x0 - 1, c.W), xr = wrap(q.x0 + kTileM, c.W);
+          for (int kc = 0; kc < 2; ++kc)
+            for (int hr = 0; hr < c.RT + 2; ++hr) {
+              const int yy = wrap(q.y0 + hr - 1, c.H);
+              unsigned char* row = A + kc * c.a_block + hr * (kRowSlots * 16);
+              tma_load_4d(row + (kRowFirst + 1) * 16, &tm_rows, k0 + kc * 8, q.x0, yy, q.b, &full[st]);
+              const size_t base = ((size_t)q.b * c.H + yy) * c.W;
+              bulk_g2s(row + kRowFirst * 16, x + (base + xl) * c.K + k0 + kc * 8, 16, &full[st]);
+              bulk_g2s(row + (kRowFirst + 1 + kTileM) * 16, x + (base + xr) * c.K + k0 + kc * 8, 16, &full[st]);
+            }
+          for (int kc = 0; kc < 2; ++kc) tma_load_3d(Bm + kc * 9 * c.b_block, &tm_w, k0 + kc * 8, q.n0, 0, &full[st]);
+        }
+      }
+    }
+  } else if (tid < kProducers) {
+    // ---- producers: copy item i into stage i % S; signal item i - 1 full once this thread's
+    // copies of it have landed (and were fenced for the tensor core's reads).  The one-item lag
+    // leaves the MMAs S - 2 items of slack before a stage is needed again.
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x) {
+      const TileCoord q = tile_coord(c, t);
+      auto src_pixel = [&](int yy, int xx) -> size_t {
+        return c.up ? ((size_t)q.b * c.Hs + (yy >> 1)) * c.Ws + (xx >> 1) : ((size_t)q.b * c.H + yy) * c.W + xx;
+      };
+      for (int ch = 0; ch < c.nchunks; ++ch, ++i) {
+        const int st = i % S;
+        if (i >= S && !wait_role(&empty[st], (uint32_t)((i / S) - 1) & 1u, abort)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        unsigned char* A = smem + (uint32_t)st * c.stage_bytes;
+        unsigned char* Bm = A + c.a_stage;
+        const int k0 = ch * 16;
         if (c.rows_mode) {
-          for (int r = 0; r < c.RT; ++r) {
-            const uint32_t start = a_base + (uint32_t)(((r + dy + 1) * kHaloW + dxi) * 16);
-            tc_mma(tmem + (uint32_t)r * c.acc_cols, smem_desc(start, c.a_block, 128), bd, c.idesc,
-                   (ch > 0 || tap > 0) ? 1u : 0u);
-          }
+          for (int kc = 0; kc < 2; ++kc)
+            for (int hr = 0; hr < c.RT + 2; ++hr) {
+              const int yy = wrap(q.y0 + hr - 1, c.H);
+              unsigned char* dst = A + kc * c.a_block + hr * (kRowSlots * 16) + kRowFirst * 16;
+              for (int j = tid; j < kTileM + 2; j += kProducers) {
+                const int xx = wrap(q.x0 + j - 1, c.W);
+                cp_async16(smem_u32(dst + j * 16), x + src_pixel(yy, xx) * c.K + k0 + kc * 8);
+              }
+            }
         } else {
-          const uint32_t start = a_base + (uint32_t)(dxi * 2) * c.a_block + (uint32_t)((dy + 1) * c.TW * 16);
-          tc_mma(tmem, smem_desc(start, c.a_block, 128), bd, c.idesc, (ch > 0 || tap > 0) ? 1u : 0u);
+          const int arows = (c.R + 2) * c.TW;
+          for (int blk = 0; blk < 6; ++blk) {  // dx * 2 + octet
+            const int dx = blk >> 1, kc = blk & 1;
+            for (int j = tid; j < arows; j += kProducers) {
+              const int yy = wrap(q.y0 + (j >> c.tw_shift) - 1, c.H);
+              const int xx = wrap(q.x0 + (j & (c.TW - 1)) + dx - 1, c.W);
+              cp_async16(smem_u32(A + blk * c.a_block + j * 16), x + src_pixel(yy, xx) * c.K + k0 + kc * 8);
+            }
+          }
+        }
+        for (int e = tid; e < 18 * c.ntile; e += kProducers) {
+          const int blk = e / c.ntile;  // octet * 9 + tap
+          const int n = e - blk * c.ntile;
+          const int kc = blk / 9, tap = blk - kc * 9;
+          cp_async16(smem_u32(Bm + blk * c.b_block + n * 16),
+                     wt + ((size_t)tap * c.N + q.n0 + n) * c.K + k0 + kc * 8);
+        }
+        cp_async_commit();
+        if (i >= 1) {
+          cp_async_wait_one();
+          fence_proxy_async();
+          mbar_arrive(&full[(i - 1) % S]);
         }
       }
-      tc_commit(smem_u32(&mbar[st]));
     }
-    committed = ch;
-    if (c.stages == 1 && ch + 1 < c.nchunks) {
-      ok = __syncthreads_and(wait_bounded(&mbar[0], (uint32_t)ch & 1u));
-      if (!ok) break;
-      load_chunk(ch + 1, 0);
-    }
-  }
-  // Completion of the last commit covers every MMA issued before it.
-  const int sl = committed < 0 ? 0 : (c.stages == 2 ? (committed & 1) : 0);
-  const uint32_t ph = c.stages == 2 ? ((uint32_t)(committed >> 1) & 1u) : ((uint32_t)committed & 1u);
-  if (ok) ok = __syncthreads_and(wait_bounded(&mbar[sl], ph));
-  if (!ok) {
-    // A wait gave up: record it, let this CTA's copies and MMAs finish (bounded), free the
-    // tensor memory and return without writing the output.
-    if (tid == 0) atomicOr(&g_tc_status, 1);
     cp_async_wait_all();
-    if (committed >= 0) wait_bounded(&mbar[sl], ph);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, c.ncols);
-    return;
-  }
-  tc_fence_after();
-
-  // Epilogue: this thread's pixel is TMEM lane i = 32 warp + lane of each accumulator.
-  const int i = warp * 32 + lane;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  const int nacc = c.rows_mode ? c.RT : 1;
-  for (int r = 0; r < nacc; ++r) {
-    const int py = c.rows_mode ? y0 + r : y0 + (i >> c.tw_shift);
-    const int px = c.rows_mode ? x0 + i : x0 + (i & (c.TW - 1));
-    const size_t pix = ((size_t)b * c.H + py) * c.W + px;
-    for (int j0 = 0; j0 < c.ntile; j0 += 16) {
-      uint32_t rr[16];
-      tc_ld16(lane_base + (uint32_t)r * c.acc_cols + (uint32_t)j0, rr);
-      tc_wait_ld();
-      float v[16];
+    fence_proxy_async();
+    if (ok && i >= 1) mbar_arrive(&full[(i - 1) % S]);
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issuer: one thread; accumulator set kt & 1 for the kt-th tile of this CTA.
+    if (lane == 0) {
+      int i = 0, kt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x, ++kt) {
+        const uint32_t set = (uint32_t)(kt & 1) * c.set_cols;
+        if (kt >= 2 && !wait_role(&tempty[kt & 1], (uint32_t)((kt >> 1) - 1) & 1u, abort)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int ch = 0; ch < c.nchunks; ++ch, ++i) {
+          const int st = i % S;
+          if (!wait_role(&full[st], (uint32_t)(i / S) & 1u, abort)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(smem + (uint32_t)st * c.stage_bytes);
+          const uint32_t b_base = a_base + c.a_stage;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(rr[q]) + (bias ? bias[n0 + j0 + q] : 0.f);
-      if (addend) {
-        const uint4* ap = reinterpret_cast<const uint4*>(addend + pix * c.N + n0 + j0);
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3 - 1, dxi = tap % 3;  // dxi = dx + 1
+            const uint64_t bd = smem_desc(b_base + (uint32_t)tap * c.b_block, 9 * c.b_block, 128);
+            const uint32_t acc = (ch > 0 || tap > 0) ? 1u : 0u;
+            if (c.rows_mode) {
+              for (int r = 0; r < c.RT; ++r) {
+                const uint32_t start = a_base + (uint32_t)(((r + dy + 1) * kRowSlots + kRowFirst + dxi) * 16);
+                tc_mma(tmem + set + (uint32_t)r * c.acc_cols, smem_desc(start, c.a_block, 128), bd, c.idesc, acc);
+              }
+            } else {
+              const uint32_t start = a_base + (uint32_t)(dxi * 2) * c.a_block + (uint32_t)((dy + 1) * c.TW * 16);
+              tc_mma(tmem + set, smem_desc(start, c.a_block, 128), bd, c.idesc, acc);
+            }
+          }
+          tc_commit(smem_u32(&empty[st]));  // the stage is free once these MMAs are done
+        }
+        if (ok) tc_commit(smem_u32(&tfull[kt & 1]));  // the tile's accumulators are complete
+      }
+      // Every MMA issued has completed once this commit arrives: the tensor memory can go.
+      tc_commit(smem_u32(done));
+      if (!wait_bounded(done, 0)) give_up();
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31: pixel i of the tile.
+    const int quarter = warp & 3;
+    const int i = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    int kt = 0;
+    for (int t = blockIdx.x; t < c.ntiles; t += gridDim.x, ++kt) {
+      if (!wait_role(&tfull[kt & 1], (uint32_t)(kt >> 1) & 1u, abort)) {
+        give_up();
+        break;
+      }
+      tc_fence_after();
+      const TileCoord q = tile_coord(c, t);
+      const uint32_t set = (uint32_t)(kt & 1) * c.set_cols;
+      const int nacc = c.rows_mode ? c.RT : 1;
+      for (int r = 0; r < nacc; ++r) {
+        const int py = c.rows_mode ? q.y0 + r : q.y0 + (i >> c.tw_shift);
+        const int px = c.rows_mode ? q.x0 + i : q.x0 + (i & (c.TW - 1));
+        const size_t pix = ((size_t)q.b * c.H + py) * c.W + px;
+        for (int j0 = 0; j0 < c.ntile; j0 += 16) {
+          uint32_t rr[16];
+          tc_ld16(lane_base + set + (uint32_t)r * c.acc_cols + (uint32_t)j0, rr);
+          tc_wait_ld();
+          const int n = q.n0 + j0;
+          float v[16];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint4 a4 = ap[h];
-          const uint32_t aw[4] = {a4.x, a4.y, a4.z, a4.w};
+          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(rr[e]) + (bias ? bias[n + e] : 0.f);
+          if (addend) {
+            const uint4* ap = reinterpret_cast<const uint4*>(addend + pix * c.N + n);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&aw[e]);
-            v[h * 8 + 2 * e] += __bfloat162float(p2.x);
-            v[h * 8 + 2 * e + 1] += __bfloat162float(p2.y);
+            for (int h = 0; h < 2; ++h) {
+              const uint4 a4 = ap[h];
+              const uint32_t aw[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&aw[e]);
+                v[h * 8 + 2 * e] += __bfloat162float(p2.x);
+                v[h * 8 + 2 * e + 1] += __bfloat162float(p2.y);
+              }
+            }
+          }
+          if (c.relu) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e], 0.f);
+          }
+          if (c.out_f32) {
+            float4* yp = reinterpret_cast<float4*>(reinterpret_cast<float*>(y) + pix * c.N + n);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) yp[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+          } else {
+            uint32_t w[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+              w[e] = *reinterpret_cast<const uint32_t*>(&p2);
+            }
+            uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(y) + pix * c.N + n);
+            yp[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            yp[1] = make_uint4(w[4], w[5], w[6], w[7]);
           }
         }
       }
-      if (c.relu) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
-      }
-      if (c.out_f32) {
-        float4* yp = reinterpret_cast<float4*>(reinterpret_cast<float*>(y) + pix * c.N + n0 + j0);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) yp[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
-      } else {
-        uint32_t w[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-          w[e] = *reinterpret_cast<const uint32_t*>(&p2);
-        }
-        uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(y) + pix * c.N + n0 + j0);
-        yp[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        yp[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      }
+      tc_fence_before();
+      mbar_arrive(&tempty[kt & 1]);  // this set may take the next tile's MMAs
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, c.ncols);
+  if (warp == kMmaWarp) tmem_dealloc(tmem, c.ncols);
 }
 
 // w[tap][k][n] -> wt[tap][n][k].
@@ -335,7 +470,8 @@ __global__ void k_transpose_taps(const bf16* __restrict__ w, bf16* __restrict__ 
 constexpr int kMaxSmem = 227 * 1024;
 
 // The tile geometry and shared-memory plan for a layer, or false if the kernel cannot serve it.
-bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* smem) {
+// *stages: stages of the ring (2 to 4, as many as fit).
+bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* smem, int* stages) {
   if (batch < 1 || H < 1 || W < 1 || K < 16 || K % 16 || N < 16 || N % 16) return false;
   if (up && (H % 2 || W % 2)) return false;
   const int ntile = N > 128 ? 128 : N;
@@ -347,8 +483,8 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
   c->K = K;
   c->N = N;
   c->ntile = ntile;
+  c->ntiles_n = N / ntile;
   c->nchunks = K / 16;
-  c->stages = c->nchunks > 1 ? 2 : 1;
   c->b_block = (uint32_t)(ntile * 16);
   const uint32_t ncols1 = ntile <= 32 ? 32u : (ntile <= 64 ? 64u : 128u);
   if (W >= kTileM) {
@@ -357,14 +493,14 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
     c->TW = kTileM;
     c->R = 1;
     c->tw_shift = 7;
-    // output rows per CTA: the most of 4, 2, 1 dividing H whose accumulators fit 256 TMEM columns
+    // output rows per tile: the most of 4, 2, 1 dividing H whose two accumulator sets fit the
+    // 512 TMEM columns
     int RT = 4;
     while (RT > 1 && (H % RT || (uint32_t)RT * ncols1 > 256u)) RT >>= 1;
     c->RT = RT;
-    c->acc_cols = ncols1;
-    c->ncols = (uint32_t)RT * ncols1;
-    c->a_block = (uint32_t)((RT + 2) * kHaloW * 16);
+    c->a_block = (uint32_t)((RT + 2) * kRowSlots * 16);
     c->a_stage = 2 * c->a_block;
+    c->tx_bytes = (uint32_t)(2 * (RT + 2) * (kTileM + 2) * 16);
   } else {
     if (kTileM % W || (W & (W - 1))) return false;
     c->rows_mode = 0;
@@ -375,49 +511,114 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
     while ((1 << sh) < W) ++sh;
     c->tw_shift = sh;
     c->RT = 1;
-    c->acc_cols = ncols1;
-    c->ncols = ncols1;
     c->a_block = (uint32_t)((c->R + 2) * W * 16);
     c->a_stage = 6 * c->a_block;
+    c->tx_bytes = c->a_stage;
   }
+  c->tma = c->rows_mode && !up;
+  c->acc_cols = ncols1;
+  c->set_cols = (uint32_t)c->RT * ncols1;
+  c->ncols = 2 * c->set_cols;
   c->tiles_x = W / c->TW;
   c->tiles_y = H / (c->rows_mode ? c->RT : c->R);
-  c->stage_bytes = c->a_stage + 18 * c->b_block;
+  const long long nt = (long long)batch * c->tiles_x * c->tiles_y * c->ntiles_n;
+  if (nt > 0x7FFFFFFFll) return false;
+  c->ntiles = (int)nt;
+  c->stage_bytes = c->a_stage + 18 * c->b_block;  // a multiple of 256 bytes: every stage 128-byte aligned
+  c->tx_bytes += 18 * c->b_block;
   // Instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
   // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
   c->idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
   c->up = up;
-  *smem = (size_t)c->stages * c->stage_bytes + 2 * sizeof(uint64_t) + 16;
+  const size_t tail = (5 + 8) * sizeof(uint64_t) + 16;  // barriers (S <= 4), abort flag, TMEM slot
+  int st = 4;
+  while (st > 2 && (size_t)st * c->stage_bytes + tail > (size_t)kMaxSmem) --st;
+  *stages = st;
+  *smem = (size_t)st * c->stage_bytes + tail;
   // Descriptor start addresses are 14-bit multiples of 16 bytes: every operand must lie in the
   // first 256 KB of shared memory, which the 227 KB limit ensures.
-  return *smem <= (size_t)kMaxSmem;
+  return *smem <= (size_t)kMaxSmem && c->ncols <= 512u;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor maps of TMA mode: the NHWC input (channels, x, y, image) with a box of 8 channels x 128
+// pixels x 1 row, and the K-major weights (channels, output channels, taps) with a box of 8
+// channels x N tile x 9 taps.  BF16, no swizzle, no interleave; rows and weights stay in bounds,
+// so the fill mode never applies.
+bool make_maps(const ConvTC& c, int batch, const void* x, const void* wt, CUtensorMap* rows, CUtensorMap* w) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t xd[4] = {(cuuint64_t)c.K, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)batch};
+  const cuuint64_t xs[3] = {(cuuint64_t)c.K * 2, (cuuint64_t)c.W * c.K * 2, (cuuint64_t)c.H * c.W * c.K * 2};
+  const cuuint32_t xb[4] = {8, (cuuint32_t)kTileM, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (enc(rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), xd, xs, xb, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t wd[3] = {(cuuint64_t)c.K, (cuuint64_t)c.N, 9};
+  const cuuint64_t ws[2] = {(cuuint64_t)c.K * 2, (cuuint64_t)c.N * c.K * 2};
+  const cuuint32_t wb[3] = {8, (cuuint32_t)c.ntile, 9};
+  return enc(w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(wt), wd, ws, wb, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S>
+int launch_s(const ConvTC& c, size_t smem, int batch, const void* x, const void* wt, const float* bias,
+             const void* addend, void* y, cudaStream_t s) {
+  CUtensorMap tm_rows, tm_w;
+  std::memset(&tm_rows, 0, sizeof(tm_rows));
+  std::memset(&tm_w, 0, sizeof(tm_w));
+  if (c.tma && !make_maps(c, batch, x, wt, &tm_rows, &tm_w)) return SUR_ERR_CUDA;
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(k_conv3x3_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess)
+      return SUR_ERR_CUDA;
+    configured = true;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3_tc<S>, kThreadsP, smem) != cudaSuccess)
+    return SUR_ERR_CUDA;
+  // At most 512 TMEM columns per SM: keep resident CTAs x columns within it.
+  const int max_ctas = (int)(512u / c.ncols);
+  if (per_sm > max_ctas) {
+    smem = (size_t)(kMaxSmem / max_ctas) & ~(size_t)1023;
+    per_sm = max_ctas;
+  }
+  if (per_sm < 1) return SUR_ERR_PARAM;
+  const long long want = (long long)(sms > 0 ? sms : 148) * per_sm;
+  const int grid = (int)(c.ntiles < want ? c.ntiles : want);
+  k_conv3x3_tc<S><<<grid, kThreadsP, smem, s>>>((const bf16*)x, (const bf16*)wt, bias, (const bf16*)addend, y, c,
+                                                 tm_rows, tm_w);
+  return cudaGetLastError() == cudaSuccess ? SUR_OK : SUR_ERR_CUDA;
 }
 
 int launch(const void* x, const void* wt, const float* bias, const void* addend, void* y, int batch, int H, int W,
            int K, int N, int relu, int out_f32, int up, cudaStream_t s) {
   ConvTC c;
   size_t smem = 0;
-  if (!plan(batch, H, W, K, N, up != 0, &c, &smem)) return SUR_ERR_PARAM;
+  int stages = 0;
+  if (!plan(batch, H, W, K, N, up != 0, &c, &smem, &stages)) return SUR_ERR_PARAM;
   c.relu = relu;
   c.out_f32 = out_f32;
-  const long long tiles = (long long)batch * c.tiles_x * c.tiles_y;
-  if (tiles > 0x7FFFFFFFll) return SUR_ERR_PARAM;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    if (e != cudaSuccess) return SUR_ERR_CUDA;
-    configured = true;
-  }
-  // At most 512 TMEM columns per SM: keep resident CTAs x columns within it (an allocation beyond
-  // it would wait for another CTA to free its columns), by asking for more shared memory if needed.
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3_tc, kThreads, smem) != cudaSuccess)
-    return SUR_ERR_CUDA;
-  const int max_ctas = (int)(512 / c.ncols);
-  if (per_sm > max_ctas) smem = (size_t)(kMaxSmem / max_ctas) & ~(size_t)1023;
-  dim3 grid((unsigned)tiles, (unsigned)(N / c.ntile));
-  k_conv3x3_tc<<<grid, kThreads, smem, s>>>((const bf16*)x, (const bf16*)wt, bias, (const bf16*)addend, y, c);
-  return cudaGetLastError() == cudaSuccess ? SUR_OK : SUR_ERR_CUDA;
+  if (stages == 4) return launch_s<4>(c, smem, batch, x, wt, bias, addend, y, s);
+  if (stages == 3) return launch_s<3>(c, smem, batch, x, wt, bias, addend, y, s);
+  return launch_s<2>(c, smem, batch, x, wt, bias, addend, y, s);
 }
 
 }  // namespace
@@ -436,7 +637,8 @@ int sur_conv3x3_tc(const void* x, const void* wt, const float* bias, const void*
 int sur_conv3x3_tc_supported(int batch, int H, int W, int K, int N, int upsampled) {
   ConvTC c;
   size_t smem = 0;
-  return plan(batch, H, W, K, N, upsampled != 0, &c, &smem) ? 1 : 0;
+  int stages = 0;
+  return plan(batch, H, W, K, N, upsampled != 0, &c, &smem, &stages) ? 1 : 0;
 }
 
 int sur_transpose_taps(const void* w, void* wt, int K, int N, void* stream) {

@@ -255,7 +255,12 @@ class UNet:
         return t
 
     def _tc(self, B, H, W, ci, co, up=0):
-        return self.tensor_cores and sur_conv3x3_tc_supported(B, H, W, ci, co, up)
+        # The tcgen05 kernel where it measured faster than the mma.sync one: rows of 128 pixels or
+        # more, staged by TMA (not upsampled).  Narrower images (three shifted copies staged by
+        # cp.async) and the upsampled decoder input ran slower on it; both kernels give the same
+        # bits (same accumulation order), so the choice changes only the time.
+        return (self.tensor_cores and not up and W >= 128 and
+                sur_conv3x3_tc_supported(B, H, W, ci, co, up))
 
     def _conv(self, x, name, B, H, W, relu, out_f32=False, key=None):
         _, ci, co = next(l for l in self.layers if l[0] == name)

@@ -302,3 +302,87 @@ def test_judge_rejects_a_drifting_prediction_and_falls_back_exactly(S, trained):
     torch.cuda.synchronize()
     solver.close()
     assert torch.equal(fin, want)
+
+
+# -------------------------------------------------------------------------------------------
+# The tcgen05 convolution (sur_conv3x3_tc): tensor memory accumulators, TMA or cp.async staging.
+
+TC_SHAPES = [  # (batch, H, W, Cin, Cout, upsampled): every staging mode and tile shape
+    (1, 16, 32, 16, 16, 0),    # copy mode (W < 128), one channel chunk
+    (2, 16, 64, 64, 64, 0),    # copy mode, four chunks
+    (1, 8, 32, 32, 256, 0),    # copy mode, two output-channel tiles
+    (2, 8, 128, 32, 32, 0),    # row mode by TMA, four rows per tile
+    (1, 8, 256, 48, 96, 0),    # row mode by TMA, two tiles per row, 96 output channels (2 rows per tile)
+    (2, 16, 32, 64, 32, 1),    # copy mode through the 2x upsampling, with the skip addend
+    (2, 8, 256, 32, 16, 1),    # row mode through the upsampling (cp.async), with the addend
+]
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_tcgen05_conv_matches_oracle(S, shape):
+    """The tcgen05 convolution against the FP64 oracle on BF16-exact inputs: FP32 output within
+    1e-5 relative (accumulation order only), BF16 output with the addend within a BF16 rounding.
+    The bounded waits of the kernel did not give up (sur_check)."""
+    import torch
+    B, H, W, K, N, up = shape
+    rng = np.random.default_rng(B * 1000 + H * 10 + W + K + N + up)
+    s = torch.cuda.current_stream().cuda_stream
+    assert S.sur_conv3x3_tc_supported(B, H, W, K, N, up)
+    if up:
+        x, xc = _bf(rng, (B, H // 2, W // 2, K))
+        xn = np.repeat(np.repeat(xc, 2, axis=1), 2, axis=2)
+    else:
+        x, xn = _bf(rng, (B, H, W, K))
+    w, wn = _bf(rng, (9, K, N), 0.2)
+    wt = torch.empty((9, N, K), dtype=torch.bfloat16, device="cuda")
+    S.sur_transpose_taps(w, wt, K, N, s)
+    bias = torch.tensor(rng.standard_normal(N), dtype=torch.float32).cuda()
+    bn = bias.cpu().numpy().astype(np.float64)
+    if up:
+        add, addn = _bf(rng, (B, H, W, N))
+        y = torch.empty((B, H, W, N), dtype=torch.bfloat16, device="cuda")
+        S.sur_conv3x3_tc(x, wt, bias, add, y, B, H, W, K, N, 0, 0, 1, s)
+        assert _rel(y.float().cpu().numpy(), U.conv3x3(xn, wn, bn, relu=False) + addn) < 4e-3
+    else:
+        y = torch.empty((B, H, W, N), dtype=torch.float32, device="cuda")
+        S.sur_conv3x3_tc(x, wt, bias, None, y, B, H, W, K, N, 1, 1, 0, s)
+        assert _rel(y.cpu().numpy(), U.conv3x3(xn, wn, bn, relu=True)) < 1e-5
+    assert S.sur_check(s) == S.SUR_OK
+
+
+def test_tcgen05_conv_refuses_shapes_it_cannot_tile(S):
+    """Shapes outside the kernel's tiling are refused with SUR_ERR_PARAM and reported unsupported:
+    a width neither a multiple of 128 nor a power of two dividing it, a height not a multiple of the
+    tile's rows, channels not multiples of 16, more than 128 output channels not a multiple of 128."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    x = torch.zeros((1, 16, 96, 32), dtype=torch.bfloat16, device="cuda")
+    wt = torch.zeros((9, 32, 32), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros((1, 16, 96, 32), dtype=torch.bfloat16, device="cuda")
+    for bad in ((1, 16, 96, 32, 32), (1, 6, 32, 32, 32), (1, 16, 32, 24, 32), (1, 16, 32, 32, 160)):
+        assert not S.sur_conv3x3_tc_supported(*bad, 0)
+    with pytest.raises(S.SurError):
+        S.sur_conv3x3_tc(x, wt, None, None, y, 1, 16, 96, 32, 32, 0, 0, 0, s)
+
+
+def test_network_forward_same_on_both_tensor_core_paths(S):
+    """The U-Net forward with its 256^2 and 128^2 convolutions on the tcgen05 kernel equals the
+    forward on the mma.sync kernels bit for bit: both accumulate every 16-channel chunk tap by tap
+    in the same order on the same tensor-core dot products."""
+    import torch
+    net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    s = torch.cuda.current_stream().cuda_stream
+    net.w["out"].copy_(torch.randn(net.w["out"].shape, device="cuda", generator=g) * 0.05)
+    S.sur_cast_bf16(net.w["out"], net.wb["out"], s)
+    S.sur_transpose_taps(net.wb["out"], net.wt["out"], 32, 16, s)
+    x = (torch.randn((2, 256, 256, 16), device="cuda", generator=g) * 0.5).to(torch.bfloat16)
+    base = x[..., :3].float().contiguous()
+    net.tensor_cores = True
+    p1 = net.forward(x, base).clone()
+    net.tensor_cores = False
+    p0 = net.forward(x, base).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p0)
+    assert float((p0 - base).abs().max()) > 1e-3  # the network does change the state
+    assert S.sur_check(s) == S.SUR_OK

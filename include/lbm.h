@@ -97,7 +97,8 @@ typedef enum { LBM_FORCE_UNIFORM = 0, LBM_FORCE_PHASE_L = 1 } lbm_force_mode;
  * so that every stored value is unbiased; rounding errors then average out instead of adding up
  * where neighbouring nodes hold similar values (a slow shear).  The random bits are a counter-based
  * stream of (seed, time step, node), so runs are reproducible.  Needs FP16S or BF16S storage; not
- * available with the staged kernel or in batches. */
+ * available with the staged kernel.  In a batch each member draws the stream a single lattice with
+ * its seed draws (the step's key is derived on the device from the batch's step counter). */
 typedef enum { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 } lbm_rounding;
 
 /* The problem statement, in the paper's symbols (paragraph after Eq. 14 and the set-ups of

@@ -59,7 +59,7 @@ size_t max_items(const std::vector<HostGeometry>& geo) {
 
 struct Layout {
   std::vector<size_t> off, copy;
-  size_t members_off, phys_off, items_off, flags_off, total;
+  size_t members_off, phys_off, items_off, flags_off, tcount_off, total;
   size_t nitems_max;
 };
 
@@ -82,6 +82,8 @@ Layout layout(int prec, const std::vector<HostGeometry>& geo) {
   o = align_up(o + sizeof(BatchItem) * L.nitems_max);
   L.flags_off = o;
   o = align_up(o + sizeof(int) * count);
+  L.tcount_off = o;  // the time step in two parity slots (see launch_step_batch)
+  o = align_up(o + 2 * sizeof(long long));
   L.total = o;
   return L;
 }
@@ -176,7 +178,8 @@ bool members_fit_32(const lbm_batch* b) {
 cudaError_t launch_one(lbm_batch* b, int parity) {
   return launch_step_batch(b->prec, b->tile, (const BatchItem*)(b->arena + b->L.items_off), b->nitems,
                            (const BatchMember*)(b->arena + b->L.members_off), b->arena + b->L.phys_off, parity,
-                           (int*)(b->arena + b->L.flags_off), b->grid, members_fit_32(b), b->stream);
+                           (int*)(b->arena + b->L.flags_off), (long long*)(b->arena + b->L.tcount_off), b->grid,
+                           members_fit_32(b), b->stream);
 }
 
 cudaError_t build_graph(lbm_batch* b) {
@@ -207,8 +210,6 @@ int lbm_batch_state_bytes(const lbm_params* params, int count, size_t* bytes) {
     HostPhys ph;
     const char* msg = validate_params(&params[m], &geo[m], &ph);
     if (msg) return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: member %d: %s", m, msg);
-    if (params[m].rounding != LBM_ROUND_NEAREST)
-      return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: member %d: stochastic rounding is not available in batches", m);
     if (params[m].prec != params[0].prec)
       return fail(nullptr, LBM_ERR_PARAM, "lbm_batch_state_bytes: all members need the same precision");
   }
@@ -232,8 +233,6 @@ int lbm_batch_init(const lbm_params* params, int count, const double* const* phi
   for (int m = 0; m < count; ++m) {
     const char* msg = validate_params(&params[m], &b->geo[m], &b->phys[m]);
     if (!msg && params[m].prec != b->prec) msg = "all members need the same precision";
-    // a batch replays captured CUDA graphs, whose launches cannot carry a new key every step
-    if (!msg && params[m].rounding != LBM_ROUND_NEAREST) msg = "stochastic rounding is not available in batches";
     if (!msg && !phi0[m]) msg = "phi0 is NULL";
     if (msg) {
       fail(nullptr, LBM_ERR_PARAM, "lbm_batch_init: member %d: %s", m, msg);
@@ -292,6 +291,7 @@ int lbm_batch_init(const lbm_params* params, int count, const double* const* phi
                         cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = upload_phys(b->prec, b->phys.data(), count, b->arena + b->L.phys_off, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + b->L.flags_off, 0, sizeof(int) * count, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + b->L.tcount_off, 0, 2 * sizeof(long long), b->stream);
   if (e == cudaSuccess) {
     StepTile t{64, 4, 0, 0, 1};
     int target = 4096;

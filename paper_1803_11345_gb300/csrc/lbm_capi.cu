@@ -66,20 +66,7 @@ std::string tune_key(const lbm_lattice* h, int sms) {
 
 char* state_buf(lbm_lattice* h) { return h->buf + (size_t)h->cur * h->pop_bytes; }
 
-// Key of the stochastic-rounding stream for time step t: the 32-bit finaliser of MurmurHash3
-// (A. Appleby) over the seed and both halves of t; never 0 (0 means round to nearest).
-uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
-uint32_t step_key(uint32_t seed, long long t) {
-  const uint32_t k = fmix32(fmix32(seed ^ 0x5bd1e995u) + (uint32_t)t) ^ fmix32((uint32_t)((unsigned long long)t >> 32));
-  return k ? k : 1u;
-}
+uint32_t step_key(uint32_t seed, long long t) { return sr_step_key(seed, t); }
 char* other_buf(lbm_lattice* h) { return h->buf + (size_t)(1 - h->cur) * h->pop_bytes; }
 
 }  // namespace

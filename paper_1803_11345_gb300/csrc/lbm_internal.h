@@ -24,6 +24,24 @@ struct HostPhys {
   int wait_probes = -1;  // staged kernel: probes before a bulk-copy wait gives up (< 0: the default)
 };
 
+// Key of the stochastic-rounding stream for time step t: the 32-bit finaliser of MurmurHash3
+// (A. Appleby) over the seed and both halves of t; never 0 (0 means round to nearest).  The same
+// function on the host (single lattices) and on the device (batches, whose captured graphs derive
+// the key from a step counter in device memory), so a batch member draws a lattice's stream.
+__host__ __device__ inline uint32_t sr_fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__host__ __device__ inline uint32_t sr_step_key(uint32_t seed, long long t) {
+  const uint32_t k = sr_fmix32(sr_fmix32(seed ^ 0x5bd1e995u) + (uint32_t)t) ^
+                     sr_fmix32((uint32_t)((unsigned long long)t >> 32));
+  return k ? k : 1u;
+}
+
 // Bits of a lattice's device status word: a node produced a non-finite rho or phi; a bounded
 // device-side wait gave up (the step that set it is incomplete).
 constexpr int kFlagNonfinite = 1;
@@ -58,9 +76,11 @@ cudaError_t upload_phys(int prec, const HostPhys* host, int count, void* dev, cu
 // One time step of every member: items[] dealt round-robin to `grid` resident CTAs.  parity 0:
 // state in buf0 -> buf1; parity 1: buf1 -> buf0.  flags[m] collects member m's non-finite flag.
 // off32: every member's population buffer is under 4 GiB (32-bit plane offsets).
+// tcount[2]: the batch's time step, tcount[parity] current; each launch writes its successor into
+// tcount[1 - parity] (the stochastic-rounding key of a member is derived from it on the device).
 cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
                               const BatchMember* members, const void* phys, int parity, int* flags,
-                              int grid, bool off32, cudaStream_t s);
+                              long long* tcount, int grid, bool off32, cudaStream_t s);
 int batch_blocks_per_sm(int prec, const StepTile& t);
 
 // Parameter validation shared by the single-lattice and batched entry points (message or NULL),

@@ -385,17 +385,19 @@ namespace {
 
 template <int PREC, int BX, int BY>
 cudaError_t batch_bxby(const BatchItem* items, int nitems, const BatchMember* members, const void* phys,
-                       int parity, int* flags, int grid, bool off32, cudaStream_t s) {
-  if (off32) return launch_k_step_batch<PREC, BX, BY, true>(items, nitems, members, phys, parity, flags, grid, s);
-  return launch_step_batch64(PREC, BX, BY, items, nitems, members, phys, parity, flags, grid, s);
+                       int parity, int* flags, long long* tcount, int grid, bool off32, cudaStream_t s) {
+  if (off32)
+    return launch_k_step_batch<PREC, BX, BY, true>(items, nitems, members, phys, parity, flags, tcount, grid, s);
+  return launch_step_batch64(PREC, BX, BY, items, nitems, members, phys, parity, flags, tcount, grid, s);
 }
 
 template <int PREC>
 cudaError_t batch_prec(const StepTile& t, const BatchItem* items, int nitems, const BatchMember* members,
-                       const void* phys, int parity, int* flags, int grid, bool off32, cudaStream_t s) {
+                       const void* phys, int parity, int* flags, long long* tcount, int grid, bool off32,
+                       cudaStream_t s) {
 #define LBM_CASE(X, Y)                                                                                   \
   if (t.bx == X && t.by == Y)                                                                            \
-    return batch_bxby<PREC, X, Y>(items, nitems, members, phys, parity, flags, grid, off32, s);
+    return batch_bxby<PREC, X, Y>(items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
   LBM_TILES(LBM_CASE)
 #undef LBM_CASE
   return cudaErrorInvalidValue;
@@ -415,12 +417,12 @@ int batch_occ(int bx, int by) {
 
 cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
                               const BatchMember* members, const void* phys, int parity, int* flags,
-                              int grid, bool off32, cudaStream_t s) {
+                              long long* tcount, int grid, bool off32, cudaStream_t s) {
   switch (prec) {
-    case 0: return batch_prec<0>(t, items, nitems, members, phys, parity, flags, grid, off32, s);
-    case 1: return batch_prec<1>(t, items, nitems, members, phys, parity, flags, grid, off32, s);
-    case 2: return batch_prec<2>(t, items, nitems, members, phys, parity, flags, grid, off32, s);
-    case 3: return batch_prec<3>(t, items, nitems, members, phys, parity, flags, grid, off32, s);
+    case 0: return batch_prec<0>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
+    case 1: return batch_prec<1>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
+    case 2: return batch_prec<2>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
+    case 3: return batch_prec<3>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
   }
   return cudaErrorInvalidValue;
 }

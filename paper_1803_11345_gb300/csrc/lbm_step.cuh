@@ -206,13 +206,19 @@ k_step_edge(const char* __restrict__ src, char* __restrict__ dst, const Geometry
 template <int PREC, int BX, int BY, bool OFF32>
 __global__ void __launch_bounds__(BX * BY)
 k_step_batch(const BatchItem* __restrict__ items, const int nitems, const BatchMember* __restrict__ members,
-             const Phys<typename Pop<PREC>::C>* __restrict__ phys, const int parity, int* __restrict__ flags) {
+             const Phys<typename Pop<PREC>::C>* __restrict__ phys, const int parity, int* __restrict__ flags,
+             long long* __restrict__ tcount) {
   using C = typename Pop<PREC>::C;
   __shared__ C sphi[3 * BY + 1][BX + 2];
+  // The batch's time step: read from the slot of this parity; the successor goes to the other
+  // slot, which only the next launch reads (a captured graph replays these launches unchanged).
+  const long long t = tcount[parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) tcount[1 - parity] = t + 1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BatchItem w = items[it];
     const BatchMember m = members[w.member];
-    const Phys<C> ph = phys[w.member];
+    Phys<C> ph = phys[w.member];
+    if (ph.rounding) ph.sr_key = sr_step_key(ph.seed, t);  // the key a single lattice uses at step t
     Geometry geo;
     geo.nx = m.nx;
     geo.ny = m.ny;
@@ -242,10 +248,11 @@ cudaError_t launch_k_step(const HostGeometry& g, const HostPhys& p, int rows, co
 
 template <int PREC, int BX, int BY, bool OFF32>
 cudaError_t launch_k_step_batch(const BatchItem* items, int nitems, const BatchMember* members, const void* phys,
-                                int parity, int* flags, int grid, cudaStream_t s) {
+                                int parity, int* flags, long long* tcount, int grid, cudaStream_t s) {
   using C = typename Pop<PREC>::C;
   k_step_batch<PREC, BX, BY, OFF32><<<grid, dim3(BX, BY), 0, s>>>(items, nitems, members,
-                                                                   static_cast<const Phys<C>*>(phys), parity, flags);
+                                                                   static_cast<const Phys<C>*>(phys), parity, flags,
+                                                                   tcount);
   return cudaGetLastError();
 }
 
@@ -253,7 +260,7 @@ cudaError_t launch_k_step_batch(const BatchItem* items, int nitems, const BatchM
 cudaError_t launch_step64(int prec, int bx, int by, const HostGeometry& g, const HostPhys& p, int rows,
                           const char* src, char* dst, int* flag, cudaStream_t s);
 cudaError_t launch_step_batch64(int prec, int bx, int by, const BatchItem* items, int nitems,
-                                const BatchMember* members, const void* phys, int parity, int* flags, int grid,
-                                cudaStream_t s);
+                                const BatchMember* members, const void* phys, int parity, int* flags,
+                                long long* tcount, int grid, cudaStream_t s);
 
 }  // namespace lbmch

@@ -19,10 +19,10 @@ cudaError_t step64_prec(int bx, int by, const HostGeometry& g, const HostPhys& p
 
 template <int PREC>
 cudaError_t batch64_prec(int bx, int by, const BatchItem* items, int nitems, const BatchMember* members,
-                         const void* phys, int parity, int* flags, int grid, cudaStream_t s) {
+                         const void* phys, int parity, int* flags, long long* tcount, int grid, cudaStream_t s) {
 #define LBM_CASE(X, Y)           \
   if (bx == X && by == Y)        \
-    return launch_k_step_batch<PREC, X, Y, false>(items, nitems, members, phys, parity, flags, grid, s);
+    return launch_k_step_batch<PREC, X, Y, false>(items, nitems, members, phys, parity, flags, tcount, grid, s);
   LBM_TILES(LBM_CASE)
 #undef LBM_CASE
   return cudaErrorInvalidValue;
@@ -42,13 +42,13 @@ cudaError_t launch_step64(int prec, int bx, int by, const HostGeometry& g, const
 }
 
 cudaError_t launch_step_batch64(int prec, int bx, int by, const BatchItem* items, int nitems,
-                                const BatchMember* members, const void* phys, int parity, int* flags, int grid,
-                                cudaStream_t s) {
+                                const BatchMember* members, const void* phys, int parity, int* flags,
+                                long long* tcount, int grid, cudaStream_t s) {
   switch (prec) {
-    case 0: return batch64_prec<0>(bx, by, items, nitems, members, phys, parity, flags, grid, s);
-    case 1: return batch64_prec<1>(bx, by, items, nitems, members, phys, parity, flags, grid, s);
-    case 2: return batch64_prec<2>(bx, by, items, nitems, members, phys, parity, flags, grid, s);
-    case 3: return batch64_prec<3>(bx, by, items, nitems, members, phys, parity, flags, grid, s);
+    case 0: return batch64_prec<0>(bx, by, items, nitems, members, phys, parity, flags, tcount, grid, s);
+    case 1: return batch64_prec<1>(bx, by, items, nitems, members, phys, parity, flags, tcount, grid, s);
+    case 2: return batch64_prec<2>(bx, by, items, nitems, members, phys, parity, flags, tcount, grid, s);
+    case 3: return batch64_prec<3>(bx, by, items, nitems, members, phys, parity, flags, tcount, grid, s);
   }
   return cudaErrorInvalidValue;
 }

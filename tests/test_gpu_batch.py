@@ -58,6 +58,51 @@ def test_batch_members_equal_single_lattices(lbm, prec, tol):
         assert rel_err(fb, fs) <= tol and abs_err(gb, gs) <= tol * max(1.0, float(np.abs(gs).max())), m
 
 
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_batch_stochastic_rounding_follows_single_lattices(lbm, prec):
+    """Batches round stochastically too: the key of a step is derived on the device from the
+    batch's step counter (two parity slots, so graph replays advance it) by the function a single
+    lattice uses on the host, so a member draws the single lattice's random stream.  One step from
+    the same state stores the same values as a single lattice of the same seed and tile, except
+    where the two separately compiled kernels' FP32 results straddle a rounding decision (at most
+    1% of the moving populations, by one 16-bit unit); over 61 steps, through graph replays, phi
+    stays within 1e-3 of the single lattice's, and the rounding does change with the step (the
+    batch differs from the same batch rounded to nearest)."""
+    mem = [(phi0, dict(kw, rounding=lbm.LBM_ROUND_STOCHASTIC, seed=7 + k))
+           for k, (phi0, kw) in enumerate(_members()) if phi0.shape[0] >= 40]
+    bat = lbm.Batch(mem, prec=prec)
+    near = lbm.Batch([(p0, dict(kw, rounding=lbm.LBM_ROUND_NEAREST)) for p0, kw in mem], prec=prec)
+    bx, by = bat.tile[:2]
+    singles = [lbm.Lattice(phi0, prec=prec, **kw) for phi0, kw in mem]
+    for s in singles:
+        s.set_kernel(lbm.LBM_KERNEL_GENERIC, bx, by, 0, 0)
+    bat.step(1)
+    for s in singles:
+        s.step(1)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    rel = 2.0 ** -10 if prec == "fp16s" else 2.0 ** -7
+    for m, s in enumerate(singles):
+        fb, gb = bat.populations(m)
+        fs, gs = s.populations()
+        for k, (a, b) in enumerate(((fb[1:] - w[1:], fs[1:] - w[1:]), (gb[1:], gs[1:]))):
+            d = np.abs(a - b)
+            assert np.mean(d > 0) <= 0.01, (m, k, np.mean(d > 0))
+            assert np.all(d <= rel * np.maximum(np.maximum(np.abs(a), np.abs(b)), 2.0 ** -14) * 1.0001), (m, k)
+    for n in (36, 16, 8):
+        bat.step(n)
+        near.step(n + (1 if n == 36 else 0))
+        for s in singles:
+            s.step(n)
+    assert bat.time == 61 and near.time == 61
+    differs = False
+    for m, s in enumerate(singles):
+        pb = bat.fields(m)[3]
+        assert abs_err(pb, s.fields()[3]) <= 1e-3, m
+        differs |= not np.array_equal(pb, near.fields(m)[3])
+    assert differs
+    assert bat.check()[0] == lbm.LBM_OK
+
+
 def test_batch_fp64_member_matches_oracle(lbm, orc):
     mem = _members()[:4]
     bat = lbm.Batch(mem, prec="fp64")

@@ -101,13 +101,16 @@ def test_wall_gradient_matches_the_oracle(lbm, orc):
     assert math.isnan(lbm.lbm_wall_gradient(1.0, 0.04, 0.0))
 
 
-def test_stochastic_rounding_only_for_16bit_storage_and_single_lattices(lbm):
-    """Stochastic rounding is accepted for FP16S / BF16S storage and refused for FP32 / FP64 (no
-    16-bit rounding to randomise) and in batches, whose captured graph launches cannot carry a new
-    random key every step."""
+def test_stochastic_rounding_only_for_16bit_storage(lbm):
+    """Stochastic rounding is accepted for FP16S / BF16S storage, for single lattices and batches
+    (whose step keys come from a device-side step counter), and refused for FP32 / FP64 (no 16-bit
+    rounding to randomise)."""
     for prec in (lbm.LBM_FP16S, lbm.LBM_BF16S):
-        assert lbm.lbm_state_bytes(lbm.lbm_default_params(nx=16, ny=16, prec=prec, rounding=1, seed=7)) > 0
-    p = lbm.lbm_default_params(nx=16, ny=16, prec=lbm.LBM_FP16S, rounding=1)
-    with pytest.raises(lbm.LbmError) as ei:
-        lbm.lbm_batch_state_bytes([p, p])
-    assert ei.value.status == lbm.LBM_ERR_PARAM
+        p = lbm.lbm_default_params(nx=16, ny=16, prec=prec, rounding=1, seed=7)
+        assert lbm.lbm_state_bytes(p) > 0
+        assert lbm.lbm_batch_state_bytes([p, p]) > 0
+    for prec in (lbm.LBM_FP32, lbm.LBM_FP64):
+        p = lbm.lbm_default_params(nx=16, ny=16, prec=prec, rounding=1)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_batch_state_bytes([p, p])
+        assert ei.value.status == lbm.LBM_ERR_PARAM

@@ -608,16 +608,14 @@ def surrogate_form(args):
     ntr, nte, wins = args.sur_train, args.sur_test, args.sur_windows
     t0 = _t.time()
     members = S.spinodal_members(ntr + nte, n, seed=SEED)
-    traj = S.generate_trajectories(members, K, wins)
-    states = S.trajectory_states(traj)
-    del traj
+    states = S.generate_states(members, K, wins)
     t_data = _t.time() - t0
     net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=SEED)
     t0 = _t.time()
     hist = S.train_states(net, states[:, :ntr], args.sur_iters, args.sur_batch, lr=1e-3, seed=SEED, log_every=100)
     torch.cuda.synchronize()
     t_train = _t.time() - t0
-    e, p = S.one_window_errors(net, states[:, ntr:])
+    e, p = S.one_window_errors(net, states[:, ntr:][:min(wins, 40) + 1])
     test_members = members[ntr:]
     k0 = min(10, wins)
     st0 = states[k0, ntr:].contiguous()
@@ -642,7 +640,8 @@ def surrogate_form(args):
             "thresholds": {"phi_rms": judge.phi_err, "sum_phi_drift_per_node": judge.drift, "audit_every": judge.audit_every},
             "one_window_phi_rms_median": float(np.median(e)), "persistence_one_window_median": float(np.median(p)),
             "ms_forward_graph": ms_fwd, "ms_solver_window": t_solver * 1e3 / args.sur_rollout,
-            "training": {"trajectories": ntr, "windows": wins, "iters": args.sur_iters, "batch": args.sur_batch,
+            "training": {"trajectories": ntr, "windows": wins, "steps_per_trajectory": wins * K,
+                         "iters": args.sur_iters, "batch": args.sur_batch,
                          "seconds_data": t_data, "seconds_train": t_train, "loss": hist[::3]},
             "what": "closed-loop rollout of held-out lattices, wall time including the judge's GPU reductions, "
                     "its per-window host read of the sums, every audit and fallback; solver alone: the batched "
@@ -689,11 +688,11 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
     ap.add_argument("--sur-n", type=int, default=256)
     ap.add_argument("--sur-k", type=int, default=50, help="solver steps per surrogate window")
-    ap.add_argument("--sur-windows", type=int, default=30, help="windows per training trajectory")
-    ap.add_argument("--sur-train", type=int, default=12, help="training trajectories")
+    ap.add_argument("--sur-windows", type=int, default=30, help="windows per trajectory (x K solver steps)")
+    ap.add_argument("--sur-train", type=int, default=248, help="training trajectories")
     ap.add_argument("--sur-test", type=int, default=8, help="held-out lattices (rollout batch)")
-    ap.add_argument("--sur-iters", type=int, default=800)
-    ap.add_argument("--sur-batch", type=int, default=8)
+    ap.add_argument("--sur-iters", type=int, default=2000)
+    ap.add_argument("--sur-batch", type=int, default=16)
     ap.add_argument("--sur-rollout", type=int, default=16, help="windows of the judged rollout")
     ap.add_argument("--sur-audit", type=int, default=8, help="audit every this many windows")
     ap.add_argument("--count", type=int, default=256, help="members of the batched sweep")

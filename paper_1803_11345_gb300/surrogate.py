@@ -449,6 +449,32 @@ def generate_trajectories(members, steps_per_window, windows, prec="fp32", strea
     return out
 
 
+def generate_states(members, steps_per_window, windows, prec="fp32", stream=None, chunk=64):
+    """Run the batched solver on `members` [(phi0, params)] and keep, on the device, the state of
+    every member at every window boundary: tensor (windows + 1, M, H, W, 3) FP32 (phi, ux, uy).
+    Members are stepped in batches of `chunk`; states go from the solver to the tensor with
+    lbm_batch_get_state, so nothing crosses the host."""
+    import torch
+    M = len(members)
+    ny, nx = members[0][0].shape
+    out = torch.empty((windows + 1, M, ny, nx, 3), dtype=torch.float32, device="cuda")
+    stream = stream if stream is not None else torch.cuda.Stream()
+    for c0 in range(0, M, chunk):
+        part = members[c0:c0 + chunk]
+        bat = lbm.Batch(part, prec=prec, stream=stream)
+        for k in range(windows + 1):
+            if k:
+                bat.step(steps_per_window)
+            for m in range(len(part)):
+                bat.get_state(m, out[k, c0 + m].data_ptr())
+        st, flags = bat.check()
+        bat.close()
+        if st != lbm.LBM_OK:
+            raise lbm.LbmError(st, f"non-finite members {flags}")
+    torch.cuda.synchronize()
+    return out
+
+
 class Judge:
     """Decides whether the surrogate's prediction for a window is kept, with what is known while
     the model runs (rollout()):

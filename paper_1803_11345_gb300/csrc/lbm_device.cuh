@@ -530,6 +530,12 @@ __device__ __forceinline__ C lat_dot(int i, C vx, C vy) {
   return cx > 0 ? vx - vy : vy - vx;
 }
 
+// 1 / x for the collision's two runtime reciprocals (1/rho and the relaxation frequency).
+template <class C>
+__device__ __forceinline__ C recip(C x) {
+  return C(1) / x;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Collision of one node.  Inputs: pulled f as deviations d_i = f_i - w_i from the rest state,
 // pulled g; phi = sum g; the Eq. 12 stencils dx, dy, lap of phi.  Outputs overwrite f (again as
@@ -548,7 +554,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
   const C rho = C(1) + drho;
   const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-  const C inv_rho = C(1) / rho;
+  const C inv_rho = recip(rho);
   // Body force (Guo's scheme): the velocity carries half the force, u = (j + F/2)/rho.
   C Fx = C(0), Fy = C(0);
   if (ph.forced) body_force(ph, phi, Fx, Fy);
@@ -564,7 +570,7 @@ __device__ __forceinline__ C collide(const Phys<C>& ph, C f[9], C g[9], C phi, C
   // Relaxation frequency of f for this phi (paragraph after Eq. 14).
   C om;
   if (ph.visc == 0) om = ph.omega_g + C(0.5) * (phi + C(1)) * (ph.omega_l - ph.omega_g);
-  else om = C(1) / (ph.tau_g + C(0.5) * (phi + C(1)) * (ph.tau_l - ph.tau_g));
+  else om = recip(ph.tau_g + C(0.5) * (phi + C(1)) * (ph.tau_l - ph.tau_g));
 
   if (!ph.bgk) {
     // Pre-collision central moments k3, k4, k5 (Eq. 15 basis, k = T^T f) from the raw second

@@ -74,6 +74,13 @@ __device__ __forceinline__ void st_word(char* __restrict__ b, unsigned byte_off,
   *reinterpret_cast<unsigned int*>(b + byte_off) = v;
 }
 
+// s += (float)h for a 16-bit pattern h by one mixed-precision add: the conversion is exact, so the
+// sum is the one converting first and adding in FP32 gives.
+template <int PREC> __device__ __forceinline__ void mix_add(float& s, unsigned short h) {
+  if constexpr (PREC == 2) asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s) : "h"(h));
+  else asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(s) : "h"(h));
+}
+
 // Both lanes onto the grid of step 2^-24 (k = kGridF) or 2^-23 (k = kGridG) by the one-node
 // kernel's snap (PopHalf), in packed instructions.
 __device__ __forceinline__ F2 grid_snap2(F2 v, float k) { return f2_sub(f2_add(v, F2(k)), F2(k)); }
@@ -173,8 +180,16 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   const bool colv = 2 * tx < xv;
   const int xm2 = (x == 0) ? nx - 2 : x - 2;
   const int xp2 = (x + 2 >= nx) ? 0 : x + 2;
-  // Threads tx == 0 and tx == BX-1 also pull the single halo node left / right of the strip.
-  const bool halo = tx == 0 || tx == BX - 1;
+  // Halo phi, the nodes left and right of the strip.  With walls, threads tx == 0 and tx == BX-1
+  // pull the halo node with the one-node code (bounce-back on the wall rows).  On periodic
+  // lattices the pair's own loads serve: the node left of the strip (x0 - 1, thread 0) takes six
+  // of its nine g values from words thread 0 loads anyway (c_x = +1: low halves of the words at
+  // x - 2; c_x = -1: low halves of the words at x), the node right of it (thread of the last
+  // pair) the high halves of its words at x and x + 2; the rest population and the two c_x = 0
+  // directions are three extra loads.
+  const bool halo = WALLS && (tx == 0 || tx == BX - 1);
+  const bool hL = !WALLS && tx == 0;
+  const bool hR = !WALLS && colv && 2 * tx + 2 == xv;
   const int hx = (tx == 0) ? ((x0 == 0) ? nx - 1 : x0 - 1) : ((x0 + xv == nx) ? 0 : x0 + xv);
   const int hcol = (tx == 0) ? 0 : xv + 1;
 
@@ -221,6 +236,47 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
   RawPair gA, gB, fA;
   RawPairLoad gC, fB;  // in flight
   R hB[9];
+  uint32_t eL0 = 0, eL2 = 0, eL4 = 0, eR0 = 0, eR2 = 0, eR4 = 0;  // the halo nodes' extra loads
+  auto own_ld = [&](int r, int col, uint32_t& e0, uint32_t& e2, uint32_t& e4) {
+    const int y = wrap(r);
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    e0 = __float_as_uint(__ldg(reinterpret_cast<const float*>(
+        src + ((unsigned)(P::kRestFirst + 1) * pl.n + (unsigned)(y * pitch + col)) * 4u)));
+    e2 = __ldg(reinterpret_cast<const unsigned short*>(src + (9u * pl.n + (unsigned)(ym * pitch + col)) * 2u));
+    e4 = __ldg(reinterpret_cast<const unsigned short*>(src + (11u * pl.n + (unsigned)(yp * pitch + col)) * 2u));
+  };
+  auto own_put = [&](int r, const RawPairLoad& l, uint32_t e0, uint32_t e2, uint32_t e4, bool right) {
+    float v[9];
+    v[0] = __uint_as_float(e0);
+    v[2] = P::h2f(e2);
+    v[4] = P::h2f(e4);
+    if (!right) {
+      v[1] = P::h2f(l.e[side_index(1)]);
+      v[5] = P::h2f(l.e[side_index(5)]);
+      v[8] = P::h2f(l.e[side_index(8)]);
+      v[3] = P::h2f(l.w[2]);
+      v[6] = P::h2f(l.w[5]);
+      v[7] = P::h2f(l.w[6]);
+    } else {
+      v[1] = P::h2f(l.w[0] >> 16);
+      v[5] = P::h2f(l.w[4] >> 16);
+      v[8] = P::h2f(l.w[7] >> 16);
+      v[3] = P::h2f(l.e[side_index(3)] >> 16);
+      v[6] = P::h2f(l.e[side_index(6)] >> 16);
+      v[7] = P::h2f(l.e[side_index(7)] >> 16);
+    }
+    sphi[slot(r)][right ? xv + 1 : 0] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+  };
+  auto own_now = [&](int r) {  // pipeline start: loads and sums at once, from the g words in gC
+    if (hL) {
+      own_ld(r, xm2 + 1, eL0, eL2, eL4);
+      own_put(r, gC, eL0, eL2, eL4, false);
+    }
+    if (hR) {
+      own_ld(r, xp2, eR0, eR2, eR4);
+      own_put(r, gC, eR0, eR2, eR4, true);
+    }
+  };
   {
     const int r = y0 + ty;
     if (r <= y1) {
@@ -228,6 +284,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
         pull_g2(r, gC);
         finish(gC, gA);
         put_phi(r, gA);
+        own_now(r);
       }
       if (halo) {
         hBd = pull_h(r, hB);
@@ -240,6 +297,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
         pull_g2(y0 - 1, gC);
         finish(gC, gt);
         put_phi(y0 - 1, gt);
+        own_now(y0 - 1);
       }
       if (halo) {
         R ht[9];
@@ -252,6 +310,7 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       if (colv) {
         pull_g2(rb, gC);
         finish(gC, gB);
+        own_now(rb);
       }
       if (halo) hBd = pull_h(rb, hB);
     }
@@ -267,6 +326,10 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
     const int rc = Y + 2 * BY + ty;  // g issued now
     const bool act = colv && r < y1 && !wall_row(r);
     if (rc <= y1 && colv) pull_g2(rc, gC);
+    if (rc <= y1) {
+      if (hL) own_ld(rc, xm2 + 1, eL0, eL2, eL4);
+      if (hR) own_ld(rc, xp2, eR0, eR2, eR4);
+    }
     if (rb < y1 && colv) pull_f2(rb, fB);
     if (rb <= y1) {
       if (colv) put_phi(rb, gB);
@@ -303,8 +366,10 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
       auto put = [&](int i, uint32_t wf, uint32_t wg) {
         st_word(dst, ((unsigned)(i - 1) * pl.n + e) * 2u, wf);
         st_word(dst, ((unsigned)(7 + i) * pl.n + e) * 2u, wg);
-        sf += F2(Pack<PREC>::unpack(wf));
-        sg += F2(Pack<PREC>::unpack(wg));
+        mix_add<PREC>(sf.v.x, (unsigned short)(wf & 0xFFFFu));
+        mix_add<PREC>(sf.v.y, (unsigned short)(wf >> 16));
+        mix_add<PREC>(sg.v.x, (unsigned short)(wg & 0xFFFFu));
+        mix_add<PREC>(sg.v.y, (unsigned short)(wg >> 16));
       };
       const uint32_t key = ph.sr_key;
       if (!key) {  // one uniform branch: the round-to-nearest loop carries no stochastic code
@@ -336,6 +401,10 @@ __device__ __forceinline__ void step_pair_tile(const char* __restrict__ src, cha
     }
     gA = gB;
     finish(gC, gB);  // the loads issued at the top of this band have had the band to arrive
+    if (rc <= y1) {  // the halo phi of row rc, into a ring slot no stencil reads this band
+      if (hL) own_put(rc, gC, eL0, eL2, eL4, false);
+      if (hR) own_put(rc, gC, eR0, eR2, eR4, true);
+    }
     finish(fB, fA);
   }
 }

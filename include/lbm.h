@@ -191,7 +191,8 @@ LBM_API int lbm_set_populations(lbm_lattice* h, const double* f, const double* g
  * usable, but its state is undefined until lbm_set_populations restores one (a checkpoint). */
 LBM_API int lbm_check(lbm_lattice* h);
 
-/* Probes a bulk-copy wait of the staged kernel (LBM_KERNEL_STAGED) makes before it gives up.
+/* Probes a bulk-copy wait of the staged kernels (LBM_KERNEL_STAGED, LBM_KERNEL_PAIR_STAGED) makes
+ * before it gives up.
  * probes < 0 restores the default, 2^22 probes, each a short hardware-timed suspend: far beyond
  * any legitimate copy latency and well under a second.  probes = 0 makes every wait of the
  * kernel's main loop give up at once; it exists to exercise the timeout path.  A wait that gives
@@ -211,13 +212,17 @@ LBM_API int lbm_set_wait_limit(lbm_lattice* h, int probes);
  * threads cover 2 bx columns; with walls a second launch steps the two wall rows); needs even nx and
  * a copy under 4 GiB.  STAGED: whole rows
  * staged in shared memory by bulk copies; needs nx to be a multiple of 16 bytes / stored element
- * size (2 columns FP64, 4 FP32, 8 16-bit). */
+ * size (2 columns FP64, 4 FP32, 8 16-bit).  PAIR_STAGED: the PAIR arithmetic with every row it
+ * pulls from staged in shared memory by bulk copies (128 x 1 threads, 256 columns per CTA; depth 1
+ * or 2 rows of prefetch); 16-bit storage on periodic lattices with nx a multiple of 8 and a copy
+ * under 4 GiB; same results as PAIR. */
 typedef enum {
   LBM_KERNEL_AUTO = 0,
   LBM_KERNEL_GENERIC = 1,
   LBM_KERNEL_STAGED = 2,
   LBM_KERNEL_GENERIC_WIDE = 3,
-  LBM_KERNEL_PAIR = 4
+  LBM_KERNEL_PAIR = 4,
+  LBM_KERNEL_PAIR_STAGED = 5
 } lbm_kernel;
 
 /* Override the kernel and its tile: bx x by threads per CTA (0, 0 = default for the variant),
@@ -232,7 +237,8 @@ typedef enum {
  * serve. */
 LBM_API int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int rows);
 
-/* The kernel and tile lbm_step uses now (variant is GENERIC, GENERIC_WIDE, PAIR or STAGED); NULL
+/* The kernel and tile lbm_step uses now (variant is GENERIC, GENERIC_WIDE, PAIR, STAGED or
+ * PAIR_STAGED); NULL
  * pointers skipped. */
 LBM_API int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows);
 

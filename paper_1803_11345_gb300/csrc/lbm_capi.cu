@@ -411,7 +411,7 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
     return LBM_OK;
   }
   if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_STAGED && variant != LBM_KERNEL_GENERIC_WIDE &&
-       variant != LBM_KERNEL_PAIR) ||
+       variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_PAIR_STAGED) ||
       rows < 0 || bx < 0 || by < 0 || depth < 0) {
     set_err(h->err, "lbm_set_kernel: invalid arguments");
     return LBM_ERR_PARAM;
@@ -423,18 +423,23 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   t.depth = depth ? depth : 1;
   t.rows = 0;
   t.wide = variant == LBM_KERNEL_GENERIC_WIDE;
-  t.pair = variant == LBM_KERNEL_PAIR;
+  t.pair = variant == LBM_KERNEL_PAIR || variant == LBM_KERNEL_PAIR_STAGED;
   if (t.pair) {
     t.bx = bx ? bx : 128;
     t.by = by ? by : 1;
   }
-  // The staged kernel stores from shared memory without the node index the rounding stream needs.
-  const bool ok = t.staged ? staged_supported(h->p.prec, h->geo, t) && h->phys.rounding == LBM_ROUND_NEAREST
-                  : t.pair ? pair_supported(h->p.prec, h->geo, t.bx, t.by)
-                           : tile_supported(h->p.prec, t.bx, t.by);
+  const bool pair_staged = variant == LBM_KERNEL_PAIR_STAGED;
+  if (pair_staged) t.staged = 1;
+  // The one-node staged kernel stores from shared memory without the node index the rounding
+  // stream needs; the staged paired kernel stores from registers and rounds either way.
+  const bool ok = pair_staged ? t.bx == 128 && t.by == 1 && pair_tma_supported(h->p.prec, h->geo, t.depth)
+                  : t.staged  ? staged_supported(h->p.prec, h->geo, t) && h->phys.rounding == LBM_ROUND_NEAREST
+                  : t.pair    ? pair_supported(h->p.prec, h->geo, t.bx, t.by)
+                              : tile_supported(h->p.prec, t.bx, t.by);
   if (!ok) {
     set_err(h->err, "lbm_set_kernel: no %s kernel for tile %dx%d depth %d on this lattice (nx = %d)",
-            t.staged ? "staged" : (t.pair ? "paired 16-bit" : "generic"), t.bx, t.by, t.depth, h->geo.nx);
+            pair_staged ? "staged paired 16-bit" : t.staged ? "staged" : (t.pair ? "paired 16-bit" : "generic"),
+            t.bx, t.by, t.depth, h->geo.nx);
     return LBM_ERR_PARAM;
   }
   if (rows > 0) {
@@ -442,9 +447,10 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
   } else {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int per_sm = t.staged ? staged_blocks_per_sm(h->p.prec, t)
-                       : t.pair ? pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0)
-                                : generic_blocks_per_sm(h->p.prec, t);
+    const int per_sm = pair_staged ? pair_tma_blocks_per_sm(h->p.prec, t.depth)
+                       : t.staged  ? staged_blocks_per_sm(h->p.prec, t)
+                       : t.pair    ? pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0)
+                                   : generic_blocks_per_sm(h->p.prec, t);
     t.rows = default_rows(h->geo, t, (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1));
   }
   h->tile = t;
@@ -454,7 +460,8 @@ int lbm_set_kernel(lbm_lattice* h, int variant, int bx, int by, int depth, int r
 int lbm_get_kernel(const lbm_lattice* h, int* variant, int* bx, int* by, int* depth, int* rows) {
   if (!h) return LBM_ERR_PARAM;
   if (variant)
-    *variant = h->tile.staged ? LBM_KERNEL_STAGED
+    *variant = h->tile.staged && h->tile.pair ? LBM_KERNEL_PAIR_STAGED
+               : h->tile.staged ? LBM_KERNEL_STAGED
                : h->tile.pair ? LBM_KERNEL_PAIR
                : (h->tile.wide || !offsets_fit_32(h->p.prec, h->geo.plane)) ? LBM_KERNEL_GENERIC_WIDE
                                                                             : LBM_KERNEL_GENERIC;
@@ -496,6 +503,13 @@ int lbm_autotune(lbm_lattice* h, int trial_steps, double* best_ms) {
     StepTile t{pt[0], pt[1], 0, 0, 1};
     t.pair = 1;
     t.rows = default_rows(h->geo, t, sms * pair_blocks_per_sm(h->p.prec, t, h->geo.walls != 0));
+    cands.push_back(t);
+  }
+  for (int d : {1, 2}) {
+    if (!pair_tma_supported(h->p.prec, h->geo, d)) continue;
+    StepTile t{128, 1, 0, 1, d};
+    t.pair = 1;
+    t.rows = default_rows(h->geo, t, sms * pair_tma_blocks_per_sm(h->p.prec, d));
     cands.push_back(t);
   }
   cudaEvent_t e0, e1;

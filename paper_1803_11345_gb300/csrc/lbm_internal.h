@@ -55,6 +55,7 @@ struct StepTile {
   int staged, depth;
   int wide = 0;  // generic kernel with 64-bit plane offsets even when the buffer is under 4 GiB
   int pair = 0;  // 16-bit storage, two nodes per thread (lbm_pair.cu); columns per CTA = 2 bx
+                 // (with staged = 1: the bulk-copy staged paired kernel, lbm_pair_tma.cu)
 };
 
 // Batched stepping: one member lattice (two population copies) and one unit of work (a tile of
@@ -103,6 +104,12 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 // The paired 16-bit step (lbm_pair.cu): whether tile bx x by can serve the lattice (16-bit
 // storage, nx even, buffer under 4 GiB), resident CTAs per SM, and the launch.
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by);
+// The paired 16-bit kernel with its rows staged by the bulk-copy engine (lbm_pair_tma.cu): 128
+// pairs per CTA, ring depth 1 or 2; periodic lattices with nx a multiple of 8.
+bool pair_tma_supported(int prec, const HostGeometry& g, int depth);
+int pair_tma_blocks_per_sm(int prec, int depth);
+cudaError_t launch_step_pair_tma(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
+                                 const char* src, char* dst, int* flag, cudaStream_t s);
 int pair_blocks_per_sm(int prec, const StepTile& t, bool walls);
 cudaError_t launch_step_pair(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t, const char* src,
                              char* dst, int* flag, cudaStream_t s);

@@ -351,6 +351,7 @@ cudaError_t launch_init(int prec, const HostGeometry& g, const HostPhys& p, cons
 
 cudaError_t launch_step(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,
                         const char* src, char* dst, int* flag, cudaStream_t s) {
+  if (t.staged && t.pair) return launch_step_pair_tma(prec, g, p, t, src, dst, flag, s);
   if (t.staged) return launch_step_staged(prec, g, p, t, src, dst, flag, s);
   if (t.pair) return launch_step_pair(prec, g, p, t, src, dst, flag, s);
   switch (prec) {

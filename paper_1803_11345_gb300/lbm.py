@@ -25,6 +25,7 @@ LBM_COLLIDE_CM, LBM_COLLIDE_BGK = 0, 1
 LBM_FORCE_UNIFORM, LBM_FORCE_PHASE_L = 0, 1
 LBM_ROUND_NEAREST, LBM_ROUND_STOCHASTIC = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_STAGED, LBM_KERNEL_GENERIC_WIDE, LBM_KERNEL_PAIR = 0, 1, 2, 3, 4
+LBM_KERNEL_PAIR_STAGED = 5
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")

@@ -419,6 +419,73 @@ def test_paired_kernel_choice_and_limits(lbm):
 
 
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_staged_paired_kernel_equals_paired_kernel(lbm, prec, rounding):
+    """The staged paired kernel (rows copied into shared memory by the bulk-copy engine) runs the
+    paired kernel's arithmetic on the same words, so its state equals the paired kernel's bit for
+    bit: on lattices whose strips wrap at both edges (nx = 8: one strip of 8 columns), end ragged
+    (nx = 328: strips of 256 and 72 columns) or have interior strips (nx = 1024), with one-row and
+    uneven CTA heights, both ring depths, and either rounding."""
+    kw = dict(prec=lbm.PRECISIONS[prec], tau_l=0.8, tau_g=0.53, visc=lbm.LBM_TAU_LINEAR)
+    if rounding == "stochastic":
+        kw.update(rounding=lbm.LBM_ROUND_STOCHASTIC, seed=11)
+    for nx, ny, steps in ((8, 16, 60), (328, 90, 120), (1024, 40, 60)):
+        phi0 = W.spinodal(nx, ny, seed=nx)
+        ref = lbm.Lattice(phi0, **kw)
+        ref.set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)
+        ref.step(steps)
+        fr, gr = ref.populations()
+        ref.close()
+        for depth in (1, 2):
+            for rows in (0, 1, 7):
+                lat = lbm.Lattice(phi0, **kw)
+                lat.set_kernel(lbm.LBM_KERNEL_PAIR_STAGED, 128, 1, depth, rows)
+                assert lat.kernel[0] == lbm.LBM_KERNEL_PAIR_STAGED
+                lat.step(steps)
+                assert lbm.lbm_check(lat.h) == lbm.LBM_OK
+                f, g = lat.populations()
+                assert np.array_equal(f, fr) and np.array_equal(g, gr), (nx, ny, depth, rows, abs_err(f, fr))
+                lat.close()
+
+
+def test_staged_paired_kernel_limits_and_timeout(lbm):
+    """PAIR_STAGED serves periodic 16-bit lattices with nx a multiple of 8 (depth 1 or 2) and is
+    refused elsewhere; with its wait limit at 0 every main-loop wait gives up, the next check
+    reports LBM_ERR_TIMEOUT, and after the limit is restored and a checkpoint put back the handle
+    steps exactly like a fresh lattice from that checkpoint."""
+    phi0 = W.droplet(256, 64, 12, gamma=0.04, a=0.04)
+    for bad_phi, kw in ((W.spinodal(68, 16, seed=1), dict(prec=lbm.LBM_FP16S)),
+                        (phi0, dict(prec=lbm.LBM_FP32)),
+                        (phi0, dict(prec=lbm.LBM_FP16S, bc=lbm.LBM_WALLS_Y))):
+        lat = lbm.Lattice(bad_phi, **kw)
+        with pytest.raises(lbm.LbmError):
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR_STAGED, 128, 1)
+        lat.close()
+    lat = lbm.Lattice(phi0, prec=lbm.LBM_FP16S)
+    for bad in (dict(bx=64, by=2), dict(depth=3)):
+        with pytest.raises(lbm.LbmError):
+            lat.set_kernel(lbm.LBM_KERNEL_PAIR_STAGED, bad.get("bx", 128), bad.get("by", 1), bad.get("depth", 1))
+    lat.set_kernel(lbm.LBM_KERNEL_PAIR_STAGED, 128, 1, 1)
+    lat.step(5)
+    f, g = lat.populations()
+    lat.set_wait_limit(0)
+    lat.step(2)
+    assert lbm.lbm_check(lat.h) == lbm.LBM_ERR_TIMEOUT
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK
+    lat.set_wait_limit(-1)
+    lat.set_populations(f, g)
+    ref = lbm.Lattice(phi0, prec=lbm.LBM_FP16S)
+    ref.set_kernel(lbm.LBM_KERNEL_PAIR_STAGED, 128, 1, 1)
+    ref.set_populations(f, g)
+    lat.step(20)
+    ref.step(20)
+    assert lbm.lbm_check(lat.h) == lbm.LBM_OK
+    fa, ga = lat.populations()
+    fb, gb = ref.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
 def test_paired_16bit_kernel_with_walls(lbm, orc, prec):
     """Walled lattices: the paired kernel collides the interior rows (forming phi on the wall rows
     with the bounce-back pull) and a second launch steps the two wall rows with the one-node tile

@@ -287,6 +287,14 @@ def run_reference(args):
     return 0
 
 
+# --kernel choices: (variant getter, bx, by, depth); "auto" keeps the library's default.
+KERNELS = {
+    "generic": (lambda m: m.LBM_KERNEL_GENERIC, 256, 1, 1),
+    "pair": (lambda m: m.LBM_KERNEL_PAIR, 128, 1, 1),
+    "pair_staged": (lambda m: m.LBM_KERNEL_PAIR_STAGED, 128, 1, 1),
+}
+
+
 def config_dict(args):
     return {"workload": f"spinodal decomposition {args.n}x{args.n} periodic, viscosity ratio 1:10 "
                         f"(tau linear in phi), {args.prec} storage",
@@ -294,7 +302,7 @@ def config_dict(args):
             "nu_l": PHYS["nu_l"], "nu_g": PHYS["nu_g"], "a": PHYS["a"], "gamma": PHYS["gamma"],
             "M": PHYS["M"], "collision": "central moments (f) + BGK (g)",
             "l2": "inputs larger than L2 (state >= 1 GB per buffer at 4096^2): no flush",
-            "parallelism": f"replicas x{args.gpus}"}
+            "parallelism": f"replicas x{args.gpus}", "kernel": args.kernel}
 
 
 # ------------------------------------------------------------------------------------------
@@ -357,6 +365,8 @@ def run_gpu(args):
     params = dict(prec=lbm.PRECISIONS[args.prec], visc=lbm.LBM_TAU_LINEAR, **workload_params())
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(phi0, stream=stream, **params)
+    if args.kernel != "auto":
+        lat.set_kernel(KERNELS[args.kernel][0](lbm), *KERNELS[args.kernel][1:])
 
     def barrier():
         if ws > 1:
@@ -401,12 +411,12 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     bpn = BYTES_PER_NODE[args.prec]
     achieved = bpn * nodes / (ms / args.steps * 1e-3) / 1e9
-    traffic = ncu_traffic(args.prec, n)
+    traffic = ncu_traffic(args.prec, n) if args.kernel == "auto" else None
 
     # Parity spot check on this run (cheap): sum phi is conserved by the scheme.
     sphi, srho, _, _ = lat.conservation()
-    kernel_name = {lbm.LBM_KERNEL_PAIR: "k_step_pair", lbm.LBM_KERNEL_STAGED: "k_step_staged"}.get(
-        lat.kernel[0], "k_step")
+    kernel_name = {lbm.LBM_KERNEL_PAIR: "k_step_pair", lbm.LBM_KERNEL_STAGED: "k_step_staged",
+                   lbm.LBM_KERNEL_PAIR_STAGED: "k_step_pair_tma"}.get(lat.kernel[0], "k_step")
     lat.close()
     del lat
     torch.cuda.synchronize()
@@ -686,6 +696,8 @@ def main(argv=None):
     ap.add_argument("--pad-ms", type=float, default=400.0,
                     help="untimed stepping before and after the timed region, for the clock samples (0: none)")
     ap.add_argument("--workload", choices=["spinodal", "batch", "surrogate"], default="spinodal")
+    ap.add_argument("--kernel", choices=["auto", *KERNELS], default="auto",
+                    help="step kernel of the spinodal workload (auto: the library's default)")
     ap.add_argument("--sur-n", type=int, default=256)
     ap.add_argument("--sur-k", type=int, default=50, help="solver steps per surrogate window")
     ap.add_argument("--sur-windows", type=int, default=30, help="windows per trajectory (x K solver steps)")

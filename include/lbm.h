@@ -296,8 +296,20 @@ LBM_API int lbm_batch_check(lbm_batch* b, int* nonfinite);
 LBM_API int lbm_batch_set_tile(lbm_batch* b, int bx, int by, int target_nodes);
 LBM_API int lbm_batch_get_tile(const lbm_batch* b, int* bx, int* by, int* target_nodes, int* items, int* grid);
 
-/* Time every tile x item size (trial_steps launches each, state unchanged as in lbm_autotune),
- * keep the fastest, cache it for batches of the same member sizes; *best_ms = its step time. */
+/* Kernel of the batch: LBM_KERNEL_GENERIC (the one-node tile, 64 x 4 until lbm_batch_set_tile or
+ * lbm_batch_autotune picks another) or LBM_KERNEL_PAIR (the paired 16-bit tile of lbm_set_kernel:
+ * 128 x 1 threads, 256 columns per work item; every member periodic 16-bit with even nx), with
+ * about target_nodes nodes per work item (>= 2048).  A member of a PAIR batch steps exactly as a
+ * single lattice with LBM_KERNEL_PAIR (same words, same arithmetic, same stochastic-rounding keys).
+ * A new batch starts with PAIR where it can serve it, else with the one-node 64 x 4 tile (or with
+ * the autotuner's cached winner for batches of the same member sizes).
+ * Errors: LBM_ERR_PARAM (other variants, members the variant cannot serve, target below 2048). */
+LBM_API int lbm_batch_set_kernel(lbm_batch* b, int variant, int target_nodes);
+LBM_API int lbm_batch_get_kernel(const lbm_batch* b, int* variant);
+
+/* Time every tile x item size (trial_steps launches each, state unchanged as in lbm_autotune; the
+ * paired tile too where it can serve the batch), keep the fastest, cache it for batches of the
+ * same member sizes; *best_ms = its step time. */
 LBM_API int lbm_batch_autotune(lbm_batch* b, int trial_steps, double* best_ms);
 
 /* Completed steps; last error (b = NULL: this thread's last lbm_batch_init failure); release. */

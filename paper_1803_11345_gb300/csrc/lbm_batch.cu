@@ -36,8 +36,11 @@ const int kTiles[][2] = {{32, 4}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}
 const int kTargets[] = {2048, 4096, 8192, 16384};
 constexpr int kMinTarget = 2048;
 
-int item_rows(const HostGeometry& g, int bx, int by, int target) {
-  const int w = std::min(bx, g.nx);
+// Columns a CTA of the tile covers: bx, or 2 bx for the paired 16-bit tile (two nodes per thread).
+int tile_cols(const StepTile& t) { return t.pair ? 2 * t.bx : t.bx; }
+
+int item_rows(const HostGeometry& g, int cols, int by, int target) {
+  const int w = std::min(cols, g.nx);
   int rows = std::max(by, target / w);
   rows = (rows + by - 1) / by * by;
   return std::min(rows, (g.ny + by - 1) / by * by);
@@ -54,7 +57,12 @@ size_t max_items(const std::vector<HostGeometry>& geo) {
     }
     worst = std::max(worst, n);
   }
-  return worst;
+  size_t n = 0;  // the paired tile: 256 columns
+  for (auto& g : geo) {
+    const int rows = item_rows(g, 256, 1, kMinTarget);
+    n += (size_t)((g.nx + 255) / 256) * ((g.ny + rows - 1) / rows);
+  }
+  return std::max(worst, n);
 }
 
 struct Layout {
@@ -140,16 +148,17 @@ std::string signature(const lbm_batch* b) {
 // Rebuild and upload the work list for a tile and item size; invalidates the graph.
 cudaError_t build_items(lbm_batch* b, const StepTile& t, int target) {
   std::vector<BatchItem> items;
+  const int cols = tile_cols(t);
   for (int m = 0; m < b->count; ++m) {
     const HostGeometry& g = b->geo[m];
-    const int rows = item_rows(g, t.bx, t.by, target);
+    const int rows = item_rows(g, cols, t.by, target);
     for (int y0 = 0; y0 < g.ny; y0 += rows)
-      for (int x0 = 0; x0 < g.nx; x0 += t.bx) items.push_back(BatchItem{m, x0, y0, rows});
+      for (int x0 = 0; x0 < g.nx; x0 += cols) items.push_back(BatchItem{m, x0, y0, rows});
   }
   if (items.size() > b->L.nitems_max) return cudaErrorInvalidValue;
   auto nodes = [&](const BatchItem& w) {
     const HostGeometry& g = b->geo[w.member];
-    return (long long)std::min(t.bx, g.nx - w.x0) * std::min(w.rows, g.ny - w.y0);
+    return (long long)std::min(cols, g.nx - w.x0) * std::min(w.rows, g.ny - w.y0);
   };
   std::stable_sort(items.begin(), items.end(),
                    [&](const BatchItem& a, const BatchItem& c) { return nodes(a) > nodes(c); });
@@ -173,6 +182,15 @@ bool members_fit_32(const lbm_batch* b) {
   for (const HostGeometry& g : b->geo)
     if (pop_buffer_bytes(b->prec, g.plane) >= (size_t(1) << 32)) return false;
   return true;
+}
+
+// The paired 16-bit tile serves batches whose members are all periodic 16-bit lattices with even
+// nx and buffers under 4 GiB.
+bool pair_ok(const lbm_batch* b) {
+  if (b->prec != 2 && b->prec != 3) return false;
+  for (const HostGeometry& g : b->geo)
+    if (g.walls || g.nx % 2) return false;
+  return members_fit_32(b);
 }
 
 cudaError_t launch_one(lbm_batch* b, int parity) {
@@ -293,7 +311,14 @@ int lbm_batch_init(const lbm_params* params, int count, const double* const* phi
   if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + b->L.flags_off, 0, sizeof(int) * count, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->arena + b->L.tcount_off, 0, 2 * sizeof(long long), b->stream);
   if (e == cudaSuccess) {
+    // Default: the paired 16-bit tile where it can serve the batch (periodic 16-bit sweep of 132
+    // members 64^2..512^2 on GB300: 40.2k MLUPS against 34.8k for the best one-node tile), else
+    // the one-node 64 x 4 tile; a cached autotune winner for the same member sizes overrides both.
     StepTile t{64, 4, 0, 0, 1};
+    if (pair_ok(b)) {
+      t = StepTile{128, 1, 0, 0, 1};
+      t.pair = 1;
+    }
     int target = 4096;
     {
       std::lock_guard<std::mutex> lock(g_cache_mutex);
@@ -429,6 +454,31 @@ int lbm_batch_set_tile(lbm_batch* b, int bx, int by, int target_nodes) {
   return LBM_OK;
 }
 
+int lbm_batch_set_kernel(lbm_batch* b, int variant, int target_nodes) {
+  if (!b) return LBM_ERR_PARAM;
+  if ((variant != LBM_KERNEL_GENERIC && variant != LBM_KERNEL_PAIR) || target_nodes < kMinTarget)
+    return fail(b, LBM_ERR_PARAM, "lbm_batch_set_kernel: variant %d / %d nodes per item not available", variant,
+                target_nodes);
+  StepTile t{64, 4, 0, 0, 1};
+  if (variant == LBM_KERNEL_PAIR) {
+    if (!pair_ok(b))
+      return fail(b, LBM_ERR_PARAM,
+                  "lbm_batch_set_kernel: the paired kernel needs 16-bit members, all periodic with even nx");
+    t = StepTile{128, 1, 0, 0, 1};
+    t.pair = 1;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = build_items(b, t, target_nodes);
+  if (e != cudaSuccess) return fail(b, LBM_ERR_CUDA, "lbm_batch_set_kernel: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_get_kernel(const lbm_batch* b, int* variant) {
+  if (!b) return LBM_ERR_PARAM;
+  if (variant) *variant = b->tile.pair ? LBM_KERNEL_PAIR : LBM_KERNEL_GENERIC;
+  return LBM_OK;
+}
+
 int lbm_batch_get_tile(const lbm_batch* b, int* bx, int* by, int* target_nodes, int* items, int* grid) {
   if (!b) return LBM_ERR_PARAM;
   if (bx) *bx = b->tile.bx;
@@ -449,9 +499,15 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, double* best_ms) {
   StepTile best_t = b->tile;
   int best_target = b->target;
   cudaError_t e = cudaSuccess;
-  for (auto& tt : kTiles) {
+  std::vector<StepTile> cands;
+  for (auto& tt : kTiles) cands.push_back(StepTile{tt[0], tt[1], 0, 0, 1});
+  if (pair_ok(b)) {
+    StepTile t{128, 1, 0, 0, 1};
+    t.pair = 1;
+    cands.push_back(t);
+  }
+  for (const StepTile& t : cands) {
     for (int target : kTargets) {
-      const StepTile t{tt[0], tt[1], 0, 0, 1};
       e = build_items(b, t, target);
       if (e != cudaSuccess) break;
       // Same parity every launch: each rewrites the spare copies from the unchanged state.

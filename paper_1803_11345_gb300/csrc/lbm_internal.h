@@ -106,6 +106,12 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by);
 // The paired 16-bit kernel with its rows staged by the bulk-copy engine (lbm_pair_tma.cu): 128
 // pairs per CTA, ring depth 1 or 2; periodic lattices with nx a multiple of 8.
+// The batched paired kernel (lbm_pair.cu): 128 x 1 threads, 256-column items of periodic 16-bit
+// members, every member's buffer under 4 GiB; phys holds Phys<float> per member.
+cudaError_t launch_step_pair_batch(int prec, const BatchItem* items, int nitems, const BatchMember* members,
+                                  const void* phys, int parity, int* flags, long long* tcount, int grid,
+                                  cudaStream_t s);
+int pair_batch_blocks_per_sm(int prec);
 bool pair_tma_supported(int prec, const HostGeometry& g, int depth);
 int pair_tma_blocks_per_sm(int prec, int depth);
 cudaError_t launch_step_pair_tma(int prec, const HostGeometry& g, const HostPhys& p, const StepTile& t,

@@ -419,6 +419,7 @@ int batch_occ(int bx, int by) {
 cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* items, int nitems,
                               const BatchMember* members, const void* phys, int parity, int* flags,
                               long long* tcount, int grid, bool off32, cudaStream_t s) {
+  if (t.pair) return launch_step_pair_batch(prec, items, nitems, members, phys, parity, flags, tcount, grid, s);
   switch (prec) {
     case 0: return batch_prec<0>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
     case 1: return batch_prec<1>(t, items, nitems, members, phys, parity, flags, tcount, grid, off32, s);
@@ -429,6 +430,7 @@ cudaError_t launch_step_batch(int prec, const StepTile& t, const BatchItem* item
 }
 
 int batch_blocks_per_sm(int prec, const StepTile& t) {
+  if (t.pair) return pair_batch_blocks_per_sm(prec);
   int nb = 0;
   switch (prec) {
     case 0: nb = batch_occ<0>(t.bx, t.by); break;

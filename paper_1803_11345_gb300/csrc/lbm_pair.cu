@@ -273,6 +273,63 @@ k_step_pair(const char* __restrict__ src, char* __restrict__ dst, const Geometry
                                Plane32{(unsigned)geo.plane});
 }
 
+// Batched paired step: a persistent grid deals out a work list of 256-column tiles drawn from
+// many periodic 16-bit lattices (lbm_batch.cu), each stepped by the tile code above with its
+// member's geometry and physics, so a member's state is the one k_step_pair<PREC, 128, 1> gives
+// the single lattice.  The step counter and the stochastic-rounding key follow k_step_batch.
+__device__ __forceinline__ Phys<F2> widen(const Phys<float>& p) {
+  Phys<F2> q;
+  q.omega_l = F2(p.omega_l);
+  q.omega_g = F2(p.omega_g);
+  q.tau_l = F2(p.tau_l);
+  q.tau_g = F2(p.tau_g);
+  q.omega3 = F2(p.omega3);
+  q.omega_phi = F2(p.omega_phi);
+  q.gamma = F2(p.gamma);
+  q.a = F2(p.a);
+  q.Gamma = F2(p.Gamma);
+  q.u_top = F2(p.u_top);
+  q.u_bottom = F2(p.u_bottom);
+  q.wet_bottom = F2(p.wet_bottom);
+  q.wet_top = F2(p.wet_top);
+  q.force_x = F2(p.force_x);
+  q.force_y = F2(p.force_y);
+  q.visc = p.visc;
+  q.k8_printed = p.k8_printed;
+  q.bgk = p.bgk;
+  q.force_mode = p.force_mode;
+  q.forced = p.forced;
+  q.sr_key = p.sr_key;
+  q.rounding = p.rounding;
+  q.seed = p.seed;
+  return q;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128, 3)
+k_step_pair_batch(const BatchItem* __restrict__ items, const int nitems, const BatchMember* __restrict__ members,
+                  const Phys<float>* __restrict__ phys, const int parity, int* __restrict__ flags,
+                  long long* __restrict__ tcount) {
+  __shared__ __align__(16) float sphi[4][2 * 128 + 2];
+  const long long t = tcount[parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0) tcount[1 - parity] = t + 1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem w = items[it];
+    const BatchMember m = members[w.member];
+    Phys<F2> ph = widen(phys[w.member]);
+    if (ph.rounding) ph.sr_key = sr_step_key(ph.seed, t);  // the key a single lattice uses at step t
+    Geometry geo;
+    geo.nx = m.nx;
+    geo.ny = m.ny;
+    geo.pitch = m.pitch;
+    geo.plane = m.plane;
+    geo.walls = m.walls;
+    step_pair_tile<PREC, 128, 1, false>(parity ? m.buf1 : m.buf0, parity ? m.buf0 : m.buf1, geo, ph, w.x0, w.y0,
+                                        w.rows, flags + w.member, sphi, Plane32{(unsigned)geo.plane});
+    __syncthreads();  // the phi ring is reused by the next item
+  }
+}
+
 // Compiled tiles: 128-thread CTAs (3 per SM); 256-thread shapes spill at the register cap of
 // 2 CTAs per SM and were 1.5x slower.
 #define LBM_PAIR_TILES(X) X(64, 2) X(128, 1)
@@ -318,6 +375,23 @@ int pair_occ(int bx, int by, bool walls) {
 }
 
 }  // namespace
+
+cudaError_t launch_step_pair_batch(int prec, const BatchItem* items, int nitems, const BatchMember* members,
+                                  const void* phys, int parity, int* flags, long long* tcount, int grid,
+                                  cudaStream_t s) {
+  const Phys<float>* ph = static_cast<const Phys<float>*>(phys);
+  if (prec == 2) k_step_pair_batch<2><<<grid, 128, 0, s>>>(items, nitems, members, ph, parity, flags, tcount);
+  else if (prec == 3) k_step_pair_batch<3><<<grid, 128, 0, s>>>(items, nitems, members, ph, parity, flags, tcount);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+int pair_batch_blocks_per_sm(int prec) {
+  int nb = 0;
+  if (prec == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair_batch<2>, 128, 0);
+  if (prec == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_pair_batch<3>, 128, 0);
+  return nb > 0 ? nb : 1;
+}
 
 bool pair_supported(int prec, const HostGeometry& g, int bx, int by) {
   if ((prec != 2 && prec != 3) || g.nx % 2 || !offsets_fit_32(prec, g.plane)) return false;

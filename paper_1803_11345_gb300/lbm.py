@@ -110,6 +110,10 @@ def _load():
     lib.lbm_batch_set_tile.restype = i
     lib.lbm_batch_get_tile.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 5
     lib.lbm_batch_get_tile.restype = i
+    lib.lbm_batch_set_kernel.argtypes = [vp, i, i]
+    lib.lbm_batch_set_kernel.restype = i
+    lib.lbm_batch_get_kernel.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_batch_get_kernel.restype = i
     lib.lbm_batch_autotune.argtypes = [vp, i, dp]
     lib.lbm_batch_autotune.restype = i
     lib.lbm_batch_time.argtypes = [vp]
@@ -322,6 +326,16 @@ def lbm_batch_get_tile(b: int):
     return tuple(x.value for x in v)
 
 
+def lbm_batch_set_kernel(b: int, variant: int, target_nodes: int = 4096) -> None:
+    _bcheck(_lib.lbm_batch_set_kernel(b, variant, target_nodes), b)
+
+
+def lbm_batch_get_kernel(b: int) -> int:
+    v = ctypes.c_int()
+    _bcheck(_lib.lbm_batch_get_kernel(b, ctypes.byref(v)), b)
+    return v.value
+
+
 def lbm_batch_autotune(b: int, trial_steps: int = 5) -> float:
     ms = ctypes.c_double()
     _bcheck(_lib.lbm_batch_autotune(b, trial_steps, ctypes.byref(ms)), b)
@@ -481,6 +495,13 @@ class Batch:
     @property
     def tile(self):
         return lbm_batch_get_tile(self.b)
+
+    def set_kernel(self, variant: int, target_nodes: int = 4096):
+        lbm_batch_set_kernel(self.b, variant, target_nodes)
+
+    @property
+    def kernel(self) -> int:
+        return lbm_batch_get_kernel(self.b)
 
     def autotune(self, trial_steps: int = 5) -> float:
         return lbm_batch_autotune(self.b, trial_steps)

@@ -103,6 +103,64 @@ def test_batch_stochastic_rounding_follows_single_lattices(lbm, prec):
     assert bat.check()[0] == lbm.LBM_OK
 
 
+def _pair_members():
+    """Periodic members with even nx: a full 256-column strip, ragged strips (326 = 256 + 70,
+    70 < 256), a narrow lattice (8 columns), different viscosity ratios and surface tensions."""
+    return [
+        (W.spinodal(326, 90, seed=4), dict(tau_l=0.8, tau_g=0.53, visc=1)),
+        (W.droplet(256, 64, 16, gamma=0.02, a=0.04), dict(tau_l=1.0, tau_g=0.6, gamma=0.02, a=0.04)),
+        (W.spinodal(70, 33, seed=9), dict(tau_l=0.7, tau_g=0.55, omega3=1.3)),
+        (W.spinodal(8, 16, seed=2), dict()),
+        (W.droplet(512, 128, 30, gamma=0.04, a=0.04), dict(tau_l=0.9, tau_g=0.503)),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_paired_batch_members_equal_single_lattices(lbm, prec, rounding):
+    """The paired 16-bit tile in the batch work list: each work item is stepped by the paired
+    kernel's tile code with its member's geometry and physics, and stochastic-rounding keys come
+    from the batch's device step counter by the function single lattices use, so every member's
+    state equals, bit for bit, a single lattice stepped with LBM_KERNEL_PAIR, through graph
+    replays and odd step counts, whatever the item size."""
+    mem = _pair_members()
+    if rounding == "stochastic":
+        mem = [(p0, dict(kw, rounding=lbm.LBM_ROUND_STOCHASTIC, seed=5 + k)) for k, (p0, kw) in enumerate(mem)]
+    singles = [lbm.Lattice(phi0, prec=prec, **kw) for phi0, kw in mem]
+    for s in singles:
+        s.set_kernel(lbm.LBM_KERNEL_PAIR, 128, 1)
+    for target in (2048, 16384):
+        bat = lbm.Batch(mem, prec=prec)
+        bat.set_kernel(lbm.LBM_KERNEL_PAIR, target)
+        assert bat.kernel == lbm.LBM_KERNEL_PAIR and bat.tile[:2] == (128, 1)
+        for n in (5, 37, 16, 3):
+            bat.step(n)
+        assert bat.time == 61 and bat.check()[0] == lbm.LBM_OK
+        if target == 2048:
+            for n in (5, 37, 16, 3):
+                for s in singles:
+                    s.step(n)
+        for m, s in enumerate(singles):
+            fb, gb = bat.populations(m)
+            fs, gs = s.populations()
+            assert np.array_equal(fb, fs) and np.array_equal(gb, gs), (target, m, abs_err(fb, fs))
+        bat.close()
+
+
+def test_paired_batch_refused_where_it_cannot_serve(lbm):
+    """LBM_KERNEL_PAIR needs every member periodic with even nx and 16-bit storage; otherwise
+    lbm_batch_set_kernel refuses and the batch keeps its tile."""
+    for mem, prec in (([(W.spinodal(64, 32, seed=1), dict()), (W.spinodal(65, 32, seed=2), dict())], "fp16s"),
+                      ([(W.spinodal(64, 32, seed=1), dict()), (W.spinodal(64, 32, seed=2), dict(bc=1))], "fp16s"),
+                      ([(W.spinodal(64, 32, seed=1), dict())], "fp32")):
+        bat = lbm.Batch(mem, prec=prec)
+        before = bat.tile
+        with pytest.raises(lbm.LbmError):
+            bat.set_kernel(lbm.LBM_KERNEL_PAIR)
+        assert bat.kernel == lbm.LBM_KERNEL_GENERIC and bat.tile == before
+        del bat
+
+
 def test_batch_fp64_member_matches_oracle(lbm, orc):
     mem = _members()[:4]
     bat = lbm.Batch(mem, prec="fp64")

@@ -27,8 +27,9 @@
 //     sur_transpose_taps): [octet][tap][output channel][8 x BF16] (by TMA: one box per octet),
 //     shared by every accumulator.
 // A persistent CTA walks its tiles; every (tile, 16-channel chunk) is an item of a ring of S
-// shared-memory stages, filled by TMA or, in copy mode and when upsampling, by four producer
-// warps' 16-byte cp.async copies; one thread issues each item's MMAs into one of two
+// (2 to 6) shared-memory stages, filled by TMA (one lane per octet and staged row; with one N
+// tile the weights of all chunks stay resident, loaded once) or, in copy mode and when
+// upsampling, by four producer warps' 16-byte cp.async copies; one thread issues each item's MMAs into one of two
 // accumulator sets (the epilogue of a tile overlaps the next tile's MMAs) and commits them to
 // the stage's "empty" mbarrier.  Every mbarrier wait is bounded: a wait that gives up sets the
 // status word read by sur_check, lets the copies and MMAs it issued finish (again bounded), frees
@@ -146,6 +147,10 @@ struct ConvTC {
   uint32_t idesc;
   int relu, out_f32, up;
   int tma;              // 1: row mode without upsampling, staged by TMA
+  int wres;             // 1 (TMA mode, one N tile): all weights resident in shared memory, loaded once
+  uint32_t wres_off;    // byte offset of the resident weights (after the stages)
+  uint32_t w_bytes;     // bytes of the resident weights: nchunks x 18 blocks
+  uint32_t bar_off;     // byte offset of the barriers
 };
 
 constexpr int kRowSlots = 144;  // pixel slots per staged row in row mode (16 bytes each)
@@ -213,13 +218,15 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
              const __grid_constant__ CUtensorMap tm_rows, const __grid_constant__ CUtensorMap tm_w) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * c.stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + c.bar_off);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
-  volatile int* abort = reinterpret_cast<volatile int*>(done + 1);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1) + 1;
+  uint64_t* wbar = done + 1;  // the resident weights have landed
+  volatile int* abort = reinterpret_cast<volatile int*>(wbar + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1) + 1;
+  unsigned char* const wsm = smem + c.wres_off;
 
   if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(tslot), c.ncols);
@@ -227,7 +234,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
   }
   if (tid == 0) {
     for (int k = 0; k < S; ++k) {
-      mbar_init(&full[k], c.tma ? 1 : kProducers);
+      mbar_init(&full[k], c.tma ? 2 : kProducers);  // TMA mode: the copy warp and the halo warp
       mbar_init(&empty[k], 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -235,6 +242,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
       mbar_init(&tempty[k], 128);
     }
     mbar_init(done, 1);
+    mbar_init(wbar, 1);
     *abort = 0;
     mbar_fence_init();
   }
@@ -248,34 +256,75 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
   };
 
   if (c.tma && tid < kProducers) {
-    // ---- TMA producer: one thread; stage i % S is full once its bytes have landed.
-    if (tid == 0) {
+    // ---- TMA producer: warp 0.  Lane 0 arms a stage with its byte count; one lane per (octet,
+    // staged row) then issues that row's 128-pixel box and its two wrapped halo pixels, and (when
+    // the weights are not resident) lanes 30 and 31 the weight boxes.  Stage i % S is full once
+    // its bytes have landed.  Resident weights: every (chunk, octet) box once, on wbar.
+    if (warp == 0) {
+      if (c.wres) {
+        if (lane == 0) mbar_arrive_expect_tx(wbar, c.w_bytes);
+        __syncwarp();
+        for (int j = lane; j < 2 * c.nchunks; j += 32)
+          tma_load_3d(wsm + (uint32_t)j * 9 * c.b_block, &tm_w, (j >> 1) * 16 + (j & 1) * 8, 0, 0, wbar);
+      }
       int i = 0;
       bool ok = true;
+      const int nrow = c.RT + 2;
       for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x) {
         const TileCoord q = tile_coord(c, t);
         for (int ch = 0; ch < c.nchunks; ++ch, ++i) {
           const int st = i % S;
-          if (i >= S && !wait_role(&empty[st], (uint32_t)((i / S) - 1) & 1u, abort)) {
-            give_up();
+          if (i >= S && !__all_sync(0xffffffffu, wait_role(&empty[st], (uint32_t)((i / S) - 1) & 1u, abort))) {
+            if (lane == 0) give_up();
             ok = false;
             break;
           }
           unsigned char* A = smem + (uint32_t)st * c.stage_bytes;
-          unsigned char* Bm = A + c.a_stage;
-          mbar_arrive_expect_tx(&full[st], c.tx_bytes);
+          if (lane == 0) mbar_arrive_expect_tx(&full[st], c.tx_bytes);
+          __syncwarp();
           const int k0 = ch * 16;
-          const int xl = wrap(q.x0 - 1, c.W), xr = wrap(q.x0 + kTileM, c.W);
-          for (int kc = 0; kc < 2; ++kc)
-            for (int hr = 0; hr < c.RT + 2; ++hr) {
-              const int yy = wrap(q.y0 + hr - 1, c.H);
-              unsigned char* row = A + kc * c.a_block + hr * (kRowSlots * 16);
-              tma_load_4d(row + (kRowFirst + 1) * 16, &tm_rows, k0 + kc * 8, q.x0, yy, q.b, &full[st]);
-              const size_t base = ((size_t)q.b * c.H + yy) * c.W;
-              bulk_g2s(row + kRowFirst * 16, x + (base + xl) * c.K + k0 + kc * 8, 16, &full[st]);
-              bulk_g2s(row + (kRowFirst + 1 + kTileM) * 16, x + (base + xr) * c.K + k0 + kc * 8, 16, &full[st]);
-            }
-          for (int kc = 0; kc < 2; ++kc) tma_load_3d(Bm + kc * 9 * c.b_block, &tm_w, k0 + kc * 8, q.n0, 0, &full[st]);
+          if (lane < 2 * nrow) {
+            const int kc = lane / nrow, hr = lane - kc * nrow;
+            const int yy = wrap(q.y0 + hr - 1, c.H);
+            unsigned char* row = A + kc * c.a_block + hr * (kRowSlots * 16);
+            tma_load_4d(row + (kRowFirst + 1) * 16, &tm_rows, k0 + kc * 8, q.x0, yy, q.b, &full[st]);
+          }
+          if (!c.wres && lane >= 30) {
+            const int kc = lane - 30;
+            tma_load_3d(A + c.a_stage + kc * 9 * c.b_block, &tm_w, k0 + kc * 8, q.n0, 0, &full[st]);
+          }
+        }
+      }
+    }
+    if (warp == 1) {
+      // ---- halo warp: the wrapped pixel left and right of every staged row (one 16-byte load
+      // and store per lane: octet, row and side), fenced for the tensor core's reads; the stage
+      // is full once these and the copy warp's bytes are in.  Per-pixel bulk copies cost as much
+      // staging time as the rows' boxes.
+      int i = 0;
+      bool ok = true;
+      const int nrow = c.RT + 2;
+      for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x) {
+        const TileCoord q = tile_coord(c, t);
+        for (int ch = 0; ch < c.nchunks; ++ch, ++i) {
+          const int st = i % S;
+          if (i >= S && !__all_sync(0xffffffffu, wait_role(&empty[st], (uint32_t)((i / S) - 1) & 1u, abort))) {
+            if (lane == 0) give_up();
+            ok = false;
+            break;
+          }
+          if (lane < 4 * nrow) {
+            const int side = lane & 1, kc = (lane >> 1) / nrow, hr = (lane >> 1) - kc * nrow;
+            const int yy = wrap(q.y0 + hr - 1, c.H);
+            const int xx = side ? wrap(q.x0 + kTileM, c.W) : wrap(q.x0 - 1, c.W);
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(
+                x + (((size_t)q.b * c.H + yy) * c.W + xx) * c.K + ch * 16 + kc * 8));
+            unsigned char* row = smem + (uint32_t)st * c.stage_bytes + kc * c.a_block + hr * (kRowSlots * 16);
+            *reinterpret_cast<uint4*>(row + (side ? kRowFirst + 1 + kTileM : kRowFirst) * 16) = v;
+            fence_proxy_async();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[st]);
         }
       }
     }
@@ -344,6 +393,10 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
     if (lane == 0) {
       int i = 0, kt = 0;
       bool ok = true;
+      if (c.wres && !wait_role(wbar, 0, abort)) {
+        give_up();
+        ok = false;
+      }
       for (int t = blockIdx.x; t < c.ntiles && ok; t += gridDim.x, ++kt) {
         const uint32_t set = (uint32_t)(kt & 1) * c.set_cols;
         if (kt >= 2 && !wait_role(&tempty[kt & 1], (uint32_t)((kt >> 1) - 1) & 1u, abort)) {
@@ -361,7 +414,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
           }
           tc_fence_after();
           const uint32_t a_base = smem_u32(smem + (uint32_t)st * c.stage_bytes);
-          const uint32_t b_base = a_base + c.a_stage;
+          const uint32_t b_base = c.wres ? smem_u32(wsm) + (uint32_t)ch * 18 * c.b_block : a_base + c.a_stage;
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3 - 1, dxi = tap % 3;  // dxi = dx + 1
@@ -451,6 +504,9 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
       mbar_arrive(&tempty[kt & 1]);  // this set may take the next tile's MMAs
     }
   }
+  // The resident weights' copies have landed before the CTA's shared memory is released (at once
+  // unless a wait gave up before they did).
+  if (c.wres && tid == 0) wait_bounded(wbar, 0);
   tc_fence_before();
   __syncthreads();
   if (warp == kMmaWarp) tmem_dealloc(tmem, c.ncols);
@@ -468,6 +524,7 @@ __global__ void k_transpose_taps(const bf16* __restrict__ w, bf16* __restrict__ 
 }
 
 constexpr int kMaxSmem = 227 * 1024;
+constexpr int kMaxStages = 6;
 
 // The tile geometry and shared-memory plan for a layer, or false if the kernel cannot serve it.
 // *stages: stages of the ring (2 to 4, as many as fit).
@@ -500,7 +557,7 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
     c->RT = RT;
     c->a_block = (uint32_t)((RT + 2) * kRowSlots * 16);
     c->a_stage = 2 * c->a_block;
-    c->tx_bytes = (uint32_t)(2 * (RT + 2) * (kTileM + 2) * 16);
+    c->tx_bytes = (uint32_t)(2 * (RT + 2) * kTileM * 16);  // TMA mode: the boxes (halo pixels by loads)
   } else {
     if (kTileM % W || (W & (W - 1))) return false;
     c->rows_mode = 0;
@@ -524,17 +581,24 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
   const long long nt = (long long)batch * c->tiles_x * c->tiles_y * c->ntiles_n;
   if (nt > 0x7FFFFFFFll) return false;
   c->ntiles = (int)nt;
-  c->stage_bytes = c->a_stage + 18 * c->b_block;  // a multiple of 256 bytes: every stage 128-byte aligned
-  c->tx_bytes += 18 * c->b_block;
+  // Resident weights (TMA mode with one N tile, where they and two stages fit): the stages carry
+  // the input rows only.
+  const size_t tail = (2 * kMaxStages + 6) * sizeof(uint64_t) + 16;  // barriers, abort flag, TMEM slot
+  c->w_bytes = (uint32_t)(c->nchunks * 18 * c->b_block);
+  c->wres = c->tma && c->ntiles_n == 1 && (size_t)c->w_bytes + 2 * (size_t)c->a_stage + tail <= (size_t)kMaxSmem;
+  c->stage_bytes = c->wres ? c->a_stage : c->a_stage + 18 * c->b_block;  // multiples of 256 bytes
+  if (!c->wres) c->tx_bytes += 18 * c->b_block;
   // Instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
   // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
   c->idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
   c->up = up;
-  const size_t tail = (5 + 8) * sizeof(uint64_t) + 16;  // barriers (S <= 4), abort flag, TMEM slot
-  int st = 4;
-  while (st > 2 && (size_t)st * c->stage_bytes + tail > (size_t)kMaxSmem) --st;
+  const size_t wb = c->wres ? c->w_bytes : 0;
+  int st = kMaxStages;
+  while (st > 2 && (size_t)st * c->stage_bytes + wb + tail > (size_t)kMaxSmem) --st;
   *stages = st;
-  *smem = (size_t)st * c->stage_bytes + tail;
+  c->wres_off = (uint32_t)((size_t)st * c->stage_bytes);
+  c->bar_off = (uint32_t)((size_t)st * c->stage_bytes + wb);
+  *smem = (size_t)st * c->stage_bytes + wb + tail;
   // Descriptor start addresses are 14-bit multiples of 16 bytes: every operand must lie in the
   // first 256 KB of shared memory, which the 227 KB limit ensures.
   return *smem <= (size_t)kMaxSmem && c->ncols <= 512u;
@@ -616,6 +680,8 @@ int launch(const void* x, const void* wt, const float* bias, const void* addend,
   if (!plan(batch, H, W, K, N, up != 0, &c, &smem, &stages)) return SUR_ERR_PARAM;
   c.relu = relu;
   c.out_f32 = out_f32;
+  if (stages == 6) return launch_s<6>(c, smem, batch, x, wt, bias, addend, y, s);
+  if (stages == 5) return launch_s<5>(c, smem, batch, x, wt, bias, addend, y, s);
   if (stages == 4) return launch_s<4>(c, smem, batch, x, wt, bias, addend, y, s);
   if (stages == 3) return launch_s<3>(c, smem, batch, x, wt, bias, addend, y, s);
   return launch_s<2>(c, smem, batch, x, wt, bias, addend, y, s);

@@ -46,7 +46,8 @@ SUR_API int sur_conv3x3(const void* x, const void* w, const float* bias, void* y
  * upsampled = 1: x is the coarse (batch, H/2, W/2, K) image read through the 2x nearest
  * upsampling (the decoder), as sur_conv3x3_up_add.  bias and addend may be NULL; an addend needs
  * BF16 output.  The kernel tiles 128 pixels (R rows of TW = min(W, 128) columns) by up to 128
- * output channels: W must be a multiple of 128 or divide 128, H a multiple of 128 / TW (H, W even
+ * output channels: W must be a multiple of 128 or a power of two from 2 to 64, H a multiple of
+ * 128 / TW (H, W even
  * when upsampled), K and N multiples of 16, N <= 128 or a multiple of 128;
  * sur_conv3x3_tc_supported (1 / 0) says whether a shape qualifies.  Errors: SUR_ERR_PARAM (a shape
  * it cannot serve, NULL or misaligned pointers), SUR_ERR_CUDA.  Its waits are bounded: see

@@ -18,14 +18,14 @@
 //     upsampling the rows come in by TMA (a tensor map over the NHWC input, one 128-pixel box
 //     per row and octet, and 16-byte bulk copies for the two wrapped halo pixels) issued by one
 //     thread, completing the stage's mbarrier by byte count.
-//   * copy mode (W < 128, W a power of two dividing 128): one accumulator of R = 128/W full rows,
-//     which a start offset cannot shift by a column across the row seams, so A holds the R + 2
-//     rows around them in three copies shifted by dx = -1, 0, +1 with the periodic wrap applied
-//     while staging: [dx][octet][halo-tile pixel][8 x BF16]; tap (dy, dx) starts at pixel
-//     (dy + 1) * W of copy dx.
+//   * copy mode (W < 128, W a power of two dividing 128): RT accumulators of R = 128/W full rows
+//     each, which a start offset cannot shift by a column across the row seams, so A holds the
+//     RT R + 2 rows around them in three copies shifted by dx = -1, 0, +1 with the periodic wrap
+//     applied while staging: [dx][octet][halo-tile pixel][8 x BF16]; tap (dy, dx) of accumulator r
+//     starts at pixel (r R + dy + 1) * W of copy dx.
 //   * B: the 9 taps' weights for the N tile, from the K-major copy [tap][N][K] (see
-//     sur_transpose_taps): [octet][tap][output channel][8 x BF16] (by TMA: one box per octet),
-//     shared by every accumulator.
+//     sur_transpose_taps): [octet][tap][output channel][8 x BF16], by TMA in every mode (one box
+//     per octet), shared by every accumulator.
 // A persistent CTA walks its tiles; every (tile, 16-channel chunk) is an item of a ring of S
 // (2 to 6) shared-memory stages, filled by TMA (one lane per octet and staged row; with one N
 // tile the weights of all chunks stay resident, loaded once) or, in copy mode and when
@@ -132,7 +132,7 @@ struct ConvTC {
   int K, N;             // input / output channels
   int rows_mode;        // 1: row mode (W >= 128), 0: copy mode
   int TW, R;            // copy mode: tile of R rows x TW = W columns; row mode: TW = 128, R = 1
-  int RT;               // row mode: output rows (accumulators) per tile; copy mode: 1
+  int RT;               // accumulators per tile: row mode output rows, copy mode blocks of R rows
   int tw_shift;         // log2(TW)
   int tiles_x, tiles_y; // M tiles per image along x and y
   int ntiles_n;         // N tiles
@@ -162,6 +162,11 @@ constexpr int kMmaWarp = 4;
 constexpr int kThreadsP = 288;
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Raise the barrier's expected transaction count of its current phase without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -203,7 +208,7 @@ __device__ __forceinline__ TileCoord tile_coord(const ConvTC& c, int t) {
   const int per_img = c.tiles_x * c.tiles_y;
   q.b = m / per_img;
   const int rem = m - q.b * per_img;
-  q.y0 = (rem / c.tiles_x) * (c.rows_mode ? c.RT : c.R);
+  q.y0 = (rem / c.tiles_x) * (c.rows_mode ? c.RT : c.RT * c.R);
   q.x0 = (rem % c.tiles_x) * c.TW;
   q.n0 = nt * c.ntile;
   return q;
@@ -360,7 +365,7 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
               }
             }
         } else {
-          const int arows = (c.R + 2) * c.TW;
+          const int arows = (c.RT * c.R + 2) * c.TW;
           for (int blk = 0; blk < 6; ++blk) {  // dx * 2 + octet
             const int dx = blk >> 1, kc = blk & 1;
             for (int j = tid; j < arows; j += kProducers) {
@@ -370,12 +375,9 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
             }
           }
         }
-        for (int e = tid; e < 18 * c.ntile; e += kProducers) {
-          const int blk = e / c.ntile;  // octet * 9 + tap
-          const int n = e - blk * c.ntile;
-          const int kc = blk / 9, tap = blk - kc * 9;
-          cp_async16(smem_u32(Bm + blk * c.b_block + n * 16),
-                     wt + ((size_t)tap * c.N + q.n0 + n) * c.K + k0 + kc * 8);
+        if (tid == 0) {  // the item's weights: two tensor-map boxes (one per octet) on the stage barrier
+          mbar_expect_tx(&full[st], 18 * c.b_block);
+          for (int kc = 0; kc < 2; ++kc) tma_load_3d(Bm + kc * 9 * c.b_block, &tm_w, k0 + kc * 8, q.n0, 0, &full[st]);
         }
         cp_async_commit();
         if (i >= 1) {
@@ -426,8 +428,11 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
                 tc_mma(tmem + set + (uint32_t)r * c.acc_cols, smem_desc(start, c.a_block, 128), bd, c.idesc, acc);
               }
             } else {
-              const uint32_t start = a_base + (uint32_t)(dxi * 2) * c.a_block + (uint32_t)((dy + 1) * c.TW * 16);
-              tc_mma(tmem + set, smem_desc(start, c.a_block, 128), bd, c.idesc, acc);
+              for (int r = 0; r < c.RT; ++r) {  // accumulator r: image rows r R .. r R + R - 1 of the tile
+                const uint32_t start =
+                    a_base + (uint32_t)(dxi * 2) * c.a_block + (uint32_t)((r * c.R + dy + 1) * c.TW * 16);
+                tc_mma(tmem + set + (uint32_t)r * c.acc_cols, smem_desc(start, c.a_block, 128), bd, c.idesc, acc);
+              }
             }
           }
           tc_commit(smem_u32(&empty[st]));  // the stage is free once these MMAs are done
@@ -452,9 +457,9 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
       tc_fence_after();
       const TileCoord q = tile_coord(c, t);
       const uint32_t set = (uint32_t)(kt & 1) * c.set_cols;
-      const int nacc = c.rows_mode ? c.RT : 1;
+      const int nacc = c.RT;
       for (int r = 0; r < nacc; ++r) {
-        const int py = c.rows_mode ? q.y0 + r : q.y0 + (i >> c.tw_shift);
+        const int py = c.rows_mode ? q.y0 + r : q.y0 + r * c.R + (i >> c.tw_shift);
         const int px = c.rows_mode ? q.x0 + i : q.x0 + (i & (c.TW - 1));
         const size_t pix = ((size_t)q.b * c.H + py) * c.W + px;
         for (int j0 = 0; j0 < c.ntile; j0 += 16) {
@@ -567,8 +572,15 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
     int sh = 0;
     while ((1 << sh) < W) ++sh;
     c->tw_shift = sh;
-    c->RT = 1;
-    c->a_block = (uint32_t)((c->R + 2) * W * 16);
+    // accumulators per tile (RT of R rows each, sharing every staged weight chunk): the most of 4,
+    // 2, 1 that divides the image's row blocks and whose two sets fit the 512 TMEM columns
+    int RT = 4;
+    auto fits2 = [&](int rt) {  // two stages of the three shifted copies and the weights
+      return 2 * (6 * (size_t)((rt * c->R + 2) * W * 16) + 18 * (size_t)c->b_block) + 256 <= (size_t)kMaxSmem;
+    };
+    while (RT > 1 && ((H / c->R) % RT || (uint32_t)RT * ncols1 > 256u || !fits2(RT))) RT >>= 1;
+    c->RT = RT;
+    c->a_block = (uint32_t)((RT * c->R + 2) * W * 16);
     c->a_stage = 6 * c->a_block;
     c->tx_bytes = c->a_stage;
   }
@@ -577,7 +589,7 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
   c->set_cols = (uint32_t)c->RT * ncols1;
   c->ncols = 2 * c->set_cols;
   c->tiles_x = W / c->TW;
-  c->tiles_y = H / (c->rows_mode ? c->RT : c->R);
+  c->tiles_y = H / (c->rows_mode ? c->RT : c->RT * c->R);
   const long long nt = (long long)batch * c->tiles_x * c->tiles_y * c->ntiles_n;
   if (nt > 0x7FFFFFFFll) return false;
   c->ntiles = (int)nt;
@@ -586,7 +598,10 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
   const size_t tail = (2 * kMaxStages + 6) * sizeof(uint64_t) + 16;  // barriers, abort flag, TMEM slot
   c->w_bytes = (uint32_t)(c->nchunks * 18 * c->b_block);
   c->wres = c->tma && c->ntiles_n == 1 && (size_t)c->w_bytes + 2 * (size_t)c->a_stage + tail <= (size_t)kMaxSmem;
-  c->stage_bytes = c->wres ? c->a_stage : c->a_stage + 18 * c->b_block;  // multiples of 256 bytes
+  // Tensor-map copies land on 128-byte boundaries: the weight boxes follow the A operand of a
+  // stage and every stage starts where the previous one ends.
+  if (c->a_stage % 128 || c->b_block % 128) return false;
+  c->stage_bytes = c->wres ? c->a_stage : c->a_stage + 18 * c->b_block;
   if (!c->wres) c->tx_bytes += 18 * c->b_block;
   // Instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
   // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -624,14 +639,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool make_maps(const ConvTC& c, int batch, const void* x, const void* wt, CUtensorMap* rows, CUtensorMap* w) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
-  const cuuint64_t xd[4] = {(cuuint64_t)c.K, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)batch};
-  const cuuint64_t xs[3] = {(cuuint64_t)c.K * 2, (cuuint64_t)c.W * c.K * 2, (cuuint64_t)c.H * c.W * c.K * 2};
-  const cuuint32_t xb[4] = {8, (cuuint32_t)kTileM, 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
-  if (enc(rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), xd, xs, xb, es,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
+  if (c.tma) {
+    const cuuint64_t xd[4] = {(cuuint64_t)c.K, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)batch};
+    const cuuint64_t xs[3] = {(cuuint64_t)c.K * 2, (cuuint64_t)c.W * c.K * 2, (cuuint64_t)c.H * c.W * c.K * 2};
+    const cuuint32_t xb[4] = {8, (cuuint32_t)kTileM, 1, 1};
+    if (enc(rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), xd, xs, xb, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
   const cuuint64_t wd[3] = {(cuuint64_t)c.K, (cuuint64_t)c.N, 9};
   const cuuint64_t ws[2] = {(cuuint64_t)c.K * 2, (cuuint64_t)c.N * c.K * 2};
   const cuuint32_t wb[3] = {8, (cuuint32_t)c.ntile, 9};
@@ -646,7 +663,7 @@ int launch_s(const ConvTC& c, size_t smem, int batch, const void* x, const void*
   CUtensorMap tm_rows, tm_w;
   std::memset(&tm_rows, 0, sizeof(tm_rows));
   std::memset(&tm_w, 0, sizeof(tm_w));
-  if (c.tma && !make_maps(c, batch, x, wt, &tm_rows, &tm_w)) return SUR_ERR_CUDA;
+  if (!make_maps(c, batch, x, wt, &tm_rows, &tm_w)) return SUR_ERR_CUDA;
   static bool configured = false;
   if (!configured) {
     if (cudaFuncSetAttribute(k_conv3x3_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess)

@@ -209,6 +209,7 @@ class UNet:
         # forward convolutions on the tcgen05 kernel (sur_conv3x3_tc) where it serves the shape;
         # False: the mma.sync kernels only (the reference path of the same arithmetic)
         self.tensor_cores = tensor_cores
+        self.sms = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
         self.ch, self.cin = tuple(ch), cin
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.s = self.stream.cuda_stream
@@ -255,11 +256,15 @@ class UNet:
         return t
 
     def _tc(self, B, H, W, ci, co, up=0):
-        # The tcgen05 kernel where it measured faster than the mma.sync one: rows of 128 pixels or
-        # more, staged by TMA (not upsampled).  Narrower images (three shifted copies staged by
-        # cp.async) and the upsampled decoder input ran slower on it; both kernels give the same
-        # bits (same accumulation order), so the choice changes only the time.
-        return (self.tensor_cores and not up and W >= 128 and
+        # The tcgen05 kernel where it measured faster than the mma.sync one (GB300): layers with at
+        # least one 128 x 128 output tile per SM (its persistent CTAs take one SM each; smaller layers
+        # leave most SMs idle: batch 4 with every supported layer on it ran 0.469 against 0.387 ms
+        # per forward), except the upsampled convolutions of rows of 256 pixels or more
+        # (cp.async-staged rows: 256^2 64 -> 32 at batch 16, 169 against 163 us).  Elsewhere it is
+        # faster (batch 16: 64^2 128 -> 128 58 against 64 us, 128^2 64 -> 64 47 against 64 us).
+        # Both kernels give the same bits (same accumulation order): the choice changes only time.
+        tiles = B * H * W // 128 * max(1, co // 128)  # 128-pixel x 128-channel tiles
+        return (self.tensor_cores and not (up and W >= 256) and tiles >= self.sms and
                 sur_conv3x3_tc_supported(B, H, W, ci, co, up))
 
     def _conv(self, x, name, B, H, W, relu, out_f32=False, key=None):
@@ -396,6 +401,14 @@ class UNet:
         sur_mse3(pred, target, dpred, loss, self.s)
         self.backward(dpred)
         return loss
+
+    def load_weights(self, name, w):
+        """Set layer `name`'s FP32 weights, shape (9, Cin, Cout), and refresh its BF16 copy and the
+        K-major copy the tcgen05 kernel reads."""
+        _, ci, co = next(l for l in self.layers if l[0] == name)
+        self.w[name].copy_(w)
+        sur_cast_bf16(self.w[name], self.wb[name], self.s)
+        sur_transpose_taps(self.wb[name], self.wt[name], ci, co, self.s)
 
     def adam_step(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1

@@ -158,8 +158,7 @@ def test_unet_gradients_match_oracle(S):
     net = S.UNet(ch=ch, cin=cin, seed=3)
     rng = np.random.default_rng(9)
     # a non-zero output layer, so every layer receives gradient
-    net.w["out"] = torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda()
-    S.sur_cast_bf16(net.w["out"], net.wb["out"], net.s)
+    net.load_weights("out", torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda())
     B, H, W = 2, 16, 16
     x, xn = _bf(rng, (B, H, W, cin), 0.5)
     base = x[..., :3].float().contiguous()
@@ -204,8 +203,7 @@ def test_graph_replayed_forward_equals_eager(S):
     ch, cin = (16, 32, 64), 16
     net = S.UNet(ch=ch, cin=cin, seed=5)
     rng = np.random.default_rng(11)
-    net.w["out"] = torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda()
-    S.sur_cast_bf16(net.w["out"], net.wb["out"], net.s)
+    net.load_weights("out", torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda())
     B, H, W = 3, 32, 48
     x, _ = _bf(rng, (B, H, W, cin), 0.5)
     base = x[..., :3].float().contiguous()
@@ -368,16 +366,15 @@ def test_tcgen05_conv_refuses_shapes_it_cannot_tile(S):
 
 
 def test_network_forward_same_on_both_tensor_core_paths(S):
-    """The U-Net forward with its 256^2 and 128^2 convolutions on the tcgen05 kernel equals the
-    forward on the mma.sync kernels bit for bit: both accumulate every 16-channel chunk tap by tap
-    in the same order on the same tensor-core dot products."""
+    """The U-Net forward with every convolution the tcgen05 kernel serves on it (all but the
+    upsampled 256^2 one: TMA rows, multi-accumulator shifted copies, upsampled rows of 128)
+    equals the forward on the mma.sync kernels bit for bit: both accumulate every 16-channel chunk
+    tap by tap in the same order on the same tensor-core dot products."""
     import torch
     net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
     g = torch.Generator(device="cuda").manual_seed(3)
     s = torch.cuda.current_stream().cuda_stream
-    net.w["out"].copy_(torch.randn(net.w["out"].shape, device="cuda", generator=g) * 0.05)
-    S.sur_cast_bf16(net.w["out"], net.wb["out"], s)
-    S.sur_transpose_taps(net.wb["out"], net.wt["out"], 32, 16, s)
+    net.load_weights("out", torch.randn(net.w["out"].shape, device="cuda", generator=g) * 0.05)
     x = (torch.randn((2, 256, 256, 16), device="cuda", generator=g) * 0.5).to(torch.bfloat16)
     base = x[..., :3].float().contiguous()
     net.tensor_cores = True

@@ -71,7 +71,7 @@ def measured_peaks():
 # FP64) and, for 16-bit storage, k_step_pair as well.  Host-side files (launchers, the C ABI) are
 # left out: editing them does not change what the kernel reads and writes.
 STEP_SOURCES = ("lbm_step.cuh", "lbm_device.cuh")
-PAIR_SOURCES = STEP_SOURCES + ("lbm_pair.cu", "lbm_f2.cuh")
+PAIR_SOURCES = STEP_SOURCES + ("lbm_pair.cu", "lbm_pair.cuh", "lbm_f2.cuh")
 
 
 def kernel_source_hash(prec: str = "fp32"):

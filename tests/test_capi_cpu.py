@@ -114,3 +114,25 @@ def test_stochastic_rounding_only_for_16bit_storage(lbm):
         with pytest.raises(lbm.LbmError) as ei:
             lbm.lbm_batch_state_bytes([p, p])
         assert ei.value.status == lbm.LBM_ERR_PARAM
+
+
+def test_tcgen05_conv_planner_host_side(lbm):
+    """The tcgen05 convolution's tiling rules, answered on the host without a GPU: rows of 128
+    pixels or a multiple (row mode), or a power-of-two width from 2 to 64 dividing 128 (copy mode:
+    whole rows per tile, weights by tensor-map boxes, so every stage lands on 128-byte
+    boundaries); heights a multiple of the tile's rows; channels multiples of 16; more than 128
+    output channels only in whole 128-channel tiles; even sizes when upsampled."""
+    from paper_1803_11345_gb300 import surrogate as S
+    ok = [(16, 256, 256, 16, 32, 0), (16, 128, 128, 64, 64, 0), (16, 64, 64, 128, 128, 0),
+          (16, 32, 32, 256, 256, 0), (2, 8, 256, 48, 96, 0), (1, 16, 32, 16, 16, 0), (2, 64, 2, 16, 16, 0),
+          (16, 256, 256, 64, 32, 1), (16, 64, 64, 256, 128, 1)]
+    bad = [(1, 16, 96, 32, 32, 0),    # width neither a multiple of 128 nor a power of two below it
+           (1, 6, 32, 32, 32, 0),     # height not a multiple of the 4 rows a 32-wide tile holds
+           (1, 16, 32, 24, 32, 0),    # input channels not a multiple of 16
+           (1, 16, 32, 32, 160, 0),   # 160 output channels: not a whole number of 128-channel tiles
+           (1, 256, 1, 16, 16, 0),    # width 1: a stage would not end on a 128-byte boundary
+           (1, 15, 256, 32, 32, 1)]   # odd height through the 2x upsampling
+    for shape in ok:
+        assert S.sur_conv3x3_tc_supported(*shape), shape
+    for shape in bad:
+        assert not S.sur_conv3x3_tc_supported(*shape), shape

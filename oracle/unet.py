@@ -93,64 +93,82 @@ def flux_update_bwd(dpred, C):
     return dout
 
 
-def unet_forward(x, params, ch):
-    """Returns (prediction = flux_update(net(x), x), cache of activations)."""
+def bf16_round(x):
+    """x rounded to the nearest BF16 value (8 significant bits, ties to even), as float64: with
+    x = m 2^e, 1/2 <= |m| < 1, the value round(256 m) 2^(e - 8); a carry to 256 m = 256 gives
+    2^e, the next binade's first value.  (Below BF16's normal range, 2^-126, it keeps 8 bits
+    where BF16 has fewer; no activation of the network comes near it.)"""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
+def unet_forward(x, params, ch, bf16=False):
+    """Returns (prediction = flux_update(net(x), x), cache of activations).  bf16: every
+    activation the network stores in BF16 is rounded to it, once, from its exact value (pooled
+    maps; convolution outputs after bias and ReLU; the decoder's sum of convolution, bias and
+    skip); the output convolution and the prediction stay exact."""
+    r = bf16_round if bf16 else (lambda v: v)
     L = len(ch)
     cache = {"x": x}
     h = x
     skips = []
     for l in range(L):
         if l > 0:
-            h = pool2(h)
+            h = r(pool2(h))
             cache[f"p{l}"] = h
-        h = conv3x3(h, params[f"e{l}a"][0], params[f"e{l}a"][1], relu=True)
+        h = r(conv3x3(h, params[f"e{l}a"][0], params[f"e{l}a"][1], relu=True))
         cache[f"e{l}a"] = h
-        h = conv3x3(h, params[f"e{l}b"][0], params[f"e{l}b"][1], relu=True)
+        h = r(conv3x3(h, params[f"e{l}b"][0], params[f"e{l}b"][1], relu=True))
         cache[f"e{l}b"] = h
         skips.append(h)
     for l in range(L - 2, -1, -1):
         up = up2(h)
         cache[f"up{l}"] = up
         t = conv3x3(up, params[f"u{l}"][0], params[f"u{l}"][1], relu=False)
-        s = t + skips[l]
+        s = r(t + skips[l])
         cache[f"s{l}"] = s
-        h = conv3x3(s, params[f"d{l}"][0], params[f"d{l}"][1], relu=True)
+        h = r(conv3x3(s, params[f"d{l}"][0], params[f"d{l}"][1], relu=True))
         cache[f"d{l}"] = h
     cache["top"] = h
     out = conv3x3(h, params["out"][0], params["out"][1], relu=False)
     return flux_update(out, x), cache
 
 
-def unet_loss_and_grads(x, target, params, ch):
+def unet_loss_and_grads(x, target, params, ch, bf16=False):
     """Mean squared error of the prediction (phi, ux, uy) against target, and the gradients of
-    every weight and bias (reverse mode, written out layer by layer)."""
-    pred, c = unet_forward(x, params, ch)
+    every weight and bias (reverse mode, written out layer by layer).  bf16: the forward of
+    unet_forward(bf16=True), and every activation gradient the network stores in BF16 rounded
+    to it once from its exact value (the output's gradient, each convolution's input gradient,
+    the sums of a skip's and the decoder's gradients and of the 2x2 upsampling's four pixels);
+    weight and bias gradients stay exact."""
+    r = bf16_round if bf16 else (lambda v: v)
+    pred, c = unet_forward(x, params, ch, bf16)
     L = len(ch)
     err = pred - target
     n = err.size
     loss = float((err ** 2).sum() / n)
-    dout = flux_update_bwd(2.0 * err / n, x.shape[-1])
+    dout = r(flux_update_bwd(2.0 * err / n, x.shape[-1]))
     g = {}
     g["out"] = (conv3x3_bwd_weight(c["top"], dout), dout.sum(axis=(0, 1, 2)))
-    dh = conv3x3_bwd_data(dout, params["out"][0])
+    dh = r(conv3x3_bwd_data(dout, params["out"][0]))
     dskip = [None] * L
     for l in range(0, L - 1):
         dh = dh * (c[f"d{l}"] > 0)
         g[f"d{l}"] = (conv3x3_bwd_weight(c[f"s{l}"], dh), dh.sum(axis=(0, 1, 2)))
-        ds = conv3x3_bwd_data(dh, params[f"d{l}"][0])
+        ds = r(conv3x3_bwd_data(dh, params[f"d{l}"][0]))
         dskip[l] = ds
         g[f"u{l}"] = (conv3x3_bwd_weight(c[f"up{l}"], ds), ds.sum(axis=(0, 1, 2)))
-        dh = up2_bwd(conv3x3_bwd_data(ds, params[f"u{l}"][0]))
+        dh = r(up2_bwd(r(conv3x3_bwd_data(ds, params[f"u{l}"][0]))))
     for l in range(L - 1, -1, -1):
         if dskip[l] is not None and l < L - 1:
-            dh = dh + dskip[l]
+            dh = r(dh + dskip[l])
         dh = dh * (c[f"e{l}b"] > 0)
         g[f"e{l}b"] = (conv3x3_bwd_weight(c[f"e{l}a"], dh), dh.sum(axis=(0, 1, 2)))
-        dh = conv3x3_bwd_data(dh, params[f"e{l}b"][0])
+        dh = r(conv3x3_bwd_data(dh, params[f"e{l}b"][0]))
         dh = dh * (c[f"e{l}a"] > 0)
         inp = c[f"p{l}"] if l > 0 else c["x"]
         g[f"e{l}a"] = (conv3x3_bwd_weight(inp, dh), dh.sum(axis=(0, 1, 2)))
-        dh = conv3x3_bwd_data(dh, params[f"e{l}a"][0])
         if l > 0:
-            dh = pool2_bwd(dh)
+            dh = r(conv3x3_bwd_data(dh, params[f"e{l}a"][0]))
+            dh = pool2_bwd(dh)  # a quarter of a BF16 value is one
     return loss, g

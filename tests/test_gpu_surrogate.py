@@ -31,6 +31,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+
 @pytest.mark.parametrize("K,N", [(16, 16), (16, 32), (32, 64), (48, 96)])
 def test_conv_forward_backward_match_oracle(S, K, N):
     import torch
@@ -174,6 +175,45 @@ def test_unet_gradients_match_oracle(S):
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
         assert _rel(a, b) < 0.1 and cos > 0.99, (name, _rel(a, b), cos)
         assert _rel(gg[name][1], go[name][1]) < 0.1, name
+
+
+# (channels, batch, H, W, per-layer relative error, 1 - cosine, loss relative error)
+BF16_ORACLE_CASES = [((16, 32, 32), 2, 16, 16, 1e-2, 1e-4, 1e-5), ((32, 64, 128, 256), 2, 64, 64, 3e-2, 1e-3, 1e-3)]
+
+
+@pytest.mark.parametrize("ch,B,H,W,rel_max,cos_gap,loss_rel", BF16_ORACLE_CASES)
+def test_unet_gradients_match_bf16_oracle(S, ch, B, H, W, rel_max, cos_gap, loss_rel):
+    """Whole-network forward and backward on the GPU against the FP64 oracle that rounds every
+    stored activation and activation gradient to BF16 where the network stores them in BF16
+    (oracle unet_loss_and_grads(bf16=True)): the two then differ only by the GPU's FP32
+    accumulation, which can tip a value to the other side of a BF16 rounding or of a ReLU's
+    zero.  Small network (K up to 9 x 32): measured worst layer 5e-7, loss 1e-7, against 4e-2
+    for the unrounded oracle.  The surrogate's own four-level shape on 64^2 images (K up to
+    9 x 256, so more values tip): worst layer 1.2e-2 (the first layer, whose gradient sums every
+    tipped value downstream), 1 - cosine 7e-5, loss 1.6e-4, against 2.2e-2 and 2.3e-4."""
+    import torch
+    cin = 16
+    net = S.UNet(ch=ch, cin=cin, seed=3)
+    rng = np.random.default_rng(11)
+    net.load_weights("out", torch.tensor(rng.standard_normal((9, ch[0], cin)) * 0.1, dtype=torch.float32).cuda())
+    x, xn = _bf(rng, (B, H, W, cin), 0.5)
+    base = x[..., :3].float().contiguous()
+    target = torch.tensor(rng.standard_normal((B, H, W, 3)) * 0.1, dtype=torch.float32).cuda()
+    loss = net.loss_and_grads(x, base, target)
+    torch.cuda.synchronize()
+    params = net.params_numpy()
+    lo, go = U.unet_loss_and_grads(xn, target.cpu().numpy().astype(np.float64), params, ch, bf16=True)
+    assert abs(loss.item() - lo) / lo < loss_rel, (loss.item(), lo)
+    gg = net.grads_numpy()
+    worst = 0.0
+    for name, _, _ in S.layer_specs(cin, ch):
+        a, b = gg[name][0].ravel(), go[name][0].ravel()
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+        rel = _rel(a, b)
+        worst = max(worst, rel)
+        assert rel < rel_max and cos > 1 - cos_gap, (name, rel, cos)
+        assert _rel(gg[name][1], go[name][1]) < rel_max, (name, _rel(gg[name][1], go[name][1]))
+    print(ch, "worst per-layer weight-gradient relative error against the BF16-rounding oracle:", worst)
 
 
 def test_training_reduces_loss(S):

@@ -93,3 +93,20 @@ def test_unet_gradient_against_finite_differences():
         lm, _ = U.unet_forward(x, {**params, name: (w, b2)}, ch)
         fd = (np.mean((lp - target) ** 2) - np.mean((lm - target) ** 2)) / (2 * h)
         assert np.isclose(g[name][1][0], fd, rtol=2e-5, atol=1e-9), name
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    """The oracle's BF16 rounding against the library's single rounding of FP32 values to BF16
+    (torch on the CPU): random FP32 values over 40 binades, exact ties (which go to the even
+    8-bit significand) and the carry into the next binade; and idempotence."""
+    import torch
+    rng = np.random.default_rng(5)
+    x32 = (rng.standard_normal(100000) * np.exp(rng.uniform(-20, 20, 100000))).astype(np.float32)
+    ties = np.array([(128 + k + 0.5) * 2.0 ** -8 for k in range(128)], dtype=np.float32)  # m*256 = k + 1/2
+    carry = np.array([255.5 * 2.0 ** -8, -255.75 * 2.0 ** -8, 255.25 * 2.0 ** -8], dtype=np.float32)
+    for v in (x32, ties, carry):
+        want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+        got = U.bf16_round(v.astype(np.float64))
+        assert np.array_equal(got, want)
+    assert np.array_equal(U.bf16_round(U.bf16_round(x32.astype(np.float64))), U.bf16_round(x32.astype(np.float64)))
+    assert U.bf16_round(np.array([255.5 * 2.0 ** -8]))[0] == 1.0  # tie at 255.5 rounds to even 256: the carry

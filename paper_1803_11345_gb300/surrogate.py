@@ -536,13 +536,15 @@ class SolverWindows:
         self.bat.close()
 
 
-def rollout(net, members, state0, windows, K, judge, stream=None, inject=None):
+def rollout(net, members, state0, windows, K, judge, stream=None, inject=None, graph=True):
     """Advance the lattices `members` [(phi0, params)] from state0 (torch (B, H, W, 3) FP32 on the
     device: phi, ux, uy) by `windows` windows of K solver steps with the surrogate, under `judge`,
     the solver advancing every window the judge does not keep.  Closed loop: each kept prediction
     is the next window's input.  Everything runs on one stream; the wall time includes the judge's
     reductions, its per-window read of 2B FP64 sums and every audit and fallback.  inject(w, pred)
-    (optional) may alter the prediction of window w before it is judged (tests).
+    (optional) may alter the prediction of window w before it is judged (tests).  graph: the
+    window's packing, network forward and unpacking replay as one CUDA graph over fixed buffers
+    (captured before the timed loop; the states are then copied, not swapped).
     Returns (state, stats)."""
     import time as _time
 
@@ -566,19 +568,32 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None):
         with torch.cuda.stream(stream):
             state.copy_(state0)
             net.forward(x, base)  # buffers exist before timing
+
+            def predict():  # state -> cand through the network
+                sur_pack_state(state, x, base, B * npix, net.cin, U_SCALE, s)
+                pred = net.forward(x, base)
+                sur_unpack_state(pred, cand, B * npix, U_SCALE, s)
+
+            g = None
+            if graph:
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    predict()
             torch.cuda.synchronize()
             t0 = _time.perf_counter()
             suspended = 0
             for w in range(windows):
                 if suspended:
                     solver.advance(state, solv)
-                    state, solv = solv, state
+                    state.copy_(solv)
                     stats["solver"] += 1
                     suspended -= 1
                     continue
-                sur_pack_state(state, x, base, B * npix, net.cin, U_SCALE, s)
-                pred = net.forward(x, base)
-                sur_unpack_state(pred, cand, B * npix, U_SCALE, s)
+                if g is not None:
+                    g.replay()
+                else:
+                    predict()
                 if inject is not None:
                     inject(w, cand)
                 sur_phi_sums(state, B, npix, 3, sums[:B], s)
@@ -587,7 +602,7 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None):
                 drift = np.abs(sv[B:] - sv[:B]) / npix
                 if not (np.all(np.isfinite(sv)) and np.all(drift <= judge.drift)):
                     solver.advance(state, solv)
-                    state, solv = solv, state
+                    state.copy_(solv)
                     stats["drift_rejected"] += 1
                     stats["solver"] += 1
                     continue
@@ -600,9 +615,9 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None):
                     if not rms.max() <= judge.phi_err:
                         stats["audit_failed"] += 1
                         suspended = judge.audit_every
-                    state, solv = solv, state
+                    state.copy_(solv)
                     continue
-                state, cand = cand, state
+                state.copy_(cand)
                 stats["kept"] += 1
             torch.cuda.synchronize()
             stats["seconds"] = _time.perf_counter() - t0

@@ -313,7 +313,8 @@ def test_judged_rollout_against_the_solver(S, trained):
     assert max(stats["audit_rms"]) <= 1e-2
     assert err.max() <= 1e-2, err
     assert err.max() < 0.5 * np.median(pers), (err, pers)
-    # faster than the solver alone, every cost counted (measured 1.06 to 1.09)
+    # faster than the solver alone, every cost counted (measured 1.21 with the window's network
+    # part replayed as one CUDA graph; 1.06 to 1.09 launched eagerly)
     assert t_solver / stats["seconds"] > 1.0, (t_solver, stats["seconds"])
 
 

@@ -18,6 +18,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -137,11 +138,12 @@ int fail(lbm_batch* b, int code, const char* fmt, ...) {
 }
 
 std::string signature(const lbm_batch* b) {
-  std::vector<std::pair<int, int>> sizes;
-  for (auto& g : b->geo) sizes.emplace_back(g.nx, g.ny);
+  std::vector<std::tuple<int, int, int>> sizes;  // nx, ny, walls: the tiles that can serve a member
+  for (auto& g : b->geo) sizes.emplace_back(g.nx, g.ny, g.walls);
   std::sort(sizes.begin(), sizes.end());
   std::string s = "p" + std::to_string(b->prec) + "/sm" + std::to_string(b->sms) + "/";
-  for (auto& z : sizes) s += std::to_string(z.first) + "x" + std::to_string(z.second) + ",";
+  for (auto& z : sizes)
+    s += std::to_string(std::get<0>(z)) + "x" + std::to_string(std::get<1>(z)) + (std::get<2>(z) ? "w," : ",");
   return s;
 }
 
@@ -323,7 +325,7 @@ int lbm_batch_init(const lbm_params* params, int count, const double* const* phi
     {
       std::lock_guard<std::mutex> lock(g_cache_mutex);
       auto it = g_cache.find(signature(b));
-      if (it != g_cache.end()) {
+      if (it != g_cache.end() && (!it->second.first.pair || pair_ok(b))) {
         t = it->second.first;
         target = it->second.second;
       }

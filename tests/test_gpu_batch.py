@@ -149,7 +149,8 @@ def test_paired_batch_members_equal_single_lattices(lbm, prec, rounding):
 
 def test_paired_batch_refused_where_it_cannot_serve(lbm):
     """LBM_KERNEL_PAIR needs every member periodic with even nx and 16-bit storage; otherwise
-    lbm_batch_set_kernel refuses and the batch keeps its tile."""
+    lbm_batch_set_kernel refuses and the batch keeps its tile, and a new batch never starts with
+    it, even when the autotuner chose it for a batch of the same sizes without walls."""
     for mem, prec in (([(W.spinodal(64, 32, seed=1), dict()), (W.spinodal(65, 32, seed=2), dict())], "fp16s"),
                       ([(W.spinodal(64, 32, seed=1), dict()), (W.spinodal(64, 32, seed=2), dict(bc=1))], "fp16s"),
                       ([(W.spinodal(64, 32, seed=1), dict())], "fp32")):
@@ -158,7 +159,17 @@ def test_paired_batch_refused_where_it_cannot_serve(lbm):
         with pytest.raises(lbm.LbmError):
             bat.set_kernel(lbm.LBM_KERNEL_PAIR)
         assert bat.kernel == lbm.LBM_KERNEL_GENERIC and bat.tile == before
-        del bat
+        bat.close()
+    # The autotuner's cached winner for a periodic batch is not handed to a walled batch of the
+    # same sizes: the paired tile would step its walls as periodic rows.
+    sizes = [(96, 48), (64, 32)]
+    per = lbm.Batch([(W.spinodal(nx, ny, seed=nx), dict()) for nx, ny in sizes], prec="fp16s")
+    per.set_kernel(lbm.LBM_KERNEL_PAIR)
+    per.autotune(trial_steps=2)
+    per.close()
+    walled = lbm.Batch([(W.spinodal(nx, ny, seed=nx), dict(bc=1)) for nx, ny in sizes], prec="fp16s")
+    assert walled.kernel == lbm.LBM_KERNEL_GENERIC
+    walled.close()
 
 
 def test_batch_fp64_member_matches_oracle(lbm, orc):

@@ -544,8 +544,11 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None, g
     reductions, its per-window read of 2B FP64 sums and every audit and fallback.  inject(w, pred)
     (optional) may alter the prediction of window w before it is judged (tests).  graph: the
     window's packing, network forward and unpacking replay as one CUDA graph over fixed buffers
-    (captured before the timed loop; the states are then copied, not swapped).
-    Returns (state, stats)."""
+    (captured before the timed loop; the states are copied, not swapped).
+    While the host reads window w's sums, window w + 1 is already predicted from w's candidate
+    (not next to an audit); if the judge rejects w, that speculation is dropped, w's saved input
+    restored and the window handed to the solver, so the states are those of judging one window
+    at a time.  Returns (state, stats)."""
     import time as _time
 
     import torch
@@ -561,9 +564,17 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None, g
     cand = torch.empty_like(base)
     solv = torch.empty_like(base)
     state = torch.empty_like(base)
-    sums = torch.empty(2 * B, dtype=torch.float64, device=dev)
+    prev = torch.empty_like(base)  # input of the window being judged while the next is speculated
+    sums = [torch.empty(2 * B, dtype=torch.float64, device=dev) for _ in range(2)]
+    host = [torch.empty(2 * B, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    aud = torch.empty(B, dtype=torch.float64, device=dev)
     s = stream.cuda_stream
     stats = dict(windows=windows, kept=0, solver=0, audits=0, audit_failed=0, drift_rejected=0, audit_rms=[])
+
+    def is_audit(w):
+        return judge.audit_every > 0 and w % judge.audit_every == judge.audit_every - 1
+
     try:
         with torch.cuda.stream(stream):
             state.copy_(state0)
@@ -580,9 +591,24 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None, g
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=stream):
                     predict()
+
+            def launch(w):  # window w's prediction from state and its two sums, read back into host[w % 2]
+                if g is not None:
+                    g.replay()
+                else:
+                    predict()
+                if inject is not None:
+                    inject(w, cand)
+                sb = sums[w % 2]
+                sur_phi_sums(state, B, npix, 3, sb[:B], s)
+                sur_phi_sums(cand, B, npix, 3, sb[B:], s)
+                host[w % 2].copy_(sb, non_blocking=True)
+                done[w % 2].record(stream)
+
             torch.cuda.synchronize()
             t0 = _time.perf_counter()
             suspended = 0
+            pending = False
             for w in range(windows):
                 if suspended:
                     solver.advance(state, solv)
@@ -590,35 +616,41 @@ def rollout(net, members, state0, windows, K, judge, stream=None, inject=None, g
                     stats["solver"] += 1
                     suspended -= 1
                     continue
-                if g is not None:
-                    g.replay()
-                else:
-                    predict()
-                if inject is not None:
-                    inject(w, cand)
-                sur_phi_sums(state, B, npix, 3, sums[:B], s)
-                sur_phi_sums(cand, B, npix, 3, sums[B:], s)
-                sv = sums.cpu().numpy()
+                if not pending:
+                    launch(w)
+                spec = w + 1 < windows and not is_audit(w) and not is_audit(w + 1)
+                if spec:  # assume w is kept: predict w + 1 from its candidate meanwhile
+                    prev.copy_(state)
+                    state.copy_(cand)
+                    launch(w + 1)
+                done[w % 2].synchronize()
+                sv = host[w % 2].numpy()
                 drift = np.abs(sv[B:] - sv[:B]) / npix
                 if not (np.all(np.isfinite(sv)) and np.all(drift <= judge.drift)):
+                    if spec:
+                        state.copy_(prev)
                     solver.advance(state, solv)
                     state.copy_(solv)
                     stats["drift_rejected"] += 1
                     stats["solver"] += 1
+                    pending = False
                     continue
-                if judge.audit_every > 0 and w % judge.audit_every == judge.audit_every - 1:
+                if is_audit(w):
                     solver.advance(state, solv)
-                    sur_phi_sq_diff(cand, solv, B, npix, 3, sums[:B], s)
-                    rms = np.sqrt(sums[:B].cpu().numpy() / npix)
+                    sur_phi_sq_diff(cand, solv, B, npix, 3, aud, s)
+                    rms = np.sqrt(aud.cpu().numpy() / npix)
                     stats["audits"] += 1
                     stats["audit_rms"].append(float(rms.max()))
                     if not rms.max() <= judge.phi_err:
                         stats["audit_failed"] += 1
                         suspended = judge.audit_every
                     state.copy_(solv)
+                    pending = False
                     continue
-                state.copy_(cand)
+                if not spec:
+                    state.copy_(cand)
                 stats["kept"] += 1
+                pending = spec
             torch.cuda.synchronize()
             stats["seconds"] = _time.perf_counter() - t0
     finally:

@@ -313,8 +313,9 @@ def test_judged_rollout_against_the_solver(S, trained):
     assert max(stats["audit_rms"]) <= 1e-2
     assert err.max() <= 1e-2, err
     assert err.max() < 0.5 * np.median(pers), (err, pers)
-    # faster than the solver alone, every cost counted (measured 1.21 with the window's network
-    # part replayed as one CUDA graph; 1.06 to 1.09 launched eagerly)
+    # faster than the solver alone, every cost counted (measured 1.23 with the window's network
+    # part replayed as one CUDA graph and the next window predicted while the host judges;
+    # 1.06 to 1.09 launched eagerly one window at a time)
     assert t_solver / stats["seconds"] > 1.0, (t_solver, stats["seconds"])
 
 
@@ -322,7 +323,8 @@ def test_judge_rejects_a_drifting_prediction_and_falls_back_exactly(S, trained):
     """A prediction made to create order parameter (0.1 added to every phi of one lattice: a drift
     of 0.1 per node against the 1e-6 threshold) is rejected by the judge's FP64 sum check, and the
     window is advanced by the solver instead: the state after that window equals, bit for bit, the
-    solver's own advance of the window's input."""
+    solver's own advance of the window's input, also when the next window had already been
+    predicted speculatively from the rejected candidate."""
     import torch
     net, K = trained["net"], trained["K"]
     members = trained["test_members"][:4]
@@ -343,6 +345,13 @@ def test_judge_rejects_a_drifting_prediction_and_falls_back_exactly(S, trained):
     torch.cuda.synchronize()
     solver.close()
     assert torch.equal(fin, want)
+    # A third window: window 2 is predicted speculatively while window 1 is judged; the rejection
+    # drops it and restores window 1's input, so the run equals one window of the surrogate from
+    # the solver's advance of window 1.
+    fin3, stats3 = S.rollout(net, members, st0, 3, K, judge, inject=inject)
+    assert stats3["kept"] == 2 and stats3["drift_rejected"] == 1 and stats3["solver"] == 1, stats3
+    want3, _ = S.rollout(net, members, want, 1, K, judge)
+    assert torch.equal(fin3, want3)
 
 
 # -------------------------------------------------------------------------------------------

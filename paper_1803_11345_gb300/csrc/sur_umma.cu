@@ -318,16 +318,16 @@ k_conv3x3_tc(const bf16* __restrict__ x, const bf16* __restrict__ wt, const floa
             ok = false;
             break;
           }
-          if (lane < 4 * nrow) {
-            const int side = lane & 1, kc = (lane >> 1) / nrow, hr = (lane >> 1) - kc * nrow;
+          for (int e = lane; e < 4 * nrow; e += 32) {  // (octet, staged row, side)
+            const int side = e & 1, kc = (e >> 1) / nrow, hr = (e >> 1) - kc * nrow;
             const int yy = wrap(q.y0 + hr - 1, c.H);
             const int xx = side ? wrap(q.x0 + kTileM, c.W) : wrap(q.x0 - 1, c.W);
             const uint4 v = __ldg(reinterpret_cast<const uint4*>(
                 x + (((size_t)q.b * c.H + yy) * c.W + xx) * c.K + ch * 16 + kc * 8));
             unsigned char* row = smem + (uint32_t)st * c.stage_bytes + kc * c.a_block + hr * (kRowSlots * 16);
             *reinterpret_cast<uint4*>(row + (side ? kRowFirst + 1 + kTileM : kRowFirst) * 16) = v;
-            fence_proxy_async();
           }
+          fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&full[st]);
         }
@@ -569,9 +569,10 @@ bool plan(int batch, int H, int W, int K, int N, bool up, ConvTC* c, size_t* sme
     c->TW = kTileM;
     c->R = 1;
     c->tw_shift = 7;
-    // output rows per tile: the most of 4, 2, 1 dividing H whose two accumulator sets fit the
-    // 512 TMEM columns
-    int RT = 4;
+    // output rows per tile: the most of 8, 4, 2, 1 dividing H whose two accumulator sets fit the
+    // 512 TMEM columns (8 for up to 32 output channels: each staged row then serves more outputs;
+    // batch 16, 256^2 32 -> 32: 56 us against 67 at 4 rows)
+    int RT = 8;
     while (RT > 1 && (H % RT || (uint32_t)RT * ncols1 > 256u)) RT >>= 1;
     c->RT = RT;
     c->a_block = (uint32_t)((RT + 2) * kRowSlots * 16);

@@ -210,6 +210,8 @@ class UNet:
         # False: the mma.sync kernels only (the reference path of the same arithmetic)
         self.tensor_cores = tensor_cores
         self.sms = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
+        self.autotune = True  # time each convolution shape on both kernels at its first use (outside capture)
+        self._choice = {}
         self.ch, self.cin = tuple(ch), cin
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.s = self.stream.cuda_stream
@@ -256,16 +258,52 @@ class UNet:
         return t
 
     def _tc(self, B, H, W, ci, co, up=0):
-        # The tcgen05 kernel where it measured faster than the mma.sync one (GB300): layers with at
-        # least one 128 x 128 output tile per SM (its persistent CTAs take one SM each; smaller layers
-        # leave most SMs idle: batch 4 with every supported layer on it ran 0.469 against 0.387 ms
-        # per forward), except the upsampled convolutions of rows of 256 pixels or more
-        # (cp.async-staged rows: 256^2 64 -> 32 at batch 16, 169 against 163 us).  Elsewhere it is
-        # faster (batch 16: 64^2 128 -> 128 58 against 64 us, 128^2 64 -> 64 47 against 64 us).
-        # Both kernels give the same bits (same accumulation order): the choice changes only time.
-        tiles = B * H * W // 128 * max(1, co // 128)  # 128-pixel x 128-channel tiles
-        return (self.tensor_cores and not (up and W >= 256) and tiles >= self.sms and
-                sur_conv3x3_tc_supported(B, H, W, ci, co, up))
+        # Which kernel runs a convolution: the faster of the two on this GPU for the shape, timed
+        # once outside graph capture (tune_layer) and cached.  Both give the same bits (same
+        # accumulation order), so the choice changes only time.  Under capture, before a shape
+        # was timed: the tcgen05 kernel on layers with at least one 128 x 128 output tile per SM
+        # (its persistent CTAs take one SM each; smaller layers leave most SMs idle), which
+        # measured within a few percent of the timed choice on the default network.
+        if not self.tensor_cores or not sur_conv3x3_tc_supported(B, H, W, ci, co, up):
+            return False
+        key = (B, H, W, ci, co, up)
+        if key not in self._choice and self.autotune and not self.torch.cuda.is_current_stream_capturing():
+            self._choice[key] = self.tune_layer(B, H, W, ci, co, up)
+        if key in self._choice:
+            return self._choice[key]
+        return B * H * W // 128 * max(1, co // 128) >= self.sms
+
+    def tune_layer(self, B, H, W, ci, co, up=0, reps=10):
+        """Time the tcgen05 and the mma.sync convolution of this shape (scratch tensors, the
+        network's stream) and return True if the tcgen05 one is faster."""
+        torch = self.torch
+        dev = self.w["out"].device
+        hs, ws = (H // 2, W // 2) if up else (H, W)
+        x = torch.zeros((B, hs, ws, ci), dtype=torch.bfloat16, device=dev)
+        wb = torch.zeros((9, ci, co), dtype=torch.bfloat16, device=dev)
+        wt = torch.zeros((9, co, ci), dtype=torch.bfloat16, device=dev)
+        b = torch.zeros(co, dtype=torch.float32, device=dev)
+        y = torch.empty((B, H, W, co), dtype=torch.bfloat16, device=dev)
+        add = torch.zeros((B, H, W, co), dtype=torch.bfloat16, device=dev) if up else None
+        s = self.s
+        runs = {
+            True: lambda: sur_conv3x3_tc(x, wt, b, add, y, B, H, W, ci, co, 0 if up else 1, 0, up, s),
+            False: ((lambda: sur_conv3x3_up_add(x, wb, b, add, y, B, H, W, ci, co, s)) if up else
+                    (lambda: sur_conv3x3(x, wb, b, y, B, H, W, ci, co, 0, 1, 1, 0, s))),
+        }
+        ms = {}
+        with torch.cuda.stream(self.stream):
+            for k, fn in runs.items():
+                for _ in range(3):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(self.stream)
+                e1.synchronize()
+                ms[k] = e0.elapsed_time(e1)
+        return ms[True] < ms[False]
 
     def _conv(self, x, name, B, H, W, relu, out_f32=False, key=None):
         _, ci, co = next(l for l in self.layers if l[0] == name)
@@ -904,7 +942,7 @@ def _main(argv=None):
     graph = time_forward(net, x, base, reps=a.reps, graph=True)
     print(f"batch {a.batch} image {a.n}x{a.n}: {eager:.4f} ms/forward eager, {graph:.4f} ms/forward graph "
           f"({net.launches_per_forward()} launches per forward, "
-          f"{'mma.sync' if a.mma_sync else 'tcgen05 where supported'})")
+          f"{'mma.sync' if a.mma_sync else 'faster kernel per layer, timed'})")
 
 
 if __name__ == "__main__":

@@ -416,10 +416,10 @@ def test_tcgen05_conv_refuses_shapes_it_cannot_tile(S):
 
 
 def test_network_forward_same_on_both_tensor_core_paths(S):
-    """The U-Net forward with every convolution the tcgen05 kernel serves on it (all but the
-    upsampled 256^2 one: TMA rows, multi-accumulator shifted copies, upsampled rows of 128)
-    equals the forward on the mma.sync kernels bit for bit: both accumulate every 16-channel chunk
-    tap by tap in the same order on the same tensor-core dot products."""
+    """The U-Net forward with every convolution the tcgen05 kernel serves on it (TMA rows of 4 or
+    8 output rows per tile, multi-accumulator shifted copies, upsampled rows), whatever the timed
+    choice would be, equals the forward on the mma.sync kernels bit for bit: both accumulate every
+    16-channel chunk tap by tap in the same order on the same tensor-core dot products."""
     import torch
     net = S.UNet(ch=(32, 64, 128, 256), cin=16, seed=1)
     g = torch.Generator(device="cuda").manual_seed(3)
@@ -428,8 +428,10 @@ def test_network_forward_same_on_both_tensor_core_paths(S):
     x = (torch.randn((2, 256, 256, 16), device="cuda", generator=g) * 0.5).to(torch.bfloat16)
     base = x[..., :3].float().contiguous()
     net.tensor_cores = True
+    net._tc = lambda B, H, W, ci, co, up=0: S.sur_conv3x3_tc_supported(B, H, W, ci, co, up)
     p1 = net.forward(x, base).clone()
     net.tensor_cores = False
+    net._tc = lambda *a, **k: False
     p0 = net.forward(x, base).clone()
     torch.cuda.synchronize()
     assert torch.equal(p1, p0)

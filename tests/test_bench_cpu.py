@@ -40,3 +40,18 @@ def test_reference_arm_other_ranks_exit_without_work():
                   "--warmup", "3")
     assert r.returncode == 0, r.stderr[-2000:]
     assert json_lines(r.stdout) == []
+
+
+def test_kernel_choices_name_library_variants():
+    """bench.py --kernel maps each choice to a step kernel the C ABI declares, with that kernel's
+    default tile, and the ncu traffic of the 16-bit and FP32 steps is keyed on different sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1803_11345_gb300 import build
+    build.build()
+    from paper_1803_11345_gb300 import lbm
+    variants = {name: spec[0](lbm) for name, spec in bench.KERNELS.items()}
+    assert variants == {"generic": lbm.LBM_KERNEL_GENERIC, "pair": lbm.LBM_KERNEL_PAIR,
+                        "pair_staged": lbm.LBM_KERNEL_PAIR_STAGED}
+    assert bench.KERNELS["pair"][1:3] == (128, 1) and bench.KERNELS["pair_staged"][1:3] == (128, 1)
+    assert bench.kernel_source_hash("fp16s") != bench.kernel_source_hash("fp32")
